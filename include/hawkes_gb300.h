@@ -1,0 +1,156 @@
+/*
+ * hawkes_gb300.h — C ABI of the GB300 (sm_103a) library for the exact
+ * log-likelihood of a multivariate linear exponential Hawkes process and its
+ * gradient.
+ *
+ * Problem statement (paper "Massively Parallel Exact Inference for Hawkes
+ * Processes", Section 2):
+ *   events   H = {(t_k, c_k)}, k = 0..N-1, t non-decreasing on [0, T], c_k in [0, M)
+ *   intensity lambda_i(t) = mu_i + sum_{l before t} alpha[i][c_l] beta_{c_l} exp(-beta_{c_l} (t - t_l))
+ *            (Eq. hawkes_excitation with one decay per source mark; a shared decay is the
+ *             special case of Eq. hawkes_excitation with K = 1)
+ *   L        = sum_k log lambda_{c_k}(t_k) - sum_i int_0^T lambda_i(t) dt
+ *            (Eq. general_hawkes_likelihood, with the closed-form compensator
+ *             T sum_i mu_i + sum_l colsum_{c_l} (1 - exp(-beta_{c_l} (T - t_l))))
+ *   grads    dL/dmu, dL/dalpha, dL/dbeta (Appendix B, Eqs. grad_mu, grad_alpha, grad_gamma)
+ *
+ * Conventions
+ *   - Marks are 0-based (the paper counts 1..M).
+ *   - alpha is row-major M x M with row = TARGET mark, column = SOURCE mark, as the
+ *     formula of Eq. hawkes_excitation indexes it.
+ *   - beta: opts->beta_shared = 1 -> one decay beta[0] shared by every source (the
+ *     gradient d_beta is then ONE float); 0 -> beta[M], one decay per source (d_beta[M]).
+ *   - Gradients are of L itself, not of the per-event NLL -L/N.
+ *   - Ties (equal times) count the earlier-indexed event at full weight, as the
+ *     state recurrence of Eq. intensity_state_recurrence does with dt = 0.
+ *   - N = 0 is legal: L = -T sum mu and the gradients reduce to the compensator terms.
+ *
+ * Memory and ownership
+ *   - Every array argument of the device entry points is a DEVICE pointer owned by
+ *     the caller; the library never frees or keeps them.  Times are FP64, marks int32,
+ *     parameters FP32, the log-likelihood FP64, gradients FP32.
+ *   - The library allocates no memory: the caller passes a device workspace of at least
+ *     hawkes_workspace_size(...) bytes, 256-byte aligned.  Its contents on entry do not
+ *     matter; it holds the device status word afterwards.  One workspace must not be
+ *     used by two calls that run concurrently.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy default
+ *     stream).  Nothing is read back to the host except by the *_host entry points and
+ *     hawkes_last_device_status.
+ *
+ * Errors
+ *   - Errors found on the host (null pointers, sizes, a too-small workspace, an
+ *     unsupported configuration, a failed launch) are returned at once and nothing is
+ *     launched.
+ *   - Errors found on the device (unsorted times, a mark outside [0, M), a time outside
+ *     [0, T], mu <= 0, alpha < 0, beta <= 0, a non-finite parameter, an intensity <= 0)
+ *     are written to the status word in the workspace; the outputs of that call are then
+ *     NaN.  hawkes_last_device_status synchronises the stream and returns that word.
+ */
+#ifndef HAWKES_GB300_H
+#define HAWKES_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HAWKES_OK = 0,
+    HAWKES_ERR_INVALID_ARG = 1,       /* null pointer, negative size, bad offsets, T < 0      */
+    HAWKES_ERR_UNSORTED = 2,          /* t[k] < t[k-1] inside one sequence                     */
+    HAWKES_ERR_MARK_RANGE = 3,        /* c[k] outside [0, M)                                   */
+    HAWKES_ERR_TIME_RANGE = 4,        /* t[k] outside [0, T] (or not finite)                   */
+    HAWKES_ERR_PARAM_DOMAIN = 5,      /* mu <= 0, alpha < 0, beta <= 0, or a non-finite value  */
+    HAWKES_ERR_NONPOS_INTENSITY = 6,  /* some lambda_k <= 0 (impossible inside the domain)     */
+    HAWKES_ERR_WORKSPACE = 7,         /* workspace null, too small or not 256-byte aligned     */
+    HAWKES_ERR_UNSUPPORTED = 8,       /* a configuration this build does not implement         */
+    HAWKES_ERR_CUDA = 9               /* a CUDA runtime call failed                            */
+} hawkes_status;
+
+typedef struct {
+    int32_t beta_shared;  /* 1: beta[0] is one decay shared by all sources; 0: beta[M]        */
+    int32_t chunk;        /* events per scan chunk; 0 = library default                        */
+    int32_t validate;     /* 1: run the device input checks (default); 0: trust the inputs      */
+    int32_t path;         /* 0: automatic; 1: state-walk kernels; 2: chunk-GEMM kernels
+                             (shared decay only).  Both give the same result within rounding.  */
+} hawkes_opts;
+
+/* Default options: per-source decay, default chunk, validation on, automatic path. */
+hawkes_opts hawkes_default_opts(void);
+
+/* Bytes of device workspace needed by a call on N events (all sequences together),
+ * M marks and B sequences (B = 1 for the single-sequence entry points).  `grad` = 1
+ * for the *_grad entry points.  Returns 0 if the configuration is unsupported. */
+size_t hawkes_workspace_size(int64_t N, int32_t M, int32_t B, int32_t grad,
+                             const hawkes_opts* opts);
+
+/* Log-likelihood of one sequence (paper, Eq. general_hawkes_likelihood).
+ *   t [N] FP64, c [N] int32, mu [M], alpha [M*M], beta [1 or M] FP32: device inputs.
+ *   T: the observation end (host scalar), T >= t[N-1].
+ *   out_ll: device pointer to ONE double, written with L. */
+hawkes_status hawkes_loglik(const double* t, const int32_t* c, int64_t N, double T,
+                            int32_t M, const float* mu, const float* alpha, const float* beta,
+                            const hawkes_opts* opts, void* workspace, size_t workspace_bytes,
+                            double* out_ll, void* stream);
+
+/* Log-likelihood and gradient of one sequence (paper, Eq. general_hawkes_likelihood and
+ * Appendix B, Eqs. grad_mu, grad_alpha, grad_gamma).  Inputs as hawkes_loglik.
+ *   out_ll [1] FP64, d_mu [M], d_alpha [M*M], d_beta [1 if shared else M] FP32: device outputs. */
+hawkes_status hawkes_loglik_grad(const double* t, const int32_t* c, int64_t N, double T,
+                                 int32_t M, const float* mu, const float* alpha,
+                                 const float* beta, const hawkes_opts* opts, void* workspace,
+                                 size_t workspace_bytes, double* out_ll, float* d_mu,
+                                 float* d_alpha, float* d_beta, void* stream);
+
+/* Batched forms over B independent sequences of uneven length (the paper fits one
+ * sequence at a time; the batch shares one launch sequence).  Sequence s owns events
+ * [offsets[s], offsets[s+1]) of t and c; offsets [B+1] int64 with offsets[0] = 0 and
+ * offsets[B] = N; T [B] FP64; mu [B*M]; alpha [B*M*M]; beta [B] if shared else [B*M].
+ * All device pointers.  out_ll [B] FP64; d_mu [B*M]; d_alpha [B*M*M]; d_beta [B or B*M]. */
+hawkes_status hawkes_loglik_varlen(const double* t, const int32_t* c, const int64_t* offsets,
+                                   int32_t B, int64_t N, const double* T, int32_t M,
+                                   const float* mu, const float* alpha, const float* beta,
+                                   const hawkes_opts* opts, void* workspace,
+                                   size_t workspace_bytes, double* out_ll, void* stream);
+
+hawkes_status hawkes_loglik_grad_varlen(const double* t, const int32_t* c,
+                                        const int64_t* offsets, int32_t B, int64_t N,
+                                        const double* T, int32_t M, const float* mu,
+                                        const float* alpha, const float* beta,
+                                        const hawkes_opts* opts, void* workspace,
+                                        size_t workspace_bytes, double* out_ll, float* d_mu,
+                                        float* d_alpha, float* d_beta, void* stream);
+
+/* End-to-end form of hawkes_loglik_grad with HOST buffers: copies t, c and the
+ * parameters from host memory (pinned memory makes the copies asynchronous) into the
+ * device workspace, runs the same kernels, copies L and the gradients back into host
+ * memory and synchronises `stream` before returning.  The workspace (device) must hold
+ * hawkes_workspace_size_host(N, M, opts) bytes.  Device-detected errors are returned
+ * directly (the call synchronises anyway). */
+size_t hawkes_workspace_size_host(int64_t N, int32_t M, const hawkes_opts* opts);
+hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t N, double T,
+                                      int32_t M, const float* mu, const float* alpha,
+                                      const float* beta, const hawkes_opts* opts,
+                                      void* workspace, size_t workspace_bytes, double* out_ll,
+                                      float* d_mu, float* d_alpha, float* d_beta, void* stream);
+
+/* Synchronises `stream` and returns the device status word of the last call that used
+ * `workspace` (HAWKES_OK if the device found nothing wrong). */
+hawkes_status hawkes_last_device_status(void* workspace, void* stream);
+
+/* Per-mark event counts of the last validated call on `workspace` (int64 [B*M], device),
+ * or NULL if that call did not validate.  The pointer is into the workspace. */
+const int64_t* hawkes_mark_counts(void* workspace);
+
+/* Static description of a status code. */
+const char* hawkes_status_str(hawkes_status s);
+
+/* Number of kernel launches made by the last call on this thread (for accounting). */
+int32_t hawkes_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HAWKES_GB300_H */

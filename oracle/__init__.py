@@ -1,0 +1,175 @@
+"""FP64 CPU oracle for the Hawkes log-likelihood and its gradient.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package; the library
+(``paper_2604_01342_gb300``) never does.  The arithmetic lives in plain C
+(``hawkes_oracle.c``, FP64, sequential, one loop over events); this module
+compiles it with gcc on first use and marshals numpy arrays through ctypes.
+
+Conventions: marks are 0-based; ``alpha[i, j]`` is the influence of source
+mark ``j`` on target mark ``i`` (paper, Section 2, Eq. hawkes_excitation);
+``beta`` is a per-source decay vector, a shared decay being the all-equal
+vector.  Gradients are of L itself (not of -L/N).
+
+What pins each function (see ``tests/test_oracle_pins.py``):
+  * ``loglik_grad``: brute-force O(N^2 M) double sum of Eq. hawkes_excitation,
+    quadrature of the compensator integral, the Poisson closed form at
+    alpha = 0, hand-derived one- and two-event closed forms, central finite
+    differences, the Euler identity for the 1-homogeneous (mu, alpha), time
+    shift / rescale / relabelling invariances.
+  * ``grad_adjoint``: equals ``loglik_grad`` (two derivations) and FD.
+  * ``paper_grad_shared``: the paper's R/K/L form, equal to the others at
+    small T.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hawkes_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsorted times", 3: "mark out of range",
+          4: "time outside [0, T]", 5: "parameter outside its domain", 6: "intensity <= 0"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"oracle: {STATUS.get(code, code)}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math: IEEE FP64 throughout)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
+                        "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int32
+            p = ctypes.c_void_p
+            lib.oracle_loglik_grad.argtypes = [i64, p, p, d, i32, p, p, p, p, p, p, p, p]
+            lib.oracle_grad_adjoint.argtypes = [i64, p, p, d, i32, p, p, p, p, p, p, p]
+            lib.oracle_paper_grad_shared.argtypes = [i64, p, p, d, i32, p, p, d, p, p, p, p]
+            lib.oracle_loglik_grad_varlen.argtypes = [p, p, p, i32, p, i32, p, p, p, p, p, p, p]
+            lib.oracle_mark_counts.argtypes = [i64, p, i32, p]
+            for f in (lib.oracle_loglik_grad, lib.oracle_grad_adjoint, lib.oracle_paper_grad_shared,
+                      lib.oracle_loglik_grad_varlen, lib.oracle_mark_counts):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prep(t, c, mu, alpha, beta):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    M = mu.shape[-1]
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    if beta.ndim == 0 or beta.shape[-1] != M:
+        beta = np.broadcast_to(beta.reshape(beta.shape + (1,) if beta.ndim else (1,)),
+                               mu.shape)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    return t, c, mu, alpha, beta, M
+
+
+def loglik_grad(t, c, T, mu, alpha, beta, want_grad=True, want_lam=False):
+    """L and (dmu, dalpha, dbeta per source) in one FP64 forward pass."""
+    t, c, mu, alpha, beta, M = _prep(t, c, mu, alpha, beta)
+    N = t.shape[0]
+    ll = np.zeros(1)
+    lam = np.zeros(N) if want_lam else None
+    dmu = np.zeros(M) if want_grad else None
+    dal = np.zeros((M, M)) if want_grad else None
+    dbe = np.zeros(M) if want_grad else None
+    rc = _load().oracle_loglik_grad(N, _ptr(t), _ptr(c), float(T), M, _ptr(mu), _ptr(alpha),
+                                    _ptr(beta), _ptr(ll), _ptr(lam), _ptr(dmu), _ptr(dal), _ptr(dbe))
+    if rc:
+        raise OracleError(rc)
+    out = {"ll": float(ll[0])}
+    if want_grad:
+        out.update(dmu=dmu, dalpha=dal, dbeta=dbe)
+    if want_lam:
+        out["lam"] = lam
+    return out
+
+
+def loglik(t, c, T, mu, alpha, beta) -> float:
+    return loglik_grad(t, c, T, mu, alpha, beta, want_grad=False)["ll"]
+
+
+def grad_adjoint(t, c, T, mu, alpha, beta):
+    """Reverse-adjoint gradient (stores all N states: small N only)."""
+    t, c, mu, alpha, beta, M = _prep(t, c, mu, alpha, beta)
+    N = t.shape[0]
+    ll, dmu, dal, dbe = np.zeros(1), np.zeros(M), np.zeros((M, M)), np.zeros(M)
+    rc = _load().oracle_grad_adjoint(N, _ptr(t), _ptr(c), float(T), M, _ptr(mu), _ptr(alpha),
+                                     _ptr(beta), _ptr(ll), _ptr(dmu), _ptr(dal), _ptr(dbe))
+    if rc:
+        raise OracleError(rc)
+    return {"ll": float(ll[0]), "dmu": dmu, "dalpha": dal, "dbeta": dbe}
+
+
+def paper_grad_shared(t, c, T, mu, alpha, gamma):
+    """The paper's R/K/L gradient formulas for one shared decay (small T only)."""
+    t, c, mu, alpha, _, M = _prep(t, c, mu, alpha, np.ones(np.shape(mu)))
+    N = t.shape[0]
+    ll, dmu, dal, dg = np.zeros(1), np.zeros(M), np.zeros((M, M)), np.zeros(1)
+    rc = _load().oracle_paper_grad_shared(N, _ptr(t), _ptr(c), float(T), M, _ptr(mu),
+                                          _ptr(alpha), float(gamma), _ptr(ll), _ptr(dmu),
+                                          _ptr(dal), _ptr(dg))
+    if rc:
+        raise OracleError(rc)
+    return {"ll": float(ll[0]), "dmu": dmu, "dalpha": dal, "dbeta": float(dg[0])}
+
+
+def loglik_grad_varlen(t, c, offsets, T, mu, alpha, beta, want_grad=True):
+    """Per-sequence L and gradients for B independent sequences."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    B = offsets.shape[0] - 1
+    T = np.ascontiguousarray(T, dtype=np.float64).reshape(B)
+    t, c, mu, alpha, beta, M = _prep(t, c, mu, alpha, beta)
+    ll = np.zeros(B)
+    dmu = np.zeros((B, M)) if want_grad else None
+    dal = np.zeros((B, M, M)) if want_grad else None
+    dbe = np.zeros((B, M)) if want_grad else None
+    rc = _load().oracle_loglik_grad_varlen(_ptr(t), _ptr(c), _ptr(offsets), B, _ptr(T), M,
+                                           _ptr(mu), _ptr(alpha), _ptr(beta), _ptr(ll),
+                                           _ptr(dmu), _ptr(dal), _ptr(dbe))
+    if rc:
+        raise OracleError(rc)
+    out = {"ll": ll}
+    if want_grad:
+        out.update(dmu=dmu, dalpha=dal, dbeta=dbe)
+    return out
+
+
+def mark_counts(c, M):
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    out = np.zeros(M, dtype=np.int64)
+    rc = _load().oracle_mark_counts(c.shape[0], _ptr(c), M, _ptr(out))
+    if rc:
+        raise OracleError(rc)
+    return out

@@ -1,0 +1,336 @@
+/*
+ * FP64 CPU oracle for the exact log-likelihood of a multivariate linear
+ * exponential Hawkes process and its gradient.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, sequential, obviously
+ * correct statement of what the GPU library computes.  It shares no code,
+ * header, table or constant with the CUDA library, and the library never
+ * calls it.  Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg load it.
+ *
+ * Model (paper, Section 2, Eq. hawkes_excitation with one decay kernel per
+ * source mark):
+ *     lambda_p(t) = mu_p + sum_{l : l before t} alpha[p][c_l] beta_{c_l} exp(-beta_{c_l} (t - t_l))
+ * Row p of alpha is the TARGET, column q the SOURCE (the formula of Eq.
+ * hawkes_excitation indexes alpha by (target, source mark)).  Marks are
+ * 0-based.  A shared decay is the special case beta_j = beta for all j.
+ *
+ * Log-likelihood (paper, Section 2, Eq. general_hawkes_likelihood):
+ *     L = sum_k log lambda_{c_k}(t_k) - sum_m int_0^T lambda_m(t) dt
+ * with the closed-form compensator (paper, Section 2, text after the NLL
+ * objective, and the second term of Eq. grad_alpha):
+ *     int_0^T sum_m lambda_m = T sum_i mu_i
+ *                              + sum_l colsum_{c_l} (1 - exp(-beta_{c_l} (T - t_l))),
+ *     colsum_j = sum_i alpha[i][j].
+ *
+ * Source-indexed state (paper, Appendix B, the K recurrence of Eq.
+ * alpha_grad_recurrence, here with a per-source decay):
+ *     S_1 = 0,  S_k = D_k (S_{k-1} + e_{c_{k-1}}),  D_k = diag(exp(-beta_j (t_k - t_{k-1}))),
+ *     lambda_k = mu_{c_k} + sum_j alpha[c_k][j] beta_j S_{k,j}.
+ * Ties (t_k == t_{k-1}) follow the recurrence: an earlier-indexed event
+ * counts with weight exp(0) = 1.
+ *
+ * Gradients (paper, Appendix B, Eqs. grad_mu, grad_alpha, grad_gamma):
+ *   dL/dmu_i       = sum_{k : c_k = i} w_k - T,                 w_k = 1 / lambda_k
+ *   dL/dalpha_ij   = beta_j sum_{k : c_k = i} w_k S_{k,j} - E_j,
+ *                    E_j = sum_{l : c_l = j} (1 - exp(-beta_j (T - t_l)))
+ *   dL/dbeta_j     = sum_k w_k alpha[c_k][j] (S_{k,j} - beta_j G_{k,j}) - colsum_j F_j,
+ *                    F_j = sum_{l : c_l = j} (T - t_l) exp(-beta_j (T - t_l))
+ * where G_{k,j} = sum_{l<k, c_l=j} (t_k - t_l) exp(-beta_j (t_k - t_l)) = -dS_{k,j}/dbeta_j
+ * obeys G_1 = 0, G_k = D_k (G_{k-1} + dt_k (S_{k-1} + e_{c_{k-1}})).
+ * This is Eq. grad_gamma rewritten with a source-indexed state: the paper's
+ * (1 - gamma t) R + gamma L equals R - gamma (alpha G); the G form avoids the
+ * cancellation of t R against L when t is large.  The paper's own R/L form is
+ * also given below (oracle_paper_grad_shared) as a cross-check for small T.
+ *
+ * Return codes: 0 ok, 1 invalid argument, 2 unsorted times, 3 mark out of
+ * range, 4 time outside [0, T], 5 parameter outside its domain, 6 an
+ * intensity <= 0.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_OK = 0, OR_INVALID = 1, OR_UNSORTED = 2, OR_MARK = 3, OR_TIME = 4,
+       OR_PARAM = 5, OR_NONPOS = 6 };
+
+static int check_inputs(int64_t N, const double* t, const int32_t* c, double T,
+                        int32_t M, const double* mu, const double* alpha,
+                        const double* beta)
+{
+    if (M <= 0 || N < 0 || !(T >= 0.0) || !isfinite(T)) return OR_INVALID;
+    if (N > 0 && (!t || !c)) return OR_INVALID;
+    if (!mu || !alpha || !beta) return OR_INVALID;
+    for (int32_t i = 0; i < M; ++i) {
+        if (!(mu[i] > 0.0) || !isfinite(mu[i])) return OR_PARAM;
+        if (!(beta[i] > 0.0) || !isfinite(beta[i])) return OR_PARAM;
+    }
+    for (int64_t e = 0; e < (int64_t)M * M; ++e)
+        if (!(alpha[e] >= 0.0) || !isfinite(alpha[e])) return OR_PARAM;
+    for (int64_t k = 0; k < N; ++k) {
+        if (c[k] < 0 || c[k] >= M) return OR_MARK;
+        if (!(t[k] >= 0.0) || !(t[k] <= T)) return OR_TIME;
+        if (k > 0 && t[k] < t[k - 1]) return OR_UNSORTED;
+    }
+    return OR_OK;
+}
+
+/* Log-likelihood and gradient in one forward pass (forward-mode G state).
+ * Any of lam, dmu, dalpha, dbeta may be NULL.  dbeta is per source (length M);
+ * for a shared decay the caller sums it.  Memory O(M^2 + M); time O(N M). */
+int oracle_loglik_grad(int64_t N, const double* t, const int32_t* c, double T,
+                       int32_t M, const double* mu, const double* alpha,
+                       const double* beta, double* out_ll, double* lam,
+                       double* dmu, double* dalpha, double* dbeta)
+{
+    int rc = check_inputs(N, t, c, T, M, mu, alpha, beta);
+    if (rc) return rc;
+    double* S = calloc((size_t)M, sizeof(double));
+    double* G = calloc((size_t)M, sizeof(double));
+    double* E = calloc((size_t)M, sizeof(double));
+    double* F = calloc((size_t)M, sizeof(double));
+    if (!S || !G || !E || !F) { free(S); free(G); free(E); free(F); return OR_INVALID; }
+    if (dmu) memset(dmu, 0, sizeof(double) * (size_t)M);
+    if (dalpha) memset(dalpha, 0, sizeof(double) * (size_t)M * (size_t)M);
+    if (dbeta) memset(dbeta, 0, sizeof(double) * (size_t)M);
+
+    double logsum = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        if (k > 0) {
+            /* S_k = D_k (S_{k-1} + e_{c_{k-1}}), G_k = D_k (G_{k-1} + dt (S_{k-1} + e_{c_{k-1}})) */
+            double dt = t[k] - t[k - 1];
+            int32_t prev = c[k - 1];
+            for (int32_t j = 0; j < M; ++j) {
+                double d = exp(-beta[j] * dt);
+                double P = S[j] + (j == prev ? 1.0 : 0.0);
+                G[j] = d * (G[j] + dt * P);
+                S[j] = d * P;
+            }
+        }
+        int32_t i = c[k];
+        const double* arow = alpha + (size_t)i * (size_t)M;
+        double exc = 0.0;
+        for (int32_t j = 0; j < M; ++j) exc += arow[j] * beta[j] * S[j];
+        double lk = mu[i] + exc;
+        if (!(lk > 0.0)) { rc = OR_NONPOS; break; }
+        if (lam) lam[k] = lk;
+        logsum += log(lk);
+        double w = 1.0 / lk;
+        if (dmu) dmu[i] += w;
+        if (dalpha) {
+            double* drow = dalpha + (size_t)i * (size_t)M;
+            for (int32_t j = 0; j < M; ++j) drow[j] += w * beta[j] * S[j];
+        }
+        if (dbeta)
+            for (int32_t j = 0; j < M; ++j) dbeta[j] += w * arow[j] * (S[j] - beta[j] * G[j]);
+        /* compensator pieces of event k as a source */
+        double x = beta[i] * (T - t[k]);
+        E[i] += -expm1(-x);
+        F[i] += (T - t[k]) * exp(-x);
+    }
+    if (rc == OR_OK) {
+        double summu = 0.0, comp = 0.0;
+        for (int32_t i = 0; i < M; ++i) summu += mu[i];
+        for (int32_t j = 0; j < M; ++j) {
+            double cs = 0.0;
+            for (int32_t i = 0; i < M; ++i) cs += alpha[(size_t)i * M + j];
+            comp += cs * E[j];
+            if (dbeta) dbeta[j] -= cs * F[j];
+        }
+        if (out_ll) *out_ll = logsum - T * summu - comp;
+        if (dmu) for (int32_t i = 0; i < M; ++i) dmu[i] -= T;
+        if (dalpha)
+            for (int32_t i = 0; i < M; ++i)
+                for (int32_t j = 0; j < M; ++j) dalpha[(size_t)i * M + j] -= E[j];
+    }
+    free(S); free(G); free(E); free(F);
+    return rc;
+}
+
+/* Gradient by the reverse-time adjoint of the same transitions (small N:
+ * stores every state, O(N M) memory).  psi_k = dL_log/dS_k obeys
+ *     psi_N = w_N beta (.) alpha[c_N,:],   psi_k = w_k beta (.) alpha[c_k,:] + D_{k+1} psi_{k+1},
+ * and dL/dbeta_j = sum_k w_k alpha[c_k][j] S_{k,j} - sum_{k>=2} dt_k psi_{k,j} S_{k,j}
+ *                  - colsum_j F_j  (chain rule through D_k, dS_{k,j}/dbeta_j|local = -dt_k S_{k,j}).
+ * dmu and dalpha are as in oracle_loglik_grad. */
+int oracle_grad_adjoint(int64_t N, const double* t, const int32_t* c, double T,
+                        int32_t M, const double* mu, const double* alpha,
+                        const double* beta, double* out_ll, double* dmu,
+                        double* dalpha, double* dbeta)
+{
+    int rc = check_inputs(N, t, c, T, M, mu, alpha, beta);
+    if (rc) return rc;
+    size_t NM = (size_t)(N > 0 ? N : 1) * (size_t)M;
+    double* S = calloc(NM, sizeof(double));        /* S[k*M + j] */
+    double* w = calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double* psi = calloc((size_t)M, sizeof(double));
+    double* E = calloc((size_t)M, sizeof(double));
+    double* F = calloc((size_t)M, sizeof(double));
+    if (!S || !w || !psi || !E || !F) { rc = OR_INVALID; goto done; }
+    memset(dmu, 0, sizeof(double) * (size_t)M);
+    memset(dalpha, 0, sizeof(double) * (size_t)M * (size_t)M);
+    memset(dbeta, 0, sizeof(double) * (size_t)M);
+
+    double logsum = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        double* Sk = S + (size_t)k * M;
+        if (k > 0) {
+            const double* Sp = S + (size_t)(k - 1) * M;
+            double dt = t[k] - t[k - 1];
+            for (int32_t j = 0; j < M; ++j)
+                Sk[j] = exp(-beta[j] * dt) * (Sp[j] + (j == c[k - 1] ? 1.0 : 0.0));
+        }
+        int32_t i = c[k];
+        double lk = mu[i];
+        for (int32_t j = 0; j < M; ++j) lk += alpha[(size_t)i * M + j] * beta[j] * Sk[j];
+        if (!(lk > 0.0)) { rc = OR_NONPOS; goto done; }
+        logsum += log(lk);
+        w[k] = 1.0 / lk;
+        dmu[i] += w[k];
+        for (int32_t j = 0; j < M; ++j) {
+            dalpha[(size_t)i * M + j] += w[k] * beta[j] * Sk[j];
+            dbeta[j] += w[k] * alpha[(size_t)i * M + j] * Sk[j];
+        }
+        double x = beta[i] * (T - t[k]);
+        E[i] += -expm1(-x);
+        F[i] += (T - t[k]) * exp(-x);
+    }
+    /* reverse sweep */
+    for (int64_t k = N - 1; k >= 0; --k) {
+        if (k < N - 1) {
+            double dt1 = t[k + 1] - t[k];
+            for (int32_t j = 0; j < M; ++j) psi[j] *= exp(-beta[j] * dt1);
+        }
+        int32_t i = c[k];
+        for (int32_t j = 0; j < M; ++j) psi[j] += w[k] * beta[j] * alpha[(size_t)i * M + j];
+        if (k > 0) {
+            double dt = t[k] - t[k - 1];
+            const double* Sk = S + (size_t)k * M;
+            for (int32_t j = 0; j < M; ++j) dbeta[j] -= dt * psi[j] * Sk[j];
+        }
+    }
+    {
+        double summu = 0.0, comp = 0.0;
+        for (int32_t i = 0; i < M; ++i) summu += mu[i];
+        for (int32_t j = 0; j < M; ++j) {
+            double cs = 0.0;
+            for (int32_t i = 0; i < M; ++i) cs += alpha[(size_t)i * M + j];
+            comp += cs * E[j];
+            dbeta[j] -= cs * F[j];
+        }
+        *out_ll = logsum - T * summu - comp;
+        for (int32_t i = 0; i < M; ++i) dmu[i] -= T;
+        for (int32_t i = 0; i < M; ++i)
+            for (int32_t j = 0; j < M; ++j) dalpha[(size_t)i * M + j] -= E[j];
+    }
+done:
+    free(S); free(w); free(psi); free(E); free(F);
+    return rc;
+}
+
+/* The paper's own gradient formulas for one shared decay gamma (Appendix B,
+ * Eqs. grad_mu, grad_alpha, grad_gamma), driven by the paper's three state
+ * recurrences: R (Eq. intensity_state_recurrence, target-indexed, alpha
+ * folded in), K (Eq. alpha_grad_recurrence) and L (Eq.
+ * gamma_grad_recurrence):
+ *   R_i = e^{-g dt}(R_{i-1} + alpha[:, m_{i-1}]),  K_i = e^{-g dt}(K_{i-1} + e_{m_{i-1}}),
+ *   L_i = e^{-g dt}(L_{i-1} + t_{i-1} alpha[:, m_{i-1}]),
+ *   dL/dgamma = sum_i [(1 - g t_i) R_{m_i} + g L_{m_i}] / lambda_i
+ *               - sum_m sum_i alpha[m][m_i] (T - t_i) e^{-g (T - t_i)}.
+ * The (1 - g t) R + g L combination loses about log10(g t) digits; use it
+ * only with small T.  Outputs dL/dmu[M], dL/dalpha[M*M], dL/dgamma (scalar). */
+int oracle_paper_grad_shared(int64_t N, const double* t, const int32_t* c, double T,
+                             int32_t M, const double* mu, const double* alpha,
+                             double gamma, double* out_ll, double* dmu,
+                             double* dalpha, double* dgamma)
+{
+    if (!(gamma > 0.0)) return OR_PARAM;
+    double* bvec = malloc(sizeof(double) * (size_t)M);
+    if (!bvec) return OR_INVALID;
+    for (int32_t j = 0; j < M; ++j) bvec[j] = gamma;
+    int rc = check_inputs(N, t, c, T, M, mu, alpha, bvec);
+    free(bvec);
+    if (rc) return rc;
+    double* R = calloc((size_t)M, sizeof(double));
+    double* K = calloc((size_t)M, sizeof(double));
+    double* L = calloc((size_t)M, sizeof(double));
+    if (!R || !K || !L) { free(R); free(K); free(L); return OR_INVALID; }
+    memset(dmu, 0, sizeof(double) * (size_t)M);
+    memset(dalpha, 0, sizeof(double) * (size_t)M * (size_t)M);
+    double g_acc = 0.0, logsum = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        if (k > 0) {
+            double d = exp(-gamma * (t[k] - t[k - 1]));
+            int32_t q = c[k - 1];
+            for (int32_t p = 0; p < M; ++p) {
+                double a = alpha[(size_t)p * M + q];
+                R[p] = d * (R[p] + a);
+                L[p] = d * (L[p] + t[k - 1] * a);
+                K[p] = d * (K[p] + (p == q ? 1.0 : 0.0));
+            }
+        }
+        int32_t p = c[k];
+        double lk = mu[p] + gamma * R[p];
+        if (!(lk > 0.0)) { rc = OR_NONPOS; break; }
+        logsum += log(lk);
+        dmu[p] += 1.0 / lk;
+        for (int32_t q = 0; q < M; ++q) dalpha[(size_t)p * M + q] += gamma * K[q] / lk;
+        g_acc += ((1.0 - gamma * t[k]) * R[p] + gamma * L[p]) / lk;
+    }
+    if (rc == OR_OK) {
+        double summu = 0.0, comp = 0.0;
+        for (int32_t i = 0; i < M; ++i) summu += mu[i];
+        for (int64_t k = 0; k < N; ++k) {
+            int32_t q = c[k];
+            double cs = 0.0;
+            for (int32_t m = 0; m < M; ++m) cs += alpha[(size_t)m * M + q];
+            double x = gamma * (T - t[k]);
+            comp += cs * (-expm1(-x));
+            g_acc -= cs * (T - t[k]) * exp(-x);
+            for (int32_t pp = 0; pp < M; ++pp) dalpha[(size_t)pp * M + q] -= -expm1(-x);
+        }
+        for (int32_t i = 0; i < M; ++i) dmu[i] -= T;
+        *out_ll = logsum - T * summu - comp;
+        *dgamma = g_acc;
+    }
+    free(R); free(K); free(L);
+    return rc;
+}
+
+/* Batched form: B independent sequences, events of sequence s are
+ * [offsets[s], offsets[s+1]) of t and c, each with its own T[s], mu[s*M..],
+ * alpha[s*M*M..], beta[s*M..].  Outputs are per sequence; grads may be NULL. */
+int oracle_loglik_grad_varlen(const double* t, const int32_t* c, const int64_t* offsets,
+                              int32_t B, const double* T, int32_t M,
+                              const double* mu, const double* alpha, const double* beta,
+                              double* out_ll, double* dmu, double* dalpha, double* dbeta)
+{
+    if (B < 0 || !offsets) return OR_INVALID;
+    if (offsets[0] != 0) return OR_INVALID;
+    for (int32_t s = 0; s < B; ++s)
+        if (offsets[s + 1] < offsets[s]) return OR_INVALID;
+    for (int32_t s = 0; s < B; ++s) {
+        int64_t o = offsets[s], n = offsets[s + 1] - offsets[s];
+        size_t pm = (size_t)s * M, pa = (size_t)s * M * M;
+        int rc = oracle_loglik_grad(n, t ? t + o : NULL, c ? c + o : NULL, T[s], M,
+                                    mu + pm, alpha + pa, beta + pm, out_ll + s, NULL,
+                                    dmu ? dmu + pm : NULL, dalpha ? dalpha + pa : NULL,
+                                    dbeta ? dbeta + pm : NULL);
+        if (rc) return rc;
+    }
+    return OR_OK;
+}
+
+/* Integer pass: per-mark event counts, bit-exact reference for the library's
+ * validate-and-count step.  Returns the same codes as check of the inputs. */
+int oracle_mark_counts(int64_t N, const int32_t* c, int32_t M, int64_t* counts)
+{
+    if (M <= 0 || N < 0) return OR_INVALID;
+    memset(counts, 0, sizeof(int64_t) * (size_t)M);
+    for (int64_t k = 0; k < N; ++k) {
+        if (c[k] < 0 || c[k] >= M) return OR_MARK;
+        counts[c[k]] += 1;
+    }
+    return OR_OK;
+}

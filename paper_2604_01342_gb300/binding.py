@@ -1,0 +1,165 @@
+"""ctypes binding of the C ABI declared in ``include/hawkes_gb300.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libhawkes_gb300.so``.  Tensors are passed as raw device pointers
+(``torch.Tensor.data_ptr()``) together with the current CUDA stream.  The
+library is loaded on first use; if it is missing the call raises, there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_NAME = "libhawkes_gb300.so"
+_lock = threading.Lock()
+_lib = None
+
+STATUS_NAMES = {
+    0: "HAWKES_OK", 1: "HAWKES_ERR_INVALID_ARG", 2: "HAWKES_ERR_UNSORTED",
+    3: "HAWKES_ERR_MARK_RANGE", 4: "HAWKES_ERR_TIME_RANGE", 5: "HAWKES_ERR_PARAM_DOMAIN",
+    6: "HAWKES_ERR_NONPOS_INTENSITY", 7: "HAWKES_ERR_WORKSPACE", 8: "HAWKES_ERR_UNSUPPORTED",
+    9: "HAWKES_ERR_CUDA",
+}
+
+# every symbol include/hawkes_gb300.h declares
+EXPORTED = (
+    "hawkes_default_opts", "hawkes_workspace_size", "hawkes_loglik", "hawkes_loglik_grad",
+    "hawkes_loglik_varlen", "hawkes_loglik_grad_varlen", "hawkes_workspace_size_host",
+    "hawkes_loglik_grad_host", "hawkes_last_device_status", "hawkes_mark_counts",
+    "hawkes_status_str", "hawkes_last_launch_count",
+)
+
+
+class HawkesOpts(ctypes.Structure):
+    _fields_ = [("beta_shared", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("validate", ctypes.c_int32), ("path", ctypes.c_int32)]
+
+
+class HawkesError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        name = STATUS_NAMES.get(code, str(code))
+        super().__init__(f"{where}: {name}" if where else name)
+        self.code = code
+        self.name = name
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", _LIB_NAME)
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{_LIB_NAME} is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        p, i32, i64, d, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                              ctypes.c_size_t)
+        op = ctypes.POINTER(HawkesOpts)
+        L.hawkes_default_opts.argtypes = []
+        L.hawkes_default_opts.restype = HawkesOpts
+        L.hawkes_workspace_size.argtypes = [i64, i32, i32, i32, op]
+        L.hawkes_workspace_size.restype = sz
+        L.hawkes_loglik.argtypes = [p, p, i64, d, i32, p, p, p, op, p, sz, p, p]
+        L.hawkes_loglik_grad.argtypes = [p, p, i64, d, i32, p, p, p, op, p, sz, p, p, p, p, p]
+        L.hawkes_loglik_varlen.argtypes = [p, p, p, i32, i64, p, i32, p, p, p, op, p, sz, p, p]
+        L.hawkes_loglik_grad_varlen.argtypes = [p, p, p, i32, i64, p, i32, p, p, p, op, p, sz,
+                                                p, p, p, p, p]
+        L.hawkes_workspace_size_host.argtypes = [i64, i32, op]
+        L.hawkes_workspace_size_host.restype = sz
+        L.hawkes_loglik_grad_host.argtypes = [p, p, i64, d, i32, p, p, p, op, p, sz, p, p, p,
+                                              p, p]
+        L.hawkes_last_device_status.argtypes = [p, p]
+        L.hawkes_mark_counts.argtypes = [p]
+        L.hawkes_mark_counts.restype = p
+        L.hawkes_status_str.argtypes = [ctypes.c_int]
+        L.hawkes_status_str.restype = ctypes.c_char_p
+        L.hawkes_last_launch_count.argtypes = []
+        L.hawkes_last_launch_count.restype = i32
+        for name in ("hawkes_loglik", "hawkes_loglik_grad", "hawkes_loglik_varlen",
+                     "hawkes_loglik_grad_varlen", "hawkes_loglik_grad_host",
+                     "hawkes_last_device_status"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def make_opts(beta_shared: bool, chunk: int = 0, validate: bool = True, path: int = 0):
+    return HawkesOpts(int(bool(beta_shared)), int(chunk), int(bool(validate)), int(path))
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise HawkesError(rc, where)
+
+
+def hawkes_status_str(code: int) -> str:
+    return lib().hawkes_status_str(int(code)).decode()
+
+
+def hawkes_workspace_size(N: int, M: int, B: int, grad: bool, opts: HawkesOpts) -> int:
+    n = lib().hawkes_workspace_size(int(N), int(M), int(B), int(bool(grad)), ctypes.byref(opts))
+    if n == 0:
+        raise HawkesError(8, "hawkes_workspace_size")
+    return int(n)
+
+
+def hawkes_loglik(t, c, N, T, M, mu, alpha, beta, opts, ws, ws_bytes, out_ll, stream):
+    _check(lib().hawkes_loglik(t, c, int(N), float(T), int(M), mu, alpha, beta,
+                               ctypes.byref(opts), ws, int(ws_bytes), out_ll, stream),
+           "hawkes_loglik")
+
+
+def hawkes_loglik_grad(t, c, N, T, M, mu, alpha, beta, opts, ws, ws_bytes, out_ll, d_mu,
+                       d_alpha, d_beta, stream):
+    _check(lib().hawkes_loglik_grad(t, c, int(N), float(T), int(M), mu, alpha, beta,
+                                    ctypes.byref(opts), ws, int(ws_bytes), out_ll, d_mu,
+                                    d_alpha, d_beta, stream), "hawkes_loglik_grad")
+
+
+def hawkes_loglik_varlen(t, c, offsets, B, N, T, M, mu, alpha, beta, opts, ws, ws_bytes,
+                         out_ll, stream):
+    _check(lib().hawkes_loglik_varlen(t, c, offsets, int(B), int(N), T, int(M), mu, alpha,
+                                      beta, ctypes.byref(opts), ws, int(ws_bytes), out_ll,
+                                      stream), "hawkes_loglik_varlen")
+
+
+def hawkes_loglik_grad_varlen(t, c, offsets, B, N, T, M, mu, alpha, beta, opts, ws, ws_bytes,
+                              out_ll, d_mu, d_alpha, d_beta, stream):
+    _check(lib().hawkes_loglik_grad_varlen(t, c, offsets, int(B), int(N), T, int(M), mu,
+                                           alpha, beta, ctypes.byref(opts), ws, int(ws_bytes),
+                                           out_ll, d_mu, d_alpha, d_beta, stream),
+           "hawkes_loglik_grad_varlen")
+
+
+def hawkes_workspace_size_host(N: int, M: int, opts: HawkesOpts) -> int:
+    n = lib().hawkes_workspace_size_host(int(N), int(M), ctypes.byref(opts))
+    if n == 0:
+        raise HawkesError(8, "hawkes_workspace_size_host")
+    return int(n)
+
+
+def hawkes_loglik_grad_host(t, c, N, T, M, mu, alpha, beta, opts, ws, ws_bytes, out_ll, d_mu,
+                            d_alpha, d_beta, stream):
+    _check(lib().hawkes_loglik_grad_host(t, c, int(N), float(T), int(M), mu, alpha, beta,
+                                         ctypes.byref(opts), ws, int(ws_bytes), out_ll, d_mu,
+                                         d_alpha, d_beta, stream), "hawkes_loglik_grad_host")
+
+
+def hawkes_last_device_status(ws, stream) -> int:
+    return int(lib().hawkes_last_device_status(ws, stream))
+
+
+def hawkes_mark_counts_ptr(ws) -> int:
+    return lib().hawkes_mark_counts(ws) or 0
+
+
+def hawkes_last_launch_count() -> int:
+    return int(lib().hawkes_last_launch_count())
