@@ -1,0 +1,349 @@
+// Host side of the C ABI (include/hawkes_gb300.h): argument checks, workspace
+// layout, path choice and the launch sequence.  No memory is allocated here.
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace {
+
+thread_local int32_t g_last_launches = 0;
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+constexpr int kDefaultChunkWalk = 128;
+constexpr int kDefaultChunkGemm = 64;
+
+enum Path { PATH_WALK = 1, PATH_GEMM = 2 };
+
+struct Plan {
+    int path;
+    int C;
+    int Gc;
+    int64_t nb_max, ng_max;
+    size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
+        off_grp_dt, off_grp_reset, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
+        off_dal_gemm, total;
+};
+
+// Returns 0 and fills the plan, or a hawkes_status.
+int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, Plan* pl) {
+    if (N < 0 || M <= 0 || B <= 0) return HAWKES_ERR_INVALID_ARG;
+    const int shared = o ? o->beta_shared : 0;
+    int path = o ? o->path : 0;
+    if (path == 0) path = (shared && M > hk::walk_max_m(grad)) ? PATH_GEMM : PATH_WALK;
+    if (path == PATH_WALK && M > hk::walk_max_m(grad)) return HAWKES_ERR_UNSUPPORTED;
+    if (path == PATH_GEMM && (!shared || B != 1)) return HAWKES_ERR_UNSUPPORTED;
+    if (path != PATH_WALK && path != PATH_GEMM) return HAWKES_ERR_INVALID_ARG;
+    int C = (o && o->chunk > 0) ? o->chunk : (path == PATH_WALK ? kDefaultChunkWalk
+                                                                : kDefaultChunkGemm);
+    if (C < 1 || C > 4096) return HAWKES_ERR_INVALID_ARG;
+    if (path == PATH_GEMM && C > 1024) return HAWKES_ERR_INVALID_ARG;
+    pl->path = path;
+    pl->C = C;
+    pl->nb_max = (N + C - 1) / C + B;
+    int64_t target_groups = 1216;  // ~8 blocks per SM on 152 SMs
+    int64_t gc = (pl->nb_max + target_groups - 1) / target_groups;
+    if (gc < 1) gc = 1;
+    if (gc > 64) gc = 64;
+    pl->Gc = (int)gc;
+    pl->ng_max = (pl->nb_max + gc - 1) / gc;
+    const size_t nbM = (size_t)pl->nb_max * M, ngM = (size_t)pl->ng_max * M;
+    size_t o_ = align_up(sizeof(hk::WsHeader));
+    auto take = [&](size_t bytes) { size_t at = o_; o_ = align_up(o_ + bytes); return at; };
+    pl->off_counts = take(sizeof(int64_t) * (size_t)B * M);
+    pl->off_chunk_base = take(sizeof(int64_t) * ((size_t)B + 1));
+    pl->off_chunk_seq = take(sizeof(int32_t) * (size_t)pl->nb_max);
+    pl->off_Shat = take(sizeof(float) * nbM);
+    pl->off_Ghat = grad ? take(sizeof(float) * nbM) : 0;
+    pl->off_grp_v = take(sizeof(float) * ngM);
+    pl->off_grp_g = grad ? take(sizeof(float) * ngM) : 0;
+    pl->off_grp_dt = take(sizeof(double) * (size_t)pl->ng_max);
+    pl->off_grp_reset = take(sizeof(int32_t) * (size_t)pl->ng_max);
+    pl->off_carry_S = take(sizeof(float) * ngM);
+    pl->off_carry_G = grad ? take(sizeof(float) * ngM) : 0;
+    size_t n_acc = (size_t)B * (1 + 4 * (size_t)M) + (grad ? (size_t)B * M * M : 0);
+    pl->off_acc = take(sizeof(double) * n_acc);
+    if (path == PATH_GEMM) {
+        pl->off_Y = take(sizeof(float) * nbM);
+        pl->off_Z = grad ? take(sizeof(float) * nbM) : 0;
+        pl->off_W = grad ? take(sizeof(float) * nbM) : 0;
+        pl->off_dal_gemm = grad ? take(sizeof(float) * (size_t)M * M) : 0;
+    } else {
+        pl->off_Y = pl->off_Z = pl->off_W = pl->off_dal_gemm = 0;
+    }
+    pl->total = o_;
+    return 0;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) { return off ? (T*)((char*)ws + off) : nullptr; }
+
+void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int grad) {
+    p.hdr = (hk::WsHeader*)ws;
+    p.counts = at<int64_t>(ws, pl.off_counts);
+    p.chunk_base = at<int64_t>(ws, pl.off_chunk_base);
+    p.chunk_seq = at<int32_t>(ws, pl.off_chunk_seq);
+    p.Shat = at<float>(ws, pl.off_Shat);
+    p.Ghat = at<float>(ws, pl.off_Ghat);
+    p.grp_v = at<float>(ws, pl.off_grp_v);
+    p.grp_g = at<float>(ws, pl.off_grp_g);
+    p.grp_dt = at<double>(ws, pl.off_grp_dt);
+    p.grp_reset = at<int32_t>(ws, pl.off_grp_reset);
+    p.carry_S = at<float>(ws, pl.off_carry_S);
+    p.carry_G = at<float>(ws, pl.off_carry_G);
+    double* acc = at<double>(ws, pl.off_acc);
+    const size_t BM = (size_t)B * M;
+    p.ll_acc = acc;
+    p.dmu_acc = acc + B;
+    p.dbe_acc = p.dmu_acc + BM;
+    p.E_acc = p.dbe_acc + BM;
+    p.F_acc = p.E_acc + BM;
+    p.dal_acc = grad ? p.F_acc + BM : nullptr;
+    p.Y = at<float>(ws, pl.off_Y);
+    p.Z = at<float>(ws, pl.off_Z);
+    p.W = at<float>(ws, pl.off_W);
+    p.dal_gemm = at<float>(ws, pl.off_dal_gemm);
+    p.C = pl.C;
+    p.Gc = pl.Gc;
+    p.nb_max = pl.nb_max;
+    p.ng_max = pl.ng_max;
+}
+
+int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {
+    Plan pl;
+    int rc = make_plan(p.N, p.M, p.B, p.grad, o, &pl);
+    if (rc) return rc;
+    if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < pl.total) return HAWKES_ERR_WORKSPACE;
+    bind(p, ws, pl, p.B, p.M, p.grad);
+    int nl = 0;
+    const int validate = o ? o->validate : 1;
+    cudaError_t err = hk::launch_prepare(p, s, validate, &nl);
+    if (err == cudaSuccess) err = hk::launch_scan(p, s, &nl);
+    if (err == cudaSuccess) {
+        if (pl.path == PATH_WALK) {
+            err = hk::launch_walk(p, s, &nl);
+            if (err == cudaSuccess) err = hk::launch_finalize(p, s, &nl);
+        } else {
+            err = hk::launch_gemm_path(p, s, &nl);
+        }
+    }
+    g_last_launches = nl;
+    if (err != cudaSuccess) {
+        fprintf(stderr, "hawkes_gb300: CUDA error %s\n", cudaGetErrorString(err));
+        return HAWKES_ERR_CUDA;
+    }
+    return HAWKES_OK;
+}
+
+bool bad_ptrs(std::initializer_list<const void*> ps) {
+    for (const void* q : ps)
+        if (!q) return true;
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+hawkes_opts hawkes_default_opts(void) {
+    hawkes_opts o;
+    o.beta_shared = 0;
+    o.chunk = 0;
+    o.validate = 1;
+    o.path = 0;
+    return o;
+}
+
+size_t hawkes_workspace_size(int64_t N, int32_t M, int32_t B, int32_t grad,
+                             const hawkes_opts* opts) {
+    Plan pl;
+    if (make_plan(N, M, B, grad ? 1 : 0, opts, &pl)) return 0;
+    return pl.total;
+}
+
+static hawkes_status single(const double* t, const int32_t* c, int64_t N, double T, int32_t M,
+                            const float* mu, const float* alpha, const float* beta,
+                            const hawkes_opts* opts, void* ws, size_t ws_bytes, double* out_ll,
+                            float* d_mu, float* d_alpha, float* d_beta, int grad, void* stream) {
+    if (N < 0 || M <= 0 || !(T >= 0.0)) return HAWKES_ERR_INVALID_ARG;
+    if (bad_ptrs({mu, alpha, beta, out_ll})) return HAWKES_ERR_INVALID_ARG;
+    if (N > 0 && bad_ptrs({t, c})) return HAWKES_ERR_INVALID_ARG;
+    if (grad && bad_ptrs({d_mu, d_alpha, d_beta})) return HAWKES_ERR_INVALID_ARG;
+    Plan pl;
+    int rc = make_plan(N, M, 1, grad, opts, &pl);
+    if (rc) return (hawkes_status)rc;
+    if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < pl.total) return HAWKES_ERR_WORKSPACE;
+    // single sequence: offsets {0, N} and T are written into the header's spare
+    // words by the first kernel, so the call issues no host-to-device copy
+    hk::WsHeader* hdr = (hk::WsHeader*)ws;
+    cudaStream_t s = (cudaStream_t)stream;
+    hk::Problem p{};
+    p.t = t; p.c = c; p.off = (const int64_t*)&hdr->pad[0]; p.Tarr = (const double*)&hdr->pad[2];
+    p.N = N; p.B = 1; p.M = M;
+    p.single = 1; p.T_single = T;
+    p.mu = mu; p.alpha = alpha; p.beta = beta;
+    p.shared = opts ? opts->beta_shared : 0;
+    p.grad = grad;
+    p.out_ll = out_ll; p.d_mu = d_mu; p.d_alpha = d_alpha; p.d_beta = d_beta;
+    return (hawkes_status)run(p, opts, ws, ws_bytes, s);
+}
+
+hawkes_status hawkes_loglik(const double* t, const int32_t* c, int64_t N, double T, int32_t M,
+                            const float* mu, const float* alpha, const float* beta,
+                            const hawkes_opts* opts, void* workspace, size_t workspace_bytes,
+                            double* out_ll, void* stream) {
+    return single(t, c, N, T, M, mu, alpha, beta, opts, workspace, workspace_bytes, out_ll,
+                  nullptr, nullptr, nullptr, 0, stream);
+}
+
+hawkes_status hawkes_loglik_grad(const double* t, const int32_t* c, int64_t N, double T,
+                                 int32_t M, const float* mu, const float* alpha,
+                                 const float* beta, const hawkes_opts* opts, void* workspace,
+                                 size_t workspace_bytes, double* out_ll, float* d_mu,
+                                 float* d_alpha, float* d_beta, void* stream) {
+    return single(t, c, N, T, M, mu, alpha, beta, opts, workspace, workspace_bytes, out_ll,
+                  d_mu, d_alpha, d_beta, 1, stream);
+}
+
+static hawkes_status varlen(const double* t, const int32_t* c, const int64_t* offsets,
+                            int32_t B, int64_t N, const double* T, int32_t M, const float* mu,
+                            const float* alpha, const float* beta, const hawkes_opts* opts,
+                            void* ws, size_t ws_bytes, double* out_ll, float* d_mu,
+                            float* d_alpha, float* d_beta, int grad, void* stream) {
+    if (N < 0 || M <= 0 || B <= 0) return HAWKES_ERR_INVALID_ARG;
+    if (bad_ptrs({offsets, T, mu, alpha, beta, out_ll})) return HAWKES_ERR_INVALID_ARG;
+    if (N > 0 && bad_ptrs({t, c})) return HAWKES_ERR_INVALID_ARG;
+    if (grad && bad_ptrs({d_mu, d_alpha, d_beta})) return HAWKES_ERR_INVALID_ARG;
+    hk::Problem p{};
+    p.t = t; p.c = c; p.off = offsets; p.Tarr = T;
+    p.N = N; p.B = B; p.M = M;
+    p.mu = mu; p.alpha = alpha; p.beta = beta;
+    p.shared = opts ? opts->beta_shared : 0;
+    p.grad = grad;
+    p.out_ll = out_ll; p.d_mu = d_mu; p.d_alpha = d_alpha; p.d_beta = d_beta;
+    return (hawkes_status)run(p, opts, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+hawkes_status hawkes_loglik_varlen(const double* t, const int32_t* c, const int64_t* offsets,
+                                   int32_t B, int64_t N, const double* T, int32_t M,
+                                   const float* mu, const float* alpha, const float* beta,
+                                   const hawkes_opts* opts, void* workspace,
+                                   size_t workspace_bytes, double* out_ll, void* stream) {
+    return varlen(t, c, offsets, B, N, T, M, mu, alpha, beta, opts, workspace, workspace_bytes,
+                  out_ll, nullptr, nullptr, nullptr, 0, stream);
+}
+
+hawkes_status hawkes_loglik_grad_varlen(const double* t, const int32_t* c,
+                                        const int64_t* offsets, int32_t B, int64_t N,
+                                        const double* T, int32_t M, const float* mu,
+                                        const float* alpha, const float* beta,
+                                        const hawkes_opts* opts, void* workspace,
+                                        size_t workspace_bytes, double* out_ll, float* d_mu,
+                                        float* d_alpha, float* d_beta, void* stream) {
+    return varlen(t, c, offsets, B, N, T, M, mu, alpha, beta, opts, workspace, workspace_bytes,
+                  out_ll, d_mu, d_alpha, d_beta, 1, stream);
+}
+
+// Host-buffer form: staging for inputs and outputs sits after the device workspace.
+static size_t host_staging_bytes(int64_t N, int32_t M, int shared) {
+    size_t b = align_up(sizeof(double) * (size_t)N) + align_up(sizeof(int32_t) * (size_t)N);
+    b += align_up(sizeof(float) * (size_t)M) * 2 + align_up(sizeof(float) * (size_t)M * M) * 2;
+    b += align_up(sizeof(float) * (size_t)(shared ? 1 : M)) * 2 + align_up(sizeof(double));
+    return b;
+}
+
+size_t hawkes_workspace_size_host(int64_t N, int32_t M, const hawkes_opts* opts) {
+    size_t dev = hawkes_workspace_size(N, M, 1, 1, opts);
+    if (!dev) return 0;
+    return align_up(dev) + host_staging_bytes(N, M, opts ? opts->beta_shared : 0);
+}
+
+hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t N, double T,
+                                      int32_t M, const float* mu, const float* alpha,
+                                      const float* beta, const hawkes_opts* opts,
+                                      void* workspace, size_t workspace_bytes, double* out_ll,
+                                      float* d_mu, float* d_alpha, float* d_beta,
+                                      void* stream) {
+    if (N < 0 || M <= 0) return HAWKES_ERR_INVALID_ARG;
+    if (bad_ptrs({mu, alpha, beta, out_ll, d_mu, d_alpha, d_beta})) return HAWKES_ERR_INVALID_ARG;
+    if (N > 0 && bad_ptrs({t, c})) return HAWKES_ERR_INVALID_ARG;
+    size_t dev = hawkes_workspace_size(N, M, 1, 1, opts);
+    if (!dev) return HAWKES_ERR_UNSUPPORTED;
+    if (!workspace || workspace_bytes < hawkes_workspace_size_host(N, M, opts))
+        return HAWKES_ERR_WORKSPACE;
+    const int shared = opts ? opts->beta_shared : 0;
+    const size_t nbeta = shared ? 1 : (size_t)M;
+    char* st = (char*)workspace + align_up(dev);
+    auto take = [&](size_t bytes) { char* q = st; st += align_up(bytes); return q; };
+    double* t_d = (double*)take(sizeof(double) * (size_t)N);
+    int32_t* c_d = (int32_t*)take(sizeof(int32_t) * (size_t)N);
+    float* mu_d = (float*)take(sizeof(float) * (size_t)M);
+    float* dmu_d = (float*)take(sizeof(float) * (size_t)M);
+    float* al_d = (float*)take(sizeof(float) * (size_t)M * M);
+    float* dal_d = (float*)take(sizeof(float) * (size_t)M * M);
+    float* be_d = (float*)take(sizeof(float) * nbeta);
+    float* dbe_d = (float*)take(sizeof(float) * nbeta);
+    double* ll_d = (double*)take(sizeof(double));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (N > 0) {
+        e = cudaMemcpyAsync(t_d, t, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c_d, c, sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mu_d, mu, sizeof(float) * M, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(al_d, alpha, sizeof(float) * (size_t)M * M, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(be_d, beta, sizeof(float) * nbeta, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return HAWKES_ERR_CUDA;
+    hawkes_status rc = hawkes_loglik_grad(t_d, c_d, N, T, M, mu_d, al_d, be_d, opts, workspace,
+                                          dev, ll_d, dmu_d, dal_d, dbe_d, stream);
+    if (rc != HAWKES_OK) return rc;
+    e = cudaMemcpyAsync(out_ll, ll_d, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mu, dmu_d, sizeof(float) * M, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_alpha, dal_d, sizeof(float) * (size_t)M * M, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_beta, dbe_d, sizeof(float) * nbeta, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return HAWKES_ERR_CUDA;
+    return hawkes_last_device_status(workspace, stream);
+}
+
+hawkes_status hawkes_last_device_status(void* workspace, void* stream) {
+    if (!workspace) return HAWKES_ERR_WORKSPACE;
+    int32_t st = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&st, workspace, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return HAWKES_ERR_CUDA;
+    return (hawkes_status)st;
+}
+
+const int64_t* hawkes_mark_counts(void* workspace) {
+    if (!workspace) return nullptr;
+    return (const int64_t*)((char*)workspace + align_up(sizeof(hk::WsHeader)));
+}
+
+const char* hawkes_status_str(hawkes_status s) {
+    switch (s) {
+        case HAWKES_OK: return "ok";
+        case HAWKES_ERR_INVALID_ARG: return "invalid argument";
+        case HAWKES_ERR_UNSORTED: return "event times not sorted";
+        case HAWKES_ERR_MARK_RANGE: return "mark outside [0, M)";
+        case HAWKES_ERR_TIME_RANGE: return "event time outside [0, T]";
+        case HAWKES_ERR_PARAM_DOMAIN: return "parameter outside its domain";
+        case HAWKES_ERR_NONPOS_INTENSITY: return "non-positive intensity";
+        case HAWKES_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case HAWKES_ERR_UNSUPPORTED: return "configuration not supported";
+        case HAWKES_ERR_CUDA: return "CUDA runtime error";
+    }
+    return "unknown status";
+}
+
+int32_t hawkes_last_launch_count(void) { return g_last_launches; }
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal definitions shared by the kernels of libhawkes_gb300 (not part of
+// the public C ABI, which is include/hawkes_gb300.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hawkes_gb300.h"
+
+#define HK_FULL 0xffffffffu
+
+namespace hk {
+
+// Workspace header: the first 256 bytes of every workspace.
+struct WsHeader {
+    int32_t status;      // device status word (0 = ok, else a hawkes_status)
+    int32_t validated;   // 1 if the last call ran the device checks
+    int64_t nb;          // number of chunks of the last call (device-computed)
+    int64_t pad[30];
+};
+static_assert(sizeof(WsHeader) == 256, "header must be 256 bytes");
+
+// Everything one launch sequence needs.  Pointers are device pointers.
+struct Problem {
+    // events
+    const double* t;
+    const int32_t* c;
+    const int64_t* off;      // [B+1]
+    const double* Tarr;      // [B]
+    int64_t N;
+    int32_t B;
+    int32_t M;
+    // parameters (per sequence when B > 1)
+    const float* mu;         // [B*M]
+    const float* alpha;      // [B*M*M]
+    const float* beta;       // [B] if shared else [B*M]
+    int32_t shared;
+    int32_t grad;
+    int32_t single;          // 1: one sequence; off/Tarr point at header words set by k_init
+    double T_single;
+    // chunking
+    int32_t C;               // events per chunk
+    int32_t Gc;              // chunks per scan group
+    int64_t nb_max;          // upper bound on the number of chunks
+    int64_t ng_max;          // upper bound on the number of groups
+    // workspace regions
+    WsHeader* hdr;
+    int64_t* counts;         // [B*M]
+    int64_t* chunk_base;     // [B+1]
+    int32_t* chunk_seq;      // [nb_max]
+    float* Shat;             // [nb_max*M] chunk-start states
+    float* Ghat;             // [nb_max*M] chunk-start G states (grad only)
+    float* grp_v;            // [ng_max*M]
+    float* grp_g;            // [ng_max*M]
+    double* grp_dt;          // [ng_max] time span of the composite after its last reset
+    int32_t* grp_reset;      // [ng_max]
+    float* carry_S;          // [ng_max*M]
+    float* carry_G;          // [ng_max*M]
+    double* ll_acc;          // [B]   sum of log lambda
+    double* dmu_acc;         // [B*M] sum of w over events of each mark
+    double* dal_acc;         // [B*M*M]
+    double* dbe_acc;         // [B*M] excitation part of dbeta
+    double* E_acc;           // [B*M] sum (1 - exp(-beta (T - t))) per source
+    double* F_acc;           // [B*M] sum (T - t) exp(-beta (T - t)) per source
+    // chunk-GEMM path
+    float* Y;                // [nb_max*M]  alpha . Shat_b
+    float* Z;                // [nb_max*M]  alpha . Ghat_b
+    float* W;                // [nb_max*M]  per-chunk weights of the dalpha GEMM
+    float* dal_gemm;         // [M*M]
+    // outputs
+    double* out_ll;          // [B]
+    float* d_mu;
+    float* d_alpha;
+    float* d_beta;
+};
+
+__device__ __forceinline__ void set_status(WsHeader* h, int code) {
+    atomicCAS(&h->status, 0, code);
+}
+
+__device__ __forceinline__ bool failed(const WsHeader* h) {
+    return *((volatile const int32_t*)&h->status) != 0;
+}
+
+__device__ __forceinline__ float beta_of(const Problem& p, int32_t seq, int32_t j) {
+    return p.shared ? p.beta[seq] : p.beta[(int64_t)seq * p.M + j];
+}
+
+// chunk b of sequence seq covers events [s0, s1)
+__device__ __forceinline__ void chunk_range(const Problem& p, int64_t b, int32_t seq,
+                                            int64_t& s0, int64_t& s1) {
+    int64_t q = b - p.chunk_base[seq];
+    s0 = p.off[seq] + q * p.C;
+    int64_t e = p.off[seq + 1];
+    s1 = s0 + p.C < e ? s0 + p.C : e;
+}
+
+__device__ __forceinline__ int64_t num_chunks(const Problem& p) { return p.chunk_base[p.B]; }
+
+}  // namespace hk
+
+// launch helpers implemented in the .cu files
+namespace hk {
+cudaError_t launch_prepare(const Problem& p, cudaStream_t s, int validate, int* nlaunch);
+cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_finalize(const Problem& p, cudaStream_t s, int* nlaunch);
+int walk_max_m(int grad);
+}  // namespace hk
