@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: events/s of the exact log-likelihood + gradient.
+
+Workload (default): M=1,024 marks, one shared decay beta=1, mu_i ~ (i+1)^-1.1
+summing to 50, dense alpha U[0,1] at spectral radius 0.7, N=10,000,000 events
+of a seeded cluster-process simulation (synthetic; no dataset).  One step is
+one hawkes_loglik_grad call over the whole stream: validation and mark counts,
+the inter-chunk scan, intensities, log-sum, compensator and all gradients.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  Inputs are resident in HBM before the timed
+region; L2 is flushed (a 512 MB write) between timed steps and the steps are
+timed with CUDA events on the launching stream.  ``e2e`` repeats the metric
+through the host-buffer entry point (pinned inputs copied in, L and gradients
+copied out, inside the timed region).  ``roofline`` reports the dominant
+kernel's achieved rate from per-kernel CUDA events (a separate instrumented
+pass over the same steps).  ``cpu_baseline`` times the FP64 oracle on a
+bounded prefix of the same stream on one host core.
+``--impl reference`` times the oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "events/s exact loglik+grad (M=1024,N=10M) vs plain FP64 scan; % roofline"
+WORKLOAD = ("hawkes_m1024_shared_n10m: M=1024, shared beta=1, mu_i ~ (i+1)^-1.1 (sum 50), "
+            "dense alpha U[0,1] at spectral radius 0.7, N=10,000,000 cluster-simulated "
+            "events, seed 3")
+CPU_SAMPLE_EVENTS = 1 << 19
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get(
+            "bf16_tflops_sustained", d["bf16_tflops"])), float(d.get("sm_max_mhz", 2070.0)), \
+            "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(n_events=None):
+    from paper_2604_01342_gb300 import synth
+    return synth.workload(4, n_events=n_events)
+
+
+def time_oracle(p, n_sample=CPU_SAMPLE_EVENTS):
+    """The FP64 oracle as it stands on one host core, on the first n_sample events."""
+    import oracle
+    n = min(n_sample, p.N)
+    t, c = p.t[:n], p.c[:n]
+    T = float(t[-1])
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)  # noqa: E731
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.loglik_grad(t, c, T, f32(p.mu), f32(p.alpha), np.full(p.M, f32(p.beta[:1])[0]))
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} events of the same stream (T = t of the last one), "
+                      f"FP64 log-likelihood + gradient, single thread, {dt:.2f} s"}
+
+
+# --------------------------------------------------------------------- reference
+def run_reference(args):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return
+    p = workload()
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; the first timed step includes nothing extra
+    times = []
+    per = None
+    for _ in range(args.steps):
+        per = time_oracle(p, CPU_SAMPLE_EVENTS // 4)
+        times.append(CPU_SAMPLE_EVENTS // 4 / per["value"])
+    n = CPU_SAMPLE_EVENTS // 4
+    value = n * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_events_per_step": n,
+                       "parallelism": "single host core"},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "sample": per["sample"]},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2604_01342_gb300 import binding as B
+
+    world, rank, local = dist_init()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workload()
+    N, M = p.N, p.M
+    opts = B.make_opts(True, args.chunk, True, 0)
+    t = torch.from_numpy(p.t).to(dev)
+    c = torch.from_numpy(p.c).to(dev)
+    mu = torch.tensor(p.mu, dtype=torch.float32, device=dev)
+    al = torch.tensor(p.alpha, dtype=torch.float32, device=dev)
+    be = torch.tensor(p.beta[:1], dtype=torch.float32, device=dev)
+    ws_bytes = B.hawkes_workspace_size(N, M, 1, True, opts)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    out_ll = torch.empty((), dtype=torch.float64, device=dev)
+    dmu = torch.empty(M, dtype=torch.float32, device=dev)
+    dal = torch.empty(M, M, dtype=torch.float32, device=dev)
+    dbe = torch.empty(1, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    def step():
+        B.hawkes_loglik_grad(t.data_ptr(), c.data_ptr(), N, p.T, M, mu.data_ptr(), al.data_ptr(),
+                             be.data_ptr(), opts, ws.data_ptr(), ws_bytes, out_ll.data_ptr(),
+                             dmu.data_ptr(), dal.data_ptr(), dbe.data_ptr(), sptr)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    rc = B.hawkes_last_device_status(ws.data_ptr(), sptr)
+    if rc:
+        raise B.HawkesError(rc, "device status after warm-up")
+    launches_per_step = B.hawkes_last_launch_count()
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * N / (ms * 1e-3)
+    ll_val = float(out_ll.item())
+
+    # ---- per-kernel timing (instrumented pass, same steps)
+    B.hawkes_profile_enable(True)
+    kern = {}
+    for i in range(args.steps):
+        flush.zero_()
+        step()
+        for name, kms in B.hawkes_profile_read():
+            kern.setdefault(name, []).append(kms)
+    B.hawkes_profile_enable(False)
+    kern_ms = {k: sum(v) / len(v) for k, v in kern.items()}
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if rank == 0 or True:
+        hb = B.hawkes_workspace_size_host(N, M, opts)
+        wsh = torch.empty(hb, dtype=torch.uint8, device=dev)
+        th = torch.from_numpy(p.t).pin_memory()
+        ch = torch.from_numpy(p.c).pin_memory()
+        muh = mu.cpu().pin_memory(); alh = al.cpu().pin_memory(); beh = be.cpu().pin_memory()
+        llh = torch.empty((), dtype=torch.float64).pin_memory()
+        dmuh = torch.empty(M, dtype=torch.float32).pin_memory()
+        dalh = torch.empty(M, M, dtype=torch.float32).pin_memory()
+        dbeh = torch.empty(1, dtype=torch.float32).pin_memory()
+
+        def host_step():
+            B.hawkes_loglik_grad_host(th.data_ptr(), ch.data_ptr(), N, p.T, M, muh.data_ptr(),
+                                      alh.data_ptr(), beh.data_ptr(), opts, wsh.data_ptr(), hb,
+                                      llh.data_ptr(), dmuh.data_ptr(), dalh.data_ptr(),
+                                      dbeh.data_ptr(), sptr)
+
+        for _ in range(2):
+            host_step()
+        e_ms = []
+        for i in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            host_step()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            e_ms.append(a.elapsed_time(b))
+        em = sum(e_ms) / len(e_ms)
+        if world > 1:
+            tt = torch.tensor([em], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            em = float(tt.item())
+        h2d = N * 8 + N * 4 + 4 * (M + M * M + 1)
+        d2h = 8 + 4 * (M + M * M + 1)
+        e2e = {"value": world * N / (em * 1e-3), "unit": "events/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": em}
+        del wsh
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    hbm, bf16, bf16_sus, sm_max, src = peaks()
+    roof = roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src)
+    cpu = time_oracle(p) if world == 1 else None
+    line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events": N, "M": M, "beta": "shared",
+                       "chunk": args.chunk or "default", "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "loglik": ll_val},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+            "roofline": roof, "cpu_baseline": cpu,
+            "kernels_ms": {k: round(v, 4) for k, v in kern_ms.items()}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
+    """Dominant kernel's achieved rate against its bound (units stated in the design doc)."""
+    if not kern_ms:
+        return None
+    name = max(kern_ms, key=kern_ms.get)
+    ms = kern_ms[name]
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12    # FMA = 2 flops
+    if name.startswith("gemm"):
+        C = args.chunk or 64
+        nb = (N + C - 1) // C
+        flops = 2.0 * M * M * nb
+        achieved = flops / (ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "peak_source": "FP32 CUDA-core peak from 152 SMs x 128 FMA/clk at max SM clock"}
+    if name in ("chunk_epilogue", "walk"):
+        C = args.chunk or 64
+        pairs = N * (C - 1) / 2.0
+        flops = 2.0 * (N * M) if name == "walk" else 2.0 * pairs * 2
+        achieved = flops / (ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "peak_source": "FP32 CUDA-core peak from 152 SMs x 128 FMA/clk at max SM clock"}
+    byts = 12.0 * N
+    achieved = byts / (ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -150,6 +150,15 @@ const char* hawkes_status_str(hawkes_status s);
 /* Number of kernel launches made by the last call on this thread (for accounting). */
 int32_t hawkes_last_launch_count(void);
 
+/* Per-kernel timing for measurement (no counterpart in the paper).  After
+ * hawkes_profile_enable(1), each call on this thread records a CUDA event on its stream
+ * after every kernel it launches.  hawkes_profile_read synchronises on the last event and
+ * writes up to `cap` (milliseconds, static kernel name) pairs of the most recent call, in
+ * launch order; it returns how many it wrote (negative hawkes_status on a CUDA error).
+ * Events are created once, at the first enable; nothing is allocated on the device. */
+int32_t hawkes_profile_enable(int32_t on);
+int32_t hawkes_profile_read(float* ms, const char** names, int32_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,8 @@ EXPORTED = (
     "hawkes_default_opts", "hawkes_workspace_size", "hawkes_loglik", "hawkes_loglik_grad",
     "hawkes_loglik_varlen", "hawkes_loglik_grad_varlen", "hawkes_workspace_size_host",
     "hawkes_loglik_grad_host", "hawkes_last_device_status", "hawkes_mark_counts",
-    "hawkes_status_str", "hawkes_last_launch_count",
+    "hawkes_status_str", "hawkes_last_launch_count", "hawkes_profile_enable",
+    "hawkes_profile_read",
 )
 
 
@@ -83,6 +84,11 @@ def lib():
         L.hawkes_status_str.restype = ctypes.c_char_p
         L.hawkes_last_launch_count.argtypes = []
         L.hawkes_last_launch_count.restype = i32
+        L.hawkes_profile_enable.argtypes = [i32]
+        L.hawkes_profile_enable.restype = i32
+        L.hawkes_profile_read.argtypes = [ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_char_p), i32]
+        L.hawkes_profile_read.restype = i32
         for name in ("hawkes_loglik", "hawkes_loglik_grad", "hawkes_loglik_varlen",
                      "hawkes_loglik_grad_varlen", "hawkes_loglik_grad_host",
                      "hawkes_last_device_status"):
@@ -163,3 +169,19 @@ def hawkes_mark_counts_ptr(ws) -> int:
 
 def hawkes_last_launch_count() -> int:
     return int(lib().hawkes_last_launch_count())
+
+
+def hawkes_profile_enable(on: bool) -> None:
+    rc = lib().hawkes_profile_enable(int(bool(on)))
+    if rc:
+        raise HawkesError(rc, "hawkes_profile_enable")
+
+
+def hawkes_profile_read(cap: int = 64):
+    """[(kernel name, milliseconds)] of the last call, in launch order."""
+    ms = (ctypes.c_float * cap)()
+    names = (ctypes.c_char_p * cap)()
+    n = lib().hawkes_profile_read(ms, names, cap)
+    if n < 0:
+        raise HawkesError(-n, "hawkes_profile_read")
+    return [(names[i].decode(), float(ms[i])) for i in range(n)]

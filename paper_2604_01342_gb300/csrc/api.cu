@@ -9,6 +9,17 @@ namespace {
 
 thread_local int32_t g_last_launches = 0;
 
+// per-kernel timing (off unless hawkes_profile_enable(1))
+constexpr int kProfMax = 64;
+struct Prof {
+    int on = 0;
+    int n = 0;
+    cudaEvent_t ev[kProfMax + 1];
+    const char* name[kProfMax];
+    bool created = false;
+};
+thread_local Prof g_prof;
+
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -119,6 +130,10 @@ int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStr
     bind(p, ws, pl, p.B, p.M, p.grad);
     int nl = 0;
     const int validate = o ? o->validate : 1;
+    if (g_prof.on) {
+        g_prof.n = 0;
+        cudaEventRecord(g_prof.ev[0], s);
+    }
     cudaError_t err = hk::launch_prepare(p, s, validate, &nl);
     if (err == cudaSuccess) err = hk::launch_scan(p, s, &nl);
     if (err == cudaSuccess) {
@@ -144,6 +159,15 @@ bool bad_ptrs(std::initializer_list<const void*> ps) {
 }
 
 }  // namespace
+
+namespace hk {
+void prof_mark(cudaStream_t s, const char* name) {
+    if (!g_prof.on || g_prof.n >= kProfMax) return;
+    g_prof.name[g_prof.n] = name;
+    cudaEventRecord(g_prof.ev[g_prof.n + 1], s);
+    ++g_prof.n;
+}
+}  // namespace hk
 
 extern "C" {
 
@@ -345,5 +369,29 @@ const char* hawkes_status_str(hawkes_status s) {
 }
 
 int32_t hawkes_last_launch_count(void) { return g_last_launches; }
+
+int32_t hawkes_profile_enable(int32_t on) {
+    if (on && !g_prof.created) {
+        for (int i = 0; i <= kProfMax; ++i)
+            if (cudaEventCreate(&g_prof.ev[i]) != cudaSuccess) return HAWKES_ERR_CUDA;
+        g_prof.created = true;
+    }
+    g_prof.on = on ? 1 : 0;
+    g_prof.n = 0;
+    return HAWKES_OK;
+}
+
+int32_t hawkes_profile_read(float* ms, const char** names, int32_t cap) {
+    if (!g_prof.created) return 0;
+    int n = g_prof.n < cap ? g_prof.n : cap;
+    if (n > 0 && cudaEventSynchronize(g_prof.ev[n]) != cudaSuccess) return -HAWKES_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]);
+        ms[i] = t;
+        names[i] = g_prof.name[i];
+    }
+    return n;
+}
 
 }  // extern "C"

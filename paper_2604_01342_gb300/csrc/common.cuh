@@ -106,4 +106,7 @@ cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_finalize(const Problem& p, cudaStream_t s, int* nlaunch);
 int walk_max_m(int grad);
+// Optional per-kernel timing: when enabled, records a CUDA event on the launch
+// stream after each kernel (names are static strings).
+void prof_mark(cudaStream_t s, const char* name);
 }  // namespace hk

@@ -68,6 +68,7 @@ __global__ void k_finalize(Problem p, int mode) {
 cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int* nl) {
     k_finalize<<<p.B, 256, 0, s>>>(p, mode);
     ++*nl;
+    prof_mark(s, "finalize");
     return cudaGetLastError();
 }
 

@@ -200,10 +200,12 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         g.Mdim = nb; g.Ndim = M; g.Kdim = M; g.atomic = 0;
         if ((err = sgemm(g, 1, p.hdr, s)) != cudaSuccess) return err;
         ++*nl;
+        prof_mark(s, "gemm_Y");
         if (p.grad) {
             g.A = p.Ghat; g.C = p.Z;
             if ((err = sgemm(g, 1, p.hdr, s)) != cudaSuccess) return err;
             ++*nl;
+            prof_mark(s, "gemm_Z");
         }
     }
     {
@@ -216,6 +218,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         int64_t grid = nb < 65535 * 16 ? nb : 65535 * 16;
         kern<<<(unsigned)(grid > 0 ? grid : 1), 256, smem, s>>>(p);
         ++*nl;
+        prof_mark(s, "chunk_epilogue");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (p.grad) {
@@ -230,6 +233,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         int splits = (int)((nb + 1023) / 1024);
         if ((err = sgemm(g, splits, p.hdr, s)) != cudaSuccess) return err;
         ++*nl;
+        prof_mark(s, "gemm_dalpha");
     }
     return launch_finalize_mode(p, s, 1, nl);
 }

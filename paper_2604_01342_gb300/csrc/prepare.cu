@@ -163,20 +163,25 @@ cudaError_t launch_prepare(const Problem& p, cudaStream_t s, int validate, int* 
                     (p.grad ? (int64_t)p.B * p.M * p.M : 0);
     k_init<<<256, 256, 0, s>>>(p, p.ll_acc, n_acc);
     ++*nl;
+    prof_mark(s, "init");
     if (validate) {
         cudaMemsetAsync(p.counts, 0, sizeof(int64_t) * (size_t)p.B * p.M, s);
         k_check_params<<<128, 256, 0, s>>>(p);
         ++*nl;
+        prof_mark(s, "check_params");
     }
     k_chunk_table<<<1, 1024, 0, s>>>(p);
+    prof_mark(s, "chunk_table");
     k_chunk_seq<<<p.B < 4096 ? p.B : 4096, 128, 0, s>>>(p);
     *nl += 2;
+    prof_mark(s, "chunk_seq");
     if (validate) {
         const int cpb = 16;
         int64_t blocks = (p.nb_max + cpb - 1) / cpb;
         if (blocks < 1) blocks = 1;
         k_validate_events<<<(unsigned)blocks, 256, 0, s>>>(p, cpb);
         ++*nl;
+        prof_mark(s, "validate_events");
     }
     return cudaGetLastError();
 }

@@ -150,12 +150,18 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
     unsigned cgrid = (unsigned)((p.M + 127) / 128);
     if (p.grad) {
         k_scan_group<0, true><<<grid, 256, smem, s>>>(p);
+        prof_mark(s, "scan_reduce");
         k_scan_carry<true><<<cgrid, 128, 0, s>>>(p);
+        prof_mark(s, "scan_carry");
         k_scan_group<1, true><<<grid, 256, smem, s>>>(p);
+        prof_mark(s, "scan_states");
     } else {
         k_scan_group<0, false><<<grid, 256, smem, s>>>(p);
+        prof_mark(s, "scan_reduce");
         k_scan_carry<false><<<cgrid, 128, 0, s>>>(p);
+        prof_mark(s, "scan_carry");
         k_scan_group<1, false><<<grid, 256, smem, s>>>(p);
+        prof_mark(s, "scan_states");
     }
     *nl += 3;
     return cudaGetLastError();

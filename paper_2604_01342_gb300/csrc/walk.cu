@@ -256,6 +256,7 @@ cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nl) {
     }
 #undef HK_WALK
     ++*nl;
+    prof_mark(s, "walk");
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
