@@ -135,6 +135,105 @@ def time_oracle(p, n_sample=CPU_SAMPLE_EVENTS):
                       f"FP64 log-likelihood + gradient, single thread, {dt:.2f} s"}
 
 
+# ------------------------------------------------------ plain FP64 scan (paper)
+def _next_pow2(n):
+    p = 1
+    while p < n:
+        p *= 2
+    return p
+
+
+def _blelloch_inclusive(s, v):
+    """Inclusive prefix products P_i = M_i ... M_1 of the compressed transitions
+    (s_i, v_i) with the paper's operator (Section 3):
+        (s_A, v_A) (.) (s_B, v_B) = (s_A s_B, s_A v_B + v_A),  A the later factor,
+    by the Blelloch up-sweep / down-sweep on a power-of-two padding (identity
+    elements (1, 0) at the end).  Plain FP64 tensor ops, one level at a time."""
+    import torch
+    n, m = v.shape
+    n2 = _next_pow2(max(n, 1))
+    S = torch.ones(n2, dtype=torch.float64, device=v.device)
+    V = torch.zeros(n2, m, dtype=torch.float64, device=v.device)
+    S[:n] = s
+    V[:n] = v
+    d = 1
+    while d < n2:                                     # up-sweep
+        r = torch.arange(2 * d - 1, n2, 2 * d, device=v.device)
+        lft = r - d
+        V[r] = S[r, None] * V[lft] + V[r]
+        S[r] = S[r] * S[lft]
+        d *= 2
+    S[n2 - 1] = 1.0
+    V[n2 - 1] = 0.0
+    d = n2 // 2
+    while d >= 1:                                     # down-sweep (exclusive)
+        r = torch.arange(2 * d - 1, n2, 2 * d, device=v.device)
+        lft = r - d
+        tS, tV = S[lft].clone(), V[lft].clone()
+        S[lft], V[lft] = S[r], V[r]
+        V[r] = tS[:, None] * V[r] + tV
+        S[r] = tS * S[r]
+        d //= 2
+    Si = s * S[:n]                                    # inclusive = M_i (.) exclusive
+    Vi = s[:, None] * V[:n] + v
+    return Si, Vi
+
+
+def fp64_scan_loglik(t, c, T, mu, alpha, gamma, batch=1 << 19):
+    """The paper's forward pass (Algorithm 1 / Algorithm 2) as plain FP64 PyTorch
+    ops, for comparison only: transitions (e^{-g dt_i}, e^{-g dt_i} alpha[:, m_{i-1}])
+    (Eq. define_augmented_M), a Blelloch scan per batch of 2^19 events, the batch
+    carry R_i = P_i R_carry (Section 3.3), lambda = mu + g R (Algorithm 1), and
+    the closed-form compensator.  Returns L as a float."""
+    import torch
+    t = t.to(torch.float64)
+    c = c.to(torch.int64)
+    mu = mu.to(torch.float64)
+    alpha = alpha.to(torch.float64)
+    n, m = t.shape[0], mu.shape[0]
+    R = torch.zeros(m, dtype=torch.float64, device=t.device)
+    logsum = torch.zeros((), dtype=torch.float64, device=t.device)
+    for b0 in range(0, n, batch):
+        b1 = min(n, b0 + batch)
+        tb = t[b0:b1]
+        prev_t = t[b0 - 1:b1 - 1] if b0 > 0 else torch.cat([tb[:1], tb[:-1]])
+        prev_c = c[b0 - 1:b1 - 1] if b0 > 0 else torch.cat([c[:1], c[b0:b1 - 1]])
+        s = torch.exp(-gamma * (tb - prev_t))
+        v = s[:, None] * alpha[:, prev_c].T
+        if b0 == 0:
+            s[0] = 1.0
+            v[0] = 0.0
+        Si, Vi = _blelloch_inclusive(s, v)
+        Rb = Si[:, None] * R[None, :] + Vi
+        cb = c[b0:b1]
+        lam = mu[cb] + gamma * Rb.gather(1, cb[:, None])[:, 0]
+        logsum = logsum + torch.log(lam).sum()
+        R = Rb[-1]
+    colsum = alpha.sum(0)
+    comp = T * mu.sum() + (colsum[c] * (-torch.expm1(-gamma * (T - t)))).sum()
+    return float((logsum - comp).item())
+
+
+def time_fp64_scan(p, dev, steps=1):
+    import torch
+    t = torch.from_numpy(p.t).to(dev)
+    c = torch.from_numpy(p.c).to(dev)
+    f32 = lambda a: torch.tensor(np.asarray(a, np.float32).astype(np.float64), device=dev)  # noqa
+    mu, al, g = f32(p.mu), f32(p.alpha), float(np.float32(p.beta[0]))
+    fp64_scan_loglik(t[:4096], c[:4096], float(p.t[4095]), mu, al, g)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        ll = fp64_scan_loglik(t, c, p.T, mu, al, g)
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    return {"value": p.N / (ms * 1e-3), "unit": "events/s", "ms_per_step": ms, "loglik": ll,
+            "kind": "paper's method as plain PyTorch FP64 ops on the same GPU: Blelloch scan "
+                    "over (s, v) pairs, batches of 2^19 events, forward only (no gradient)"}
+
+
 # --------------------------------------------------------------------- reference
 def run_reference(args):
     world, rank, _ = dist_init()
@@ -290,6 +389,7 @@ def run_ours(args):
     hbm, bf16, bf16_sus, sm_max, src = peaks()
     roof = roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src)
     cpu = time_oracle(p) if world == 1 else None
+    fp64 = time_fp64_scan(p, dev) if (world == 1 and not args.no_fp64_scan) else None
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -299,7 +399,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "loglik": ll_val},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "fp64_scan_baseline": fp64,
             "kernels_ms": {k: round(v, 4) for k, v in kern_ms.items()}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -344,6 +444,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-fp64-scan", action="store_true",
+                    help="skip the plain FP64 scan comparison leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
