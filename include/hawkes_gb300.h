@@ -136,6 +136,31 @@ hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t
                                       void* workspace, size_t workspace_bytes, double* out_ll,
                                       float* d_mu, float* d_alpha, float* d_beta, void* stream);
 
+/* hawkes_loglik_grad for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment convenience).  Some callers own no device allocator
+ * (a plain C host, a plug-in whose device memory belongs to another runtime) or must not
+ * make the blocking, device-synchronising cudaMalloc call; this entry point takes no
+ * workspace and allocates nothing.  It runs the same kernels as hawkes_loglik_grad on a
+ * fixed scratch array compiled into the library: hawkes_static_scratch_bytes() bytes
+ * (16 MiB) of device memory that every GPU loading the library holds until exit.
+ *   - Problems whose hawkes_workspace_size(N, M, 1, 1, opts) exceeds that size are
+ *     rejected with HAWKES_ERR_WORKSPACE before anything is launched.
+ *   - The first call on a device looks up the scratch address (cudaGetSymbolAddress)
+ *     with that device current and caches it; make that first call before any stream
+ *     capture.
+ *   - All calls share the one array: calls that overlap on the GPU (from several streams
+ *     or threads) race on it and must be serialised by the caller.  Each call writes or
+ *     zeroes everything it reads, so leftovers of an earlier call do not matter.
+ *   - Inputs and outputs are device pointers as in hawkes_loglik_grad; the device status
+ *     word is in the scratch array and is not readable through hawkes_last_device_status;
+ *     on a device-detected error the outputs are NaN. */
+size_t hawkes_static_scratch_bytes(void);
+hawkes_status hawkes_loglik_grad_static(const double* t, const int32_t* c, int64_t N, double T,
+                                        int32_t M, const float* mu, const float* alpha,
+                                        const float* beta, const hawkes_opts* opts,
+                                        double* out_ll, float* d_mu, float* d_alpha,
+                                        float* d_beta, void* stream);
+
 /* Synchronises `stream` and returns the device status word of the last call that used
  * `workspace` (HAWKES_OK if the device found nothing wrong). */
 hawkes_status hawkes_last_device_status(void* workspace, void* stream);

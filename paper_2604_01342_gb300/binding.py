@@ -30,7 +30,7 @@ EXPORTED = (
     "hawkes_loglik_varlen", "hawkes_loglik_grad_varlen", "hawkes_workspace_size_host",
     "hawkes_loglik_grad_host", "hawkes_last_device_status", "hawkes_mark_counts",
     "hawkes_status_str", "hawkes_last_launch_count", "hawkes_profile_enable",
-    "hawkes_profile_read",
+    "hawkes_profile_read", "hawkes_static_scratch_bytes", "hawkes_loglik_grad_static",
 )
 
 
@@ -89,7 +89,11 @@ def lib():
         L.hawkes_profile_read.argtypes = [ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_char_p), i32]
         L.hawkes_profile_read.restype = i32
-        for name in ("hawkes_loglik", "hawkes_loglik_grad", "hawkes_loglik_varlen",
+        L.hawkes_static_scratch_bytes.argtypes = []
+        L.hawkes_static_scratch_bytes.restype = sz
+        L.hawkes_loglik_grad_static.argtypes = [p, p, i64, d, i32, p, p, p, op, p, p, p, p, p]
+        for name in ("hawkes_loglik_grad_static", "hawkes_loglik", "hawkes_loglik_grad",
+                     "hawkes_loglik_varlen",
                      "hawkes_loglik_grad_varlen", "hawkes_loglik_grad_host",
                      "hawkes_last_device_status"):
             getattr(L, name).restype = ctypes.c_int
@@ -185,3 +189,15 @@ def hawkes_profile_read(cap: int = 64):
     if n < 0:
         raise HawkesError(-n, "hawkes_profile_read")
     return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def hawkes_static_scratch_bytes() -> int:
+    return int(lib().hawkes_static_scratch_bytes())
+
+
+def hawkes_loglik_grad_static(t, c, N, T, M, mu, alpha, beta, opts, out_ll, d_mu, d_alpha,
+                              d_beta, stream):
+    """hawkes_loglik_grad on the library's built-in scratch array (no workspace)."""
+    _check(lib().hawkes_loglik_grad_static(t, c, int(N), float(T), int(M), mu, alpha, beta,
+                                           ctypes.byref(opts), out_ll, d_mu, d_alpha, d_beta,
+                                           stream), "hawkes_loglik_grad_static")
