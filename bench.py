@@ -116,7 +116,7 @@ def dist_init():
 
 def workload(n_events=None):
     from paper_2604_01342_gb300 import synth
-    return synth.workload(4, n_events=n_events)
+    return synth.workload(4, n_events=n_events or None)
 
 
 def time_oracle(p, n_sample=CPU_SAMPLE_EVENTS):
@@ -273,7 +273,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = workload()
+    p = workload(args.events)
     N, M = p.N, p.M
     opts = B.make_opts(True, args.chunk, True, 0)
     t = torch.from_numpy(p.t).to(dev)
@@ -388,7 +388,8 @@ def run_ours(args):
 
     hbm, bf16, bf16_sus, sm_max, src = peaks()
     roof = roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src)
-    cpu = time_oracle(p) if world == 1 else None
+    path_roof = path_roofline(ms, N, M, hbm, clk)
+    cpu = time_oracle(p) if (world == 1 and not args.no_cpu) else None
     fp64 = time_fp64_scan(p, dev) if (world == 1 and not args.no_fp64_scan) else None
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
@@ -399,7 +400,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "loglik": ll_val},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
-            "roofline": roof, "cpu_baseline": cpu, "fp64_scan_baseline": fp64,
+            "roofline": roof, "path_roofline": path_roof, "cpu_baseline": cpu,
+            "fp64_scan_baseline": fp64,
             "kernels_ms": {k: round(v, 4) for k, v in kern_ms.items()}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -407,34 +409,82 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def kernel_work(name, N, M, C):
+    """(bound, algorithmic work per launch, unit) of each kernel of one step.
+
+    HBM kernels count the bytes the algorithm must move; tensor kernels the flops of
+    one product (the TF32 hi/lo split issues three); ALU kernels FP32 operations."""
+    nb = (N + C - 1) // C
+    pairs = N * (C - 1) / 2.0                  # pairs (k, l) inside chunks, l before k
+    table = {
+        "validate_events": ("hbm", 12.0 * N),
+        "scan_reduce": ("hbm", 12.0 * N),
+        "scan_states": ("hbm", 12.0 * N + 8.0 * M * nb),
+        "split_S": ("hbm", 4.0 * M * nb * 3),
+        "split_G": ("hbm", 4.0 * M * nb * 3),
+        "bucket": ("hbm", 12.0 * N + 16.0 * N),
+        "epilogue": ("hbm", 12.0 * N + 8.0 * N + 12.0 * N),
+        "transpose_W": ("hbm", 4.0 * M * nb * 3),
+        "transpose_S": ("hbm", 4.0 * M * nb * 3),
+        "gemm_Y": ("tensor", 2.0 * M * M * nb),
+        "gemm_Z": ("tensor", 2.0 * M * M * nb),
+        "gemm_dalpha": ("tensor", 2.0 * M * M * nb),
+        "pairs_fwd": ("alu", 5.0 * pairs),
+        "pairs_bwd": ("alu", 2.0 * pairs),
+        "walk": ("alu", 2.0 * 3.0 * N * M),
+    }
+    return table.get(name)
+
+
 def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
     """Dominant kernel's achieved rate against its bound (units stated in the design doc)."""
     if not kern_ms:
         return None
-    name = max(kern_ms, key=kern_ms.get)
-    ms = kern_ms[name]
+    C = args.chunk or 256
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12    # FMA = 2 flops
-    if name.startswith("gemm"):
-        C = args.chunk or 64
-        nb = (N + C - 1) // C
-        flops = 2.0 * M * M * nb
-        achieved = flops / (ms * 1e-3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
-                "peak_source": "FP32 CUDA-core peak from 152 SMs x 128 FMA/clk at max SM clock"}
-    if name in ("chunk_epilogue", "walk"):
-        C = args.chunk or 64
-        pairs = N * (C - 1) / 2.0
-        flops = 2.0 * (N * M) if name == "walk" else 2.0 * pairs * 2
-        achieved = flops / (ms * 1e-3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
-                "peak_source": "FP32 CUDA-core peak from 152 SMs x 128 FMA/clk at max SM clock"}
-    byts = 12.0 * N
-    achieved = byts / (ms * 1e-3) / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src}
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, FMA = 2 flops
+    tf32_peak = bf16 / 2.0                                # dense TF32 = BF16 / 2 (nominal ratio)
+    rows = {}
+    for name, ms in kern_ms.items():
+        w = kernel_work(name, N, M, C)
+        if w is None or ms <= 0:
+            continue
+        bound, work = w
+        if bound == "hbm":
+            ach, peak, unit = work / (ms * 1e-3) / 1e9, hbm, "GB/s"
+        elif bound == "tensor":
+            ach, peak, unit = work / (ms * 1e-3) / 1e12, tf32_peak, "TFLOP/s"
+        else:
+            ach, peak, unit = work / (ms * 1e-3) / 1e12, fp32_peak, "TFLOP/s"
+        rows[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                      "frac": ach / peak, "ms": ms}
+    name = max(kern_ms, key=kern_ms.get)
+    dom = rows.get(name)
+    if dom is None:
+        return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+    out = {"kernel": name, "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+           "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+           "peak_source": {"hbm": f"{src} HBM copy bandwidth",
+                           "tensor": f"{src} bf16 dense / 2 (TF32), burst",
+                           "alu": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}[dom["bound"]],
+           "per_kernel": {k: {"frac": round(v["frac"], 4), "ms": round(v["ms"], 4),
+                              "bound": v["bound"]} for k, v in rows.items()}}
+    if dom["bound"] == "tensor":
+        out["issued_frac"] = 3.0 * dom["frac"]
+    return out
+
+
+def path_roofline(ms_step, N, M, hbm, clk):
+    """The metric's roofline of the whole step: the slower of the event bytes at HBM peak
+    and 3 N M FMAs (intensity dot, dalpha row, dbeta dot) at the FP32 peak."""
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    t_hbm = 12.0 * N / (hbm * 1e9)
+    t_alu = 3.0 * N * M / (152 * 128 * sm_max * 1e6)
+    t_roof = max(t_hbm, t_alu)
+    return {"t_roof_ms": 1e3 * t_roof, "bound": "alu" if t_alu >= t_hbm else "hbm",
+            "frac": 1e3 * t_roof / ms_step,
+            "note": "3 N M FP32 FMA at 152 SMs x 128 lanes x max clock vs 12 B/event at HBM"}
 
 
 def main():
@@ -446,6 +496,9 @@ def main():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--no-fp64-scan", action="store_true",
                     help="skip the plain FP64 scan comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing leg")
+    ap.add_argument("--events", type=int, default=0,
+                    help="use only the first N events of the workload (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -70,6 +70,8 @@ def _load():
             lib.oracle_paper_grad_shared.argtypes = [i64, p, p, d, i32, p, p, d, p, p, p, p]
             lib.oracle_loglik_grad_varlen.argtypes = [p, p, p, i32, p, i32, p, p, p, p, p, p, p]
             lib.oracle_mark_counts.argtypes = [i64, p, i32, p]
+            lib.oracle_condition.argtypes = [i64, p, p, d, i32, p, p, p, p, p]
+            lib.oracle_condition.restype = ctypes.c_int
             for f in (lib.oracle_loglik_grad, lib.oracle_grad_adjoint, lib.oracle_paper_grad_shared,
                       lib.oracle_loglik_grad_varlen, lib.oracle_mark_counts):
                 f.restype = ctypes.c_int
@@ -173,3 +175,15 @@ def mark_counts(c, M):
     if rc:
         raise OracleError(rc)
     return out
+
+
+def condition(t, c, T, mu, alpha, beta):
+    """Sums of magnitudes of the terms of L and of each dL/dbeta_j (their conditioning
+    scales): {"ll": float, "dbeta": array[M]}."""
+    t, c, mu, alpha, beta, M = _prep(t, c, mu, alpha, beta)
+    sl, sb = np.zeros(1), np.zeros(M)
+    rc = _load().oracle_condition(t.shape[0], _ptr(t), _ptr(c), float(T), M, _ptr(mu),
+                                  _ptr(alpha), _ptr(beta), _ptr(sl), _ptr(sb))
+    if rc:
+        raise OracleError(rc)
+    return {"ll": float(sl[0]), "dbeta": sb}

@@ -334,3 +334,61 @@ int oracle_mark_counts(int64_t N, const int32_t* c, int32_t M, int64_t* counts)
     }
     return OR_OK;
 }
+
+/* Conditioning scales of the results (for stating errors of near-zero results):
+ *   scale_ll       = sum_k |log lambda_k| + Lambda(T)
+ *   scale_dbeta[j] = sum_k |w_k alpha[c_k][j] (S_{k,j} - beta_j G_{k,j})| + colsum_j F_j
+ * i.e. the sums of magnitudes of the terms whose difference is L or dL/dbeta_j.  A result
+ * that is much smaller than its scale is ill-conditioned: rounding of its terms, relative
+ * to the scale, is amplified by scale / |result|. */
+int oracle_condition(int64_t N, const double* t, const int32_t* c, double T, int32_t M,
+                     const double* mu, const double* alpha, const double* beta,
+                     double* scale_ll, double* scale_dbeta)
+{
+    int rc = check_inputs(N, t, c, T, M, mu, alpha, beta);
+    if (rc) return rc;
+    double* S = calloc((size_t)M, sizeof(double));
+    double* G = calloc((size_t)M, sizeof(double));
+    double* F = calloc((size_t)M, sizeof(double));
+    if (!S || !G || !F) { free(S); free(G); free(F); return OR_INVALID; }
+    memset(scale_dbeta, 0, sizeof(double) * (size_t)M);
+    double sabs = 0.0, logsum = 0.0, comp = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        if (k > 0) {
+            double dt = t[k] - t[k - 1];
+            int32_t prev = c[k - 1];
+            for (int32_t j = 0; j < M; ++j) {
+                double d = exp(-beta[j] * dt);
+                double P = S[j] + (j == prev ? 1.0 : 0.0);
+                G[j] = d * (G[j] + dt * P);
+                S[j] = d * P;
+            }
+        }
+        int32_t i = c[k];
+        const double* arow = alpha + (size_t)i * (size_t)M;
+        double lk = mu[i];
+        for (int32_t j = 0; j < M; ++j) lk += arow[j] * beta[j] * S[j];
+        if (!(lk > 0.0)) { rc = OR_NONPOS; break; }
+        sabs += fabs(log(lk));
+        logsum += log(lk);
+        double w = 1.0 / lk;
+        for (int32_t j = 0; j < M; ++j) scale_dbeta[j] += fabs(w * arow[j] * (S[j] - beta[j] * G[j]));
+        double x = beta[i] * (T - t[k]);
+        F[i] += (T - t[k]) * exp(-x);
+        double cs = 0.0;
+        for (int32_t r = 0; r < M; ++r) cs += alpha[(size_t)r * M + i];
+        comp += cs * (-expm1(-x));
+    }
+    if (rc == OR_OK) {
+        double summu = 0.0;
+        for (int32_t r = 0; r < M; ++r) summu += mu[r];
+        *scale_ll = sabs + T * summu + comp;
+        for (int32_t j = 0; j < M; ++j) {
+            double cs = 0.0;
+            for (int32_t r = 0; r < M; ++r) cs += alpha[(size_t)r * M + j];
+            scale_dbeta[j] += cs * F[j];
+        }
+    }
+    free(S); free(G); free(F);
+    return rc;
+}

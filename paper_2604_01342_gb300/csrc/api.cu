@@ -24,7 +24,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 constexpr int kDefaultChunkWalk = 128;
-constexpr int kDefaultChunkGemm = 64;
+constexpr int kDefaultChunkGemm = 256;
 
 enum Path { PATH_WALK = 1, PATH_GEMM = 2 };
 
@@ -35,7 +35,10 @@ struct Plan {
     int64_t nb_max, ng_max;
     size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
         off_grp_dt, off_grp_reset, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
-        off_dal_gemm, total;
+        off_dal_gemm, off_al_h, off_al_l, off_S_h, off_S_l, off_G_h, off_G_l, off_Wt_h, off_Wt_l,
+        off_St_h, off_St_l, off_recs, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf,
+        off_cen, off_wsum, off_colsum, off_at, total;
+    int64_t ldk, nbp;
 };
 
 // Returns 0 and fills the plan, or a hawkes_status.
@@ -51,6 +54,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
                                                                 : kDefaultChunkGemm);
     if (C < 1 || C > 4096) return HAWKES_ERR_INVALID_ARG;
     if (path == PATH_GEMM && C > 1024) return HAWKES_ERR_INVALID_ARG;
+    if (path == PATH_GEMM && M > 128 * 128) return HAWKES_ERR_UNSUPPORTED;
     pl->path = path;
     pl->C = C;
     pl->nb_max = (N + C - 1) / C + B;
@@ -76,13 +80,42 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->off_carry_G = grad ? take(sizeof(float) * ngM) : 0;
     size_t n_acc = (size_t)B * (1 + 4 * (size_t)M) + (grad ? (size_t)B * M * M : 0);
     pl->off_acc = take(sizeof(double) * n_acc);
+    pl->off_colsum = take(sizeof(double) * (size_t)B * M);
+    pl->ldk = ((int64_t)M + 3) / 4 * 4;
+    pl->nbp = (pl->nb_max + 3) / 4 * 4;
+    pl->off_Y = pl->off_Z = pl->off_W = pl->off_dal_gemm = 0;
+    pl->off_al_h = pl->off_al_l = pl->off_S_h = pl->off_S_l = pl->off_G_h = pl->off_G_l = 0;
+    pl->off_Wt_h = pl->off_Wt_l = pl->off_St_h = pl->off_St_l = 0;
+    pl->off_recs = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
+    pl->off_cen = pl->off_wsum = pl->off_at = 0;
     if (path == PATH_GEMM) {
+        const size_t h = sizeof(float);
+        const size_t P = ((size_t)M + 127) / 128;
+        pl->off_recs = take(16 * (size_t)(N > 0 ? N : 1));
+        pl->off_at = take(sizeof(float) * P * P * 128 * 128);
+        pl->off_bstart = take(sizeof(int32_t) * (size_t)pl->nb_max * (P + 1));
+        pl->off_wide = take((size_t)pl->nb_max);
+        pl->off_Aint = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
+        pl->off_Bint = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
+        if (grad) pl->off_wbuf = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
+        pl->off_cen = take(sizeof(float) * 4 * (size_t)M);
+        pl->off_wsum = take(sizeof(double) * (size_t)M);
         pl->off_Y = take(sizeof(float) * nbM);
-        pl->off_Z = grad ? take(sizeof(float) * nbM) : 0;
-        pl->off_W = grad ? take(sizeof(float) * nbM) : 0;
-        pl->off_dal_gemm = grad ? take(sizeof(float) * (size_t)M * M) : 0;
-    } else {
-        pl->off_Y = pl->off_Z = pl->off_W = pl->off_dal_gemm = 0;
+        pl->off_al_h = take(h * (size_t)M * pl->ldk);
+        pl->off_al_l = take(h * (size_t)M * pl->ldk);
+        pl->off_S_h = take(h * (size_t)pl->nb_max * pl->ldk);
+        pl->off_S_l = take(h * (size_t)pl->nb_max * pl->ldk);
+        if (grad) {
+            pl->off_Z = take(sizeof(float) * nbM);
+            pl->off_W = take(sizeof(float) * nbM);
+            pl->off_dal_gemm = take(sizeof(float) * (size_t)M * M);
+            pl->off_G_h = take(h * (size_t)pl->nb_max * pl->ldk);
+            pl->off_G_l = take(h * (size_t)pl->nb_max * pl->ldk);
+            pl->off_Wt_h = take(h * (size_t)M * pl->nbp);
+            pl->off_Wt_l = take(h * (size_t)M * pl->nbp);
+            pl->off_St_h = take(h * (size_t)M * pl->nbp);
+            pl->off_St_l = take(h * (size_t)M * pl->nbp);
+        }
     }
     pl->total = o_;
     return 0;
@@ -112,10 +145,35 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.E_acc = p.dbe_acc + BM;
     p.F_acc = p.E_acc + BM;
     p.dal_acc = grad ? p.F_acc + BM : nullptr;
+    p.colsum = at<double>(ws, pl.off_colsum);
     p.Y = at<float>(ws, pl.off_Y);
     p.Z = at<float>(ws, pl.off_Z);
     p.W = at<float>(ws, pl.off_W);
     p.dal_gemm = at<float>(ws, pl.off_dal_gemm);
+    p.al_h = at<float>(ws, pl.off_al_h);
+    p.al_l = at<float>(ws, pl.off_al_l);
+    p.S_h = at<float>(ws, pl.off_S_h);
+    p.S_l = at<float>(ws, pl.off_S_l);
+    p.G_h = at<float>(ws, pl.off_G_h);
+    p.G_l = at<float>(ws, pl.off_G_l);
+    p.Wt_h = at<float>(ws, pl.off_Wt_h);
+    p.Wt_l = at<float>(ws, pl.off_Wt_l);
+    p.St_h = at<float>(ws, pl.off_St_h);
+    p.St_l = at<float>(ws, pl.off_St_l);
+    p.recs = at<float4>(ws, pl.off_recs);
+    p.at = at<float>(ws, pl.off_at);
+    p.bstart = at<int32_t>(ws, pl.off_bstart);
+    p.wide = at<uint8_t>(ws, pl.off_wide);
+    p.Aint = at<float>(ws, pl.off_Aint);
+    p.Bint = at<float>(ws, pl.off_Bint);
+    p.wbuf = at<float>(ws, pl.off_wbuf);
+    p.cen_S = at<float>(ws, pl.off_cen);
+    p.cen_G = p.cen_S ? p.cen_S + M : nullptr;
+    p.bias_Y = p.cen_S ? p.cen_S + 2 * M : nullptr;
+    p.bias_Z = p.cen_S ? p.cen_S + 3 * M : nullptr;
+    p.wsum_acc = at<double>(ws, pl.off_wsum);
+    p.ldk = pl.ldk;
+    p.nbp = pl.nbp;
     p.C = pl.C;
     p.Gc = pl.Gc;
     p.nb_max = pl.nb_max;
@@ -130,6 +188,7 @@ int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStr
     bind(p, ws, pl, p.B, p.M, p.grad);
     int nl = 0;
     const int validate = o ? o->validate : 1;
+    p.validated = validate ? 1 : 0;
     if (g_prof.on) {
         g_prof.n = 0;
         cudaEventRecord(g_prof.ev[0], s);

@@ -36,6 +36,7 @@ struct Problem {
     int32_t shared;
     int32_t grad;
     int32_t single;          // 1: one sequence; off/Tarr point at header words set by k_init
+    int32_t validated;       // 1: the device checks (and mark counts) run in this call
     double T_single;
     // chunking
     int32_t C;               // events per chunk
@@ -61,11 +62,35 @@ struct Problem {
     double* dbe_acc;         // [B*M] excitation part of dbeta
     double* E_acc;           // [B*M] sum (1 - exp(-beta (T - t))) per source
     double* F_acc;           // [B*M] sum (T - t) exp(-beta (T - t)) per source
+    double* colsum;          // [B*M] sum_i alpha[s][i][j]
     // chunk-GEMM path
     float* Y;                // [nb_max*M]  alpha . Shat_b
     float* Z;                // [nb_max*M]  alpha . Ghat_b
     float* W;                // [nb_max*M]  per-chunk weights of the dalpha GEMM
     float* dal_gemm;         // [M*M]
+    // tf32 hi/lo operands of the tensor-core GEMMs (fp32 containers)
+    float *al_h, *al_l;      // [M][ldk]       alpha
+    float *S_h, *S_l;        // [nb_max][ldk]  chunk-start states
+    float *G_h, *G_l;        // [nb_max][ldk]
+    float *Wt_h, *Wt_l;      // [M][nbp]       W transposed (chunks contiguous)
+    float *St_h, *St_l;      // [M][nbp]       S^ transposed
+    // intra-chunk pair kernels
+    float4* recs;            // [N]  events bucketed by mark block inside each chunk
+    float* at;               // [P*P*128*128] alpha in tile-major order
+    int32_t* bstart;         // [nb_max * (P+1)] bucket offsets inside each chunk
+    uint8_t* wide;           // [nb_max] chunk spans too wide for the factorised weights
+    float* Aint;             // [N]  sum_{l<k in chunk} P_kl alpha[c_k][c_l]
+    float* Bint;             // [N]  same, weighted by (t_k - t_l)
+    float* wbuf;             // [N]  w_k = 1 / lambda_k
+    // centering of the GEMM operands (the tensor-core accumulation error is one-signed
+    // for same-signed operands; centred operands make it unbiased)
+    float* cen_S;            // [M] m_j = n_j / (beta T): stationary mean of S_j
+    float* cen_G;            // [M] m_j / beta:           stationary mean of G_j
+    float* bias_Y;           // [M] alpha . cen_S  (FP64-accumulated)
+    float* bias_Z;           // [M] alpha . cen_G
+    double* wsum_acc;        // [M] sum_b W[b][i]
+    int64_t ldk;             // M rounded up to 4
+    int64_t nbp;             // nb_max rounded up to 4
     // outputs
     double* out_ll;          // [B]
     float* d_mu;
@@ -95,6 +120,23 @@ __device__ __forceinline__ void chunk_range(const Problem& p, int64_t b, int32_t
 }
 
 __device__ __forceinline__ int64_t num_chunks(const Problem& p) { return p.chunk_base[p.B]; }
+
+// Sum of log lambda without per-event log rounding: each thread keeps the product of its
+// lambdas as an FP64 mantissa in [0.5, 1) and an integer binary exponent, and takes one
+// FP64 log when the product is folded into a sum.
+struct LogProd {
+    double m = 1.0;
+    int e = 0;
+    __device__ __forceinline__ void mul(float x) {
+        m *= (double)x;
+        int k;
+        m = frexp(m, &k);
+        e += k;
+    }
+    __device__ __forceinline__ double log_value() const {
+        return log(m) + (double)e * 0.69314718055994530942;
+    }
+};
 
 }  // namespace hk
 

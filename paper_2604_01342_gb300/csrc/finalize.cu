@@ -12,26 +12,40 @@
 
 namespace hk {
 
-// mode 0: X = dal_acc (already carries beta_j);
-// mode 1: X = beta * (dal_gemm + dal_acc)  (chunk-GEMM path, one shared beta)
-__global__ void k_finalize(Problem p, int mode) {
+// Column sums colsum[s][j] = sum_i alpha[s][i][j] in FP64: block (32 columns x 8 row groups).
+__global__ void k_colsum(Problem p, double* colsum) {
+    __shared__ double part[8][33];
+    const int M = p.M, s = blockIdx.y;
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const float* alpha = p.alpha + (int64_t)s * M * M;
+    double acc = 0.0;
+    if (j < M)
+        for (int i = threadIdx.y; i < M; i += 8) acc += (double)alpha[(int64_t)i * M + j];
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < M) {
+        double t = 0.0;
+        for (int r = 0; r < 8; ++r) t += part[r][threadIdx.x];
+        colsum[(int64_t)s * M + j] = t;
+    }
+}
+
+// Per-sequence scalars and vectors: L, dmu, dbeta.  One block per sequence.
+__global__ void k_finalize_vec(Problem p, const double* colsum) {
     const int s = blockIdx.x;
     const int M = p.M;
     const bool bad = failed(p.hdr);
     const double nanv = __longlong_as_double(0x7ff8000000000000ll);
-    const float* alpha = p.alpha + (int64_t)s * M * M;
     const float* mu = p.mu + (int64_t)s * M;
     const double T = p.Tarr[s];
     __shared__ double red_comp[32], red_mu[32], red_be[32];
     double comp = 0.0, summu = 0.0, dbsum = 0.0;
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        double cs = 0.0;
-        for (int i = 0; i < M; ++i) cs += (double)alpha[(int64_t)i * M + j];
-        const double E = p.E_acc[(int64_t)s * M + j];
-        comp += cs * E;
+        const double cs = colsum[(int64_t)s * M + j];
+        comp += cs * p.E_acc[(int64_t)s * M + j];
         summu += (double)mu[j];
         if (p.grad) {
-            double db = p.dbe_acc[(int64_t)s * M + j] - cs * p.F_acc[(int64_t)s * M + j];
+            const double db = p.dbe_acc[(int64_t)s * M + j] - cs * p.F_acc[(int64_t)s * M + j];
             if (p.shared) dbsum += db;
             else p.d_beta[(int64_t)s * M + j] = bad ? (float)nanv : (float)db;
             p.d_mu[(int64_t)s * M + j] =
@@ -52,22 +66,45 @@ __global__ void k_finalize(Problem p, int mode) {
         p.out_ll[s] = bad ? nanv : p.ll_acc[s] - T * m - c;
         if (p.grad && p.shared) p.d_beta[s] = bad ? (float)nanv : (float)b;
     }
-    if (p.grad) {
-        const float beta = p.shared ? p.beta[s] : 0.f;
-        for (int64_t e = threadIdx.x; e < (int64_t)M * M; e += blockDim.x) {
-            const int j = (int)(e % M);
-            double x;
-            if (mode == 0) x = p.dal_acc[(int64_t)s * M * M + e];
-            else x = (double)beta * ((double)p.dal_gemm[e] + p.dal_acc[e]);
-            const double v = x - p.E_acc[(int64_t)s * M + j];
-            p.d_alpha[(int64_t)s * M * M + e] = bad ? (float)nanv : (float)v;
+}
+
+// dalpha for all sequences, elementwise.
+// mode 0: X = dal_acc (already carries beta_j);
+// mode 1: X = beta * (dal_gemm + m_j wsum_i + dal_acc)  (chunk-GEMM path, one shared beta;
+//         the GEMM ran on S^ - m, so m_j sum_b W[b][i] restores the centre)
+__global__ void k_finalize_alpha(Problem p, int mode) {
+    const int M = p.M;
+    const bool bad = failed(p.hdr);
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+    const int64_t total = (int64_t)p.B * M * M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / ((int64_t)M * M), ij = e % ((int64_t)M * M);
+        const int j = (int)(ij % M);
+        double x;
+        if (mode == 0) {
+            x = p.dal_acc[e];
+        } else {
+            const float beta = p.beta[0];
+            x = (double)beta * ((double)p.dal_gemm[ij] +
+                                (double)p.cen_S[j] * p.wsum_acc[ij / M] + p.dal_acc[ij]);
         }
+        const double v = x - p.E_acc[s * M + j];
+        p.d_alpha[e] = bad ? (float)nanv : (float)v;
     }
 }
 
 cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int* nl) {
-    k_finalize<<<p.B, 256, 0, s>>>(p, mode);
-    ++*nl;
+    k_colsum<<<dim3((unsigned)((p.M + 31) / 32), (unsigned)p.B), dim3(32, 8), 0, s>>>(p, p.colsum);
+    k_finalize_vec<<<p.B, 256, 0, s>>>(p, p.colsum);
+    *nl += 2;
+    if (p.grad) {
+        int64_t total = (int64_t)p.B * p.M * p.M;
+        int64_t blocks = (total + 255) / 256;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        k_finalize_alpha<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, mode);
+        ++*nl;
+    }
     prof_mark(s, "finalize");
     return cudaGetLastError();
 }

@@ -21,217 +21,484 @@ namespace hk {
 
 cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int* nl);
 
-// ---------------------------------------------------------------------------
-// FP32 CUDA-core GEMM  C[m][n] (+)= sum_k A(m, k) B(n, k) with general strides.
-// 64 x 64 tile, 256 threads, 4 x 4 outputs per thread, k-step 16.
-// ---------------------------------------------------------------------------
-struct GemmArgs {
-    const float* A; int64_t a_m, a_k;   // A(m,k) = A[m*a_m + k*a_k]
-    const float* B; int64_t b_n, b_k;   // B(n,k) = B[n*b_n + k*b_k]
-    float* C; int64_t c_m, c_n;         // C(m,n) = C[m*c_m + n*c_n]
-    int64_t Mdim, Ndim, Kdim;
-    int64_t k_per_split;                // split-K slice length (atomic accumulate if split)
-    const int64_t* kdim_dev;            // if set, K is clipped to *kdim_dev (device count)
-    int atomic;
-};
+// Tensor-core GEMM and tf32 hi/lo splitting (tc_gemm.cu).
+cudaError_t tc_gemm_tf32x3(const float* Ah, const float* Al, int64_t lda, const float* Bh,
+                           const float* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
+                           int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
+                           cudaStream_t s, const float* bias);
+cudaError_t split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd,
+                       int64_t rows, int64_t cols, cudaStream_t s, const float* centre);
+cudaError_t transpose_split_tf32(const float* src, int64_t cols, const int64_t* rows_valid,
+                                 int64_t rows_pad, float* hi, float* lo, int64_t ldd,
+                                 cudaStream_t s, const float* centre);
 
-__global__ void __launch_bounds__(256) k_sgemm(GemmArgs g, const WsHeader* hdr) {
-    __shared__ float As[16][64 + 1];
-    __shared__ float Bs[16][64 + 1];
-    if (failed(hdr)) return;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
-    const int64_t k_begin = (int64_t)blockIdx.z * g.k_per_split;
-    int64_t k_end = k_begin + g.k_per_split;
-    int64_t kdim = g.Kdim;
-    if (g.kdim_dev && *g.kdim_dev < kdim) kdim = *g.kdim_dev;
-    if (k_end > kdim) k_end = kdim;
-    float acc[4][4] = {};
-    for (int64_t k0 = k_begin; k0 < k_end; k0 += 16) {
-        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
-            int kk = i & 15, mm = i >> 4;
-            int64_t gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < g.Mdim && gk < k_end) ? g.A[gm * g.a_m + gk * g.a_k] : 0.f;
-            int64_t gn = n0 + mm;
-            Bs[kk][mm] = (gn < g.Ndim && gk < k_end) ? g.B[gn * g.b_n + gk * g.b_k] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int64_t gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
-            if (gm < g.Mdim && gn < g.Ndim) {
-                float* dst = g.C + gm * g.c_m + gn * g.c_n;
-                if (g.atomic) atomicAdd(dst, acc[i][j]);
-                else *dst = acc[i][j];
-            }
-        }
-}
-
-static cudaError_t sgemm(const GemmArgs& g0, int splits, const WsHeader* hdr, cudaStream_t s) {
-    GemmArgs g = g0;
-    if (splits < 1) splits = 1;
-    g.k_per_split = ((g.Kdim + splits - 1) / splits + 15) / 16 * 16;
-    if (g.k_per_split < 16) g.k_per_split = 16;
-    splits = (int)((g.Kdim + g.k_per_split - 1) / g.k_per_split);
-    if (splits < 1) splits = 1;
-    g.atomic = splits > 1 ? 1 : g.atomic;
-    dim3 grid((unsigned)((g.Ndim + 63) / 64), (unsigned)((g.Mdim + 63) / 64), (unsigned)splits);
-    k_sgemm<<<grid, 256, 0, s>>>(g, hdr);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Per-chunk epilogue: intra-chunk pairs, lambda, log, weights, gradient pieces.
-// One block per chunk; the chunk's events are staged in shared memory.
-// ---------------------------------------------------------------------------
-template <bool GRAD>
-__global__ void __launch_bounds__(256) k_chunk_epilogue(Problem p) {
-    extern __shared__ unsigned char smraw[];
+// Centres of the GEMM operands: the stationary means m_j = n_j / (beta T) of S_j and
+// m_j / beta of G_j (n_j = events of mark j), and the exact products alpha . m in FP64.
+// One warp per row of alpha.
+__global__ void k_centres(Problem p, int have_counts) {
     const int M = p.M;
-    const int C = p.C;
-    double* tsh = (double*)smraw;                // [C]
-    int32_t* csh = (int32_t*)(tsh + C);          // [C]
-    float* wsh = (float*)(csh + C);              // [C]  w_k
-    float* Wrow = wsh + C;                       // [M]  W[b][:]
-    __shared__ double red_ll[8];
-    __shared__ float red_db[8];
-    if (failed(p.hdr)) return;
-    const int64_t nb = num_chunks(p);
     const float beta = p.beta[0];
     const double T = p.Tarr[0];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    auto centre = [&](int j) -> double {
+        return (have_counts && T > 0.0) ? (double)p.counts[j] / ((double)beta * T) : 0.0;
+    };
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < M; j += blockDim.x) {
+            const double m = centre(j);
+            p.cen_S[j] = (float)m;
+            p.cen_G[j] = (float)(m / beta);
+        }
+    for (int i = warp; i < M; i += nwarps) {
+        double y = 0.0, z = 0.0;
+        for (int j = lane; j < M; j += 32) {
+            const double a = (double)p.alpha[(int64_t)i * M + j];
+            const double m = (double)(float)centre(j);
+            y += a * m;
+            z += a * (double)(float)(centre(j) / beta);
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            y += __shfl_xor_sync(HK_FULL, y, o);
+            z += __shfl_xor_sync(HK_FULL, z, o);
+        }
+        if (lane == 0) {
+            p.bias_Y[i] = (float)y;
+            p.bias_Z[i] = (float)z;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Intra-chunk pairs through shared-memory tiles of alpha.
+//
+// The pairs (k, l) of one chunk with l before k need alpha[c_k][c_l].  Gathering
+// those from L2 costs a 32-byte sector per pair, so instead the marks are dealt
+// round-robin into P = ceil(M / 128) blocks (block of mark c = c mod P, position
+// c / P; dealing spreads the few very frequent marks of a skewed mark distribution
+// over all blocks), alpha is copied once into tile-major order, and every chunk's
+// events are bucketed by block (k_bucket).  The forward kernel takes work items
+// (row block I, range of chunks) from a global counter and, for each column block J,
+// keeps tile (I, J) of alpha in shared memory while pairing the chunk's bucket-I
+// events (one per lane) with its bucket-J events.  The backward kernel owns one
+// tile (I, J) of dalpha in shared memory per block of threads.
+// Pair weights are exp(-beta (t_k - t_l)) = em_k * ep_l with em = exp(-beta delta),
+// ep = exp(+beta delta), delta = t - tau_b; a chunk whose span would overflow ep is
+// flagged "wide" and uses one exp per pair instead.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 128;
+constexpr int kTileLd = kTile + 1;      // padded row stride against bank conflicts
+constexpr float kWideLimit = 80.f;      // beta * span above which exp(+beta delta) may overflow
+constexpr int kFwdChunksPerItem = 64;
+
+__device__ __forceinline__ int rec_idx(float4 r) { return __float_as_int(r.w) >> 16; }
+__device__ __forceinline__ int rec_pos(float4 r) { return __float_as_int(r.w) & 0xffff; }
+
+// alpha in tile-major order: at[((I * P + J) * 128 + r) * 128 + q] = alpha[I + P r][J + P q]
+// (zero outside the matrix).
+__global__ void k_alpha_tiles(Problem p, float* at) {
+    const int M = p.M, P = (M + kTile - 1) / kTile;
+    const int64_t total = (int64_t)P * P * kTile * kTile;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e % kTile), r = (int)((e / kTile) % kTile);
+        const int tile = (int)(e / ((int64_t)kTile * kTile));
+        const int I = tile / P, J = tile % P;
+        const int i = I + P * r, j = J + P * q;
+        at[e] = (i < M && j < M) ? p.alpha[(int64_t)i * M + j] : 0.f;
+    }
+}
+
+// One block per chunk: bucket the chunk's events by mark block (unordered inside a
+// bucket: pairs compare the in-chunk index explicitly).
+__global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t* bstart,
+                                                uint8_t* wide) {
+    extern __shared__ int32_t cnt[];      // [P] counters, then [P+1] bases
+    if (failed(p.hdr)) return;
+    const int P = (p.M + kTile - 1) / kTile;
+    int32_t* base = cnt + P;
+    const float beta = p.beta[0];
+    const int64_t nb = num_chunks(p);
     for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
         int64_t s0, s1;
         chunk_range(p, b, 0, s0, s1);
         const int n = (int)(s1 - s0);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            tsh[i] = p.t[s0 + i];
-            csh[i] = p.c[s0 + i];
-        }
-        if (GRAD)
-            for (int j = threadIdx.x; j < M; j += blockDim.x) Wrow[j] = 0.f;
+        const double tau = p.t[s0];
+        for (int q = threadIdx.x; q < P; q += blockDim.x) cnt[q] = 0;
         __syncthreads();
-        const double tau = tsh[0];
-        double ll = 0.0;
-        float db = 0.f;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const double tk = tsh[i];
-            const int ck = csh[i];
-            const float* arow = p.alpha + (int64_t)ck * M;
-            float A = 0.f, Bp = 0.f;
-            for (int l = 0; l < i; ++l) {
-                const float x = (float)(tk - tsh[l]);
-                const float e = expf(-beta * x) * __ldg(arow + csh[l]);
-                A += e;
-                if (GRAD) Bp += x * e;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[p.c[s0 + i] % P], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int q = 0; q < P; ++q) {
+                base[q] = acc;
+                bstart[b * (P + 1) + q] = acc;
+                acc += cnt[q];
+                cnt[q] = 0;
             }
+            base[P] = acc;
+            bstart[b * (P + 1) + P] = acc;
+        }
+        __syncthreads();
+        const bool isw = beta * (float)(p.t[s1 - 1] - tau) > kWideLimit;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int ck = p.c[s0 + i];
+            const float d = (float)(p.t[s0 + i] - tau);
+            const float em = expf(-beta * d);
+            const float ep = isw ? 0.f : expf(beta * d);
+            const int q = ck % P;
+            const int pos = base[q] + atomicAdd(&cnt[q], 1);
+            recs[s0 + pos] = make_float4(d, em, ep, __int_as_float((i << 16) | (ck / P)));
+        }
+        if (threadIdx.x == 0) wide[b] = isw ? 1 : 0;
+        __syncthreads();
+    }
+}
+
+// Forward pairs: for every event k,
+//   A_k = sum_{l<k in chunk} P_kl alpha[c_k][c_l],  B_k = sum (t_k - t_l) P_kl alpha[c_k][c_l].
+__global__ void __launch_bounds__(256) k_pairs_fwd(Problem p, const float4* __restrict__ recs,
+                                                   const int32_t* __restrict__ bstart,
+                                                   const uint8_t* __restrict__ wide,
+                                                   const float* __restrict__ at, float* Aout,
+                                                   float* Bout, int* counter) {
+    extern __shared__ float tile[];       // [kTile][kTileLd]
+    __shared__ int item_sh;
+    if (failed(p.hdr)) return;
+    const int M = p.M, P = (M + kTile - 1) / kTile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int nb = (int)num_chunks(p);
+    const int nranges = (nb + kFwdChunksPerItem - 1) / kFwdChunksPerItem;
+    const int nitems = nranges * P;
+    const float beta = p.beta[0];
+    const int C = p.C;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_sh;
+        if (item >= nitems) break;
+        const int I = item % P, range = item / P;
+        const int b0 = range * kFwdChunksPerItem;
+        const int b1 = min(b0 + kFwdChunksPerItem, nb);
+        for (int J = 0; J < P; ++J) {
+            __syncthreads();
+            const float* src = at + (int64_t)(I * P + J) * kTile * kTile;
+            for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x)
+                tile[(e >> 7) * kTileLd + (e & 127)] = src[e];
+            __syncthreads();
+            for (int b = b0 + warp; b < b1; b += nwarps) {
+                const int64_t s0 = (int64_t)b * C;
+                const int32_t* bs = bstart + (int64_t)b * (P + 1);
+                const int k0 = bs[I], k1 = bs[I + 1];
+                const int l0 = bs[J], nJ = bs[J + 1] - l0;
+                const float4* lrec = recs + s0 + l0;
+                const bool isw = wide[b] != 0;
+                for (int kb = k0; kb < k1; kb += 32) {
+                    const int kk = kb + lane;
+                    const bool have = kk < k1;
+                    const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int ik = have ? rec_idx(rk) : -1;
+                    const float* trow = tile + rec_pos(rk) * kTileLd;
+                    float a = 0.f, bb = 0.f;
+                    if (!isw) {
+#pragma unroll 4
+                        for (int l = 0; l < nJ; ++l) {
+                            const float4 rl = __ldg(lrec + l);
+                            const int key = __float_as_int(rl.w);
+                            float v = rk.y * rl.z * trow[key & 0xffff];
+                            v = (key >> 16) < ik ? v : 0.f;
+                            a += v;
+                            bb = fmaf(rk.x - rl.x, v, bb);
+                        }
+                    } else {
+                        for (int l = 0; l < nJ; ++l) {
+                            const float4 rl = __ldg(lrec + l);
+                            const int key = __float_as_int(rl.w);
+                            if ((key >> 16) < ik) {
+                                const float dt = rk.x - rl.x;
+                                const float v = expf(-beta * dt) * trow[key & 0xffff];
+                                a += v;
+                                bb = fmaf(dt, v, bb);
+                            }
+                        }
+                    }
+                    if (have) {
+                        const int64_t k = s0 + ik;
+                        if (J == 0) { Aout[k] = a; Bout[k] = bb; }
+                        else { Aout[k] += a; Bout[k] += bb; }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Backward pairs: dalpha_intra[c_k][c_l] += w_k P_kl over the pairs of tile (I, J).
+__global__ void __launch_bounds__(256) k_pairs_bwd(Problem p, const float4* __restrict__ recs,
+                                                   const int32_t* __restrict__ bstart,
+                                                   const uint8_t* __restrict__ wide,
+                                                   const float* __restrict__ wbuf,
+                                                   int chunks_per_cta) {
+    extern __shared__ float dtile[];      // [kTile][kTileLd]
+    if (failed(p.hdr)) return;
+    const int M = p.M, P = (M + kTile - 1) / kTile;
+    const int I = blockIdx.x / P, J = blockIdx.x % P;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int nb = (int)num_chunks(p);
+    const int b0 = blockIdx.y * chunks_per_cta;
+    const int b1 = min(b0 + chunks_per_cta, nb);
+    if (b0 >= b1) return;
+    const float beta = p.beta[0];
+    const int C = p.C;
+    for (int e = threadIdx.x; e < kTile * kTileLd; e += blockDim.x) dtile[e] = 0.f;
+    __syncthreads();
+    for (int b = b0 + warp; b < b1; b += nwarps) {
+        const int64_t s0 = (int64_t)b * C;
+        const int32_t* bs = bstart + (int64_t)b * (P + 1);
+        const int k0 = bs[I], k1 = bs[I + 1];
+        const int l0 = bs[J], nJ = bs[J + 1] - l0;
+        if (k0 == k1 || nJ == 0) continue;
+        const float4* lrec = recs + s0 + l0;
+        const bool isw = wide[b] != 0;
+        for (int kb = k0; kb < k1; kb += 32) {
+            const int kk = kb + lane;
+            const bool have = kk < k1;
+            const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int ik = have ? rec_idx(rk) : -1;
+            const float uk = have ? wbuf[s0 + ik] * rk.y : 0.f;
+            float* drow = dtile + rec_pos(rk) * kTileLd;
+            if (!isw) {
+#pragma unroll 4
+                for (int l = 0; l < nJ; ++l) {
+                    const float4 rl = __ldg(lrec + l);
+                    const int key = __float_as_int(rl.w);
+                    if ((key >> 16) < ik) atomicAdd(drow + (key & 0xffff), uk * rl.z);
+                }
+            } else {
+                const float wk = have ? wbuf[s0 + ik] : 0.f;
+                for (int l = 0; l < nJ; ++l) {
+                    const float4 rl = __ldg(lrec + l);
+                    const int key = __float_as_int(rl.w);
+                    if ((key >> 16) < ik)
+                        atomicAdd(drow + (key & 0xffff), wk * expf(-beta * (rk.x - rl.x)));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = e >> 7, q = e & 127;
+        const float v = dtile[r * kTileLd + q];
+        const int i = I + P * r, j = J + P * q;
+        if (v != 0.f && i < M && j < M) atomicAdd(&p.dal_acc[(int64_t)i * M + j], (double)v);
+    }
+}
+
+// Per-event epilogue: lambda, log, w, the W rows of the dalpha GEMM, the dbeta sum and
+// per-mark sums (dmu, compensator E and F) in shared-memory histograms flushed once per
+// block.  Blocks take contiguous ranges of chunks.
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_epilogue(Problem p, const float* Aint, const float* Bint,
+                                                  float* wbuf, int64_t chunks_per_cta) {
+    extern __shared__ float sh[];
+    const int M = p.M;
+    float* Wrow = sh;            // [M]
+    float* hE = Wrow + M;        // [M]
+    float* hF = hE + M;          // [M]
+    float* hmu = hF + M;         // [M]
+    float* hws = hmu + M;        // [M] sum over this block's chunks of W[b][:]
+    __shared__ double red_ll[8];
+    __shared__ double red_db[8];
+    if (failed(p.hdr)) return;
+    const int64_t nb = num_chunks(p);
+    const int64_t b0 = (int64_t)blockIdx.x * chunks_per_cta;
+    const int64_t b1 = b0 + chunks_per_cta < nb ? b0 + chunks_per_cta : nb;
+    if (b0 >= b1) return;
+    const float beta = p.beta[0];
+    const double T = p.Tarr[0];
+    for (int j = threadIdx.x; j < 5 * M; j += blockDim.x) sh[j] = 0.f;
+    __syncthreads();
+    LogProd lp;
+    double db = 0.0;
+    for (int64_t b = b0; b < b1; ++b) {
+        int64_t s0, s1;
+        chunk_range(p, b, 0, s0, s1);
+        const double tau = p.t[s0];
+        for (int64_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+            const double tk = p.t[k];
+            const int ck = p.c[k];
             const float delta = (float)(tk - tau);
             const float ek = expf(-beta * delta);
             const float y = p.Y[b * M + ck];
-            const float aS = ek * y + A;
+            const float aS = ek * y + Aint[k];
             const float lam = p.mu[ck] + beta * aS;
             if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
-            ll += (double)logf(lam);
-            const float w = 1.f / lam;
+            lp.mul(lam);
             const float xT = (float)(T - tk);
-            atomicAdd(&p.E_acc[ck], (double)(-expm1f(-beta * xT)));
+            atomicAdd(&hE[ck], -expm1f(-beta * xT));
             if (GRAD) {
+                const float w = 1.f / lam;
                 const float z = p.Z[b * M + ck];
-                const float aG = ek * (delta * y + z) + Bp;
-                db += w * (aS - beta * aG);
-                wsh[i] = w;
+                const float aG = ek * (delta * y + z) + Bint[k];
+                db += (double)(w * (aS - beta * aG));
+                wbuf[k] = w;
                 atomicAdd(&Wrow[ck], w * ek);
-                atomicAdd(&p.dmu_acc[ck], (double)w);
-                atomicAdd(&p.F_acc[ck], (double)(xT * expf(-beta * xT)));
+                atomicAdd(&hmu[ck], w);
+                atomicAdd(&hF[ck], xT * expf(-beta * xT));
             }
-        }
-        // block reductions
-        for (int o = 16; o >= 1; o >>= 1) {
-            ll += __shfl_xor_sync(HK_FULL, ll, o);
-            db += __shfl_xor_sync(HK_FULL, db, o);
-        }
-        if ((threadIdx.x & 31) == 0) { red_ll[threadIdx.x >> 5] = ll; red_db[threadIdx.x >> 5] = db; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0.0, d = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red_ll[w]; d += red_db[w]; }
-            atomicAdd(&p.ll_acc[0], a);
-            if (GRAD) atomicAdd(&p.dbe_acc[0], d);
         }
         if (GRAD) {
-            // intra-chunk pairs of dalpha (without the factor beta)
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const double tk = tsh[i];
-                const float w = wsh[i];
-                double* drow = p.dal_acc + (int64_t)csh[i] * M;
-                for (int l = 0; l < i; ++l) {
-                    const float x = (float)(tk - tsh[l]);
-                    atomicAdd(drow + csh[l], (double)(w * expf(-beta * x)));
-                }
+            __syncthreads();
+            for (int j = threadIdx.x; j < M; j += blockDim.x) {
+                p.W[b * M + j] = Wrow[j];
+                hws[j] += Wrow[j];
+                Wrow[j] = 0.f;
             }
-            for (int j = threadIdx.x; j < M; j += blockDim.x) p.W[b * M + j] = Wrow[j];
+            __syncthreads();
         }
-        __syncthreads();
+    }
+    double ll = lp.log_value();
+    for (int o = 16; o >= 1; o >>= 1) {
+        ll += __shfl_xor_sync(HK_FULL, ll, o);
+        db += __shfl_xor_sync(HK_FULL, db, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red_ll[threadIdx.x >> 5] = ll; red_db[threadIdx.x >> 5] = db; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, d = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red_ll[w]; d += red_db[w]; }
+        atomicAdd(&p.ll_acc[0], a);
+        if (GRAD) atomicAdd(&p.dbe_acc[0], d);
+    }
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        if (hE[j] != 0.f) atomicAdd(&p.E_acc[j], (double)hE[j]);
+        if (GRAD) {
+            if (hF[j] != 0.f) atomicAdd(&p.F_acc[j], (double)hF[j]);
+            if (hmu[j] != 0.f) atomicAdd(&p.dmu_acc[j], (double)hmu[j]);
+            if (hws[j] != 0.f) atomicAdd(&p.wsum_acc[j], (double)hws[j]);
+        }
     }
 }
 
 cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     cudaError_t err;
     const int64_t M = p.M, nb = p.nb_max;
-    // Y = Shat alpha^T, Z = Ghat alpha^T   (rows = chunks)
-    {
-        GemmArgs g{};
-        g.A = p.Shat; g.a_m = M; g.a_k = 1;
-        g.B = p.alpha; g.b_n = M; g.b_k = 1;
-        g.C = p.Y; g.c_m = M; g.c_n = 1;
-        g.Mdim = nb; g.Ndim = M; g.Kdim = M; g.atomic = 0;
-        if ((err = sgemm(g, 1, p.hdr, s)) != cudaSuccess) return err;
+    // Y = S^ alpha^T and Z = G^ alpha^T on the tensor cores (rows = chunks)
+    // mark counts exist only when the inputs were validated; without them the centre is 0
+    cudaMemsetAsync(p.wsum_acc, 0, sizeof(double) * (size_t)M, s);
+    k_centres<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(p, p.validated);
+    ++*nl;
+    prof_mark(s, "centres");
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = split_tf32(p.alpha, M, p.al_h, p.al_l, p.ldk, M, M, s, nullptr)) != cudaSuccess)
+        return err;
+    ++*nl;
+    prof_mark(s, "split_alpha");
+    if ((err = split_tf32(p.Shat, M, p.S_h, p.S_l, p.ldk, nb, M, s, p.cen_S)) != cudaSuccess)
+        return err;
+    ++*nl;
+    prof_mark(s, "split_S");
+    if ((err = tc_gemm_tf32x3(p.S_h, p.S_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Y,
+                              M, (int)nb, (int)M, M, 1, false, p.hdr, s, p.bias_Y)) != cudaSuccess)
+        return err;
+    ++*nl;
+    prof_mark(s, "gemm_Y");
+    if (p.grad) {
+        if ((err = split_tf32(p.Ghat, M, p.G_h, p.G_l, p.ldk, nb, M, s, p.cen_G)) != cudaSuccess)
+            return err;
         ++*nl;
-        prof_mark(s, "gemm_Y");
-        if (p.grad) {
-            g.A = p.Ghat; g.C = p.Z;
-            if ((err = sgemm(g, 1, p.hdr, s)) != cudaSuccess) return err;
-            ++*nl;
-            prof_mark(s, "gemm_Z");
-        }
+        prof_mark(s, "split_G");
+        if ((err = tc_gemm_tf32x3(p.G_h, p.G_l, p.ldk, p.al_h, p.al_l, p.ldk,
+                                  p.Z, M, (int)nb, (int)M, M, 1, false, p.hdr, s, p.bias_Z)) !=
+            cudaSuccess)
+            return err;
+        ++*nl;
+        prof_mark(s, "gemm_Z");
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int P = (int)((M + kTile - 1) / kTile);
+    {
+        // alpha in tile-major order, and the events of every chunk bucketed by mark block
+        int64_t total = (int64_t)P * P * kTile * kTile;
+        int64_t blocks = (total + 255) / 256;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        k_alpha_tiles<<<(unsigned)blocks, 256, 0, s>>>(p, p.at);
+        ++*nl;
+        size_t smem = sizeof(int32_t) * (2 * (size_t)P + 1);
+        int64_t grid = nb < (int64_t)sms * 16 ? nb : (int64_t)sms * 16;
+        k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 256, smem, s>>>(p, p.recs, p.bstart, p.wide);
+        ++*nl;
+        prof_mark(s, "bucket");
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     {
-        size_t smem = (size_t)p.C * (8 + 4 + 4) + sizeof(float) * (size_t)M;
-        auto kern = p.grad ? k_chunk_epilogue<true> : k_chunk_epilogue<false>;
+        // forward pairs: work items (row block, 64 chunks) from a counter in the header
+        const size_t smem = sizeof(float) * kTile * kTileLd;
+        err = cudaFuncSetAttribute(k_pairs_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        k_pairs_fwd<<<(unsigned)(sms * 3), 256, smem, s>>>(p, p.recs, p.bstart, p.wide, p.at,
+                                                           p.Aint, p.Bint,
+                                                           (int*)&p.hdr->pad[8]);
+        ++*nl;
+        prof_mark(s, "pairs_fwd");
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    {
+        const size_t smem = sizeof(float) * 5 * (size_t)M;
+        auto kern = p.grad ? k_epilogue<true> : k_epilogue<false>;
         if (smem > 48 * 1024) {
             err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (err != cudaSuccess) return err;
         }
-        int64_t grid = nb < 65535 * 16 ? nb : 65535 * 16;
-        kern<<<(unsigned)(grid > 0 ? grid : 1), 256, smem, s>>>(p);
+        int64_t blocks = (int64_t)sms * 4;
+        int64_t per = (nb + blocks - 1) / blocks;
+        if (per < 1) per = 1;
+        blocks = (nb + per - 1) / per;
+        kern<<<(unsigned)(blocks > 0 ? blocks : 1), 256, smem, s>>>(p, p.Aint, p.Bint, p.wbuf, per);
         ++*nl;
-        prof_mark(s, "chunk_epilogue");
+        prof_mark(s, "epilogue");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (p.grad) {
-        // dal_gemm[i][j] = sum_b W[b][i] Shat[b][j]   (split over chunks, atomic accumulate)
+        // backward pairs: tile (I, J) x chunk range
+        const size_t smem = sizeof(float) * kTile * kTileLd;
+        err = cudaFuncSetAttribute(k_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        int64_t R = ((int64_t)sms * 3 + P * P - 1) / (P * P);
+        int64_t per = (nb + R - 1) / R;
+        if (per < 1) per = 1;
+        R = (nb + per - 1) / per;
+        if (R < 1) R = 1;
+        k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), 256, smem, s>>>(p, p.recs, p.bstart,
+                                                                         p.wide, p.wbuf, (int)per);
+        ++*nl;
+        prof_mark(s, "pairs_bwd");
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    if (p.grad) {
+        // dalpha_gemm[i][j] = sum_b W[b][i] S^[b][j]: both operands transposed so that
+        // the chunk index is the contiguous K dimension; rows past the chunk count are 0
+        const int64_t* nb_dev = p.chunk_base + p.B;
+        if ((err = transpose_split_tf32(p.W, M, nb_dev, p.nbp, p.Wt_h, p.Wt_l, p.nbp, s, nullptr)) !=
+            cudaSuccess)
+            return err;
+        ++*nl;
+        prof_mark(s, "transpose_W");
+        if ((err = transpose_split_tf32(p.Shat, M, nb_dev, p.nbp, p.St_h, p.St_l, p.nbp, s,
+                                        p.cen_S)) != cudaSuccess)
+            return err;
+        ++*nl;
+        prof_mark(s, "transpose_S");
         cudaMemsetAsync(p.dal_gemm, 0, sizeof(float) * (size_t)M * M, s);
-        GemmArgs g{};
-        g.A = p.W; g.a_m = 1; g.a_k = M;
-        g.B = p.Shat; g.b_n = 1; g.b_k = M;
-        g.C = p.dal_gemm; g.c_m = M; g.c_n = 1;
-        g.Mdim = M; g.Ndim = M; g.Kdim = nb; g.atomic = 1;
-        g.kdim_dev = p.chunk_base + p.B;
-        int splits = (int)((nb + 1023) / 1024);
-        if ((err = sgemm(g, splits, p.hdr, s)) != cudaSuccess) return err;
+        const int tiles = (int)(((M + 127) / 128) * ((M + 255) / 256));
+        int splits = (2 * 152 + tiles - 1) / tiles;
+        if ((err = tc_gemm_tf32x3(p.Wt_h, p.Wt_l, p.nbp, p.St_h, p.St_l, p.nbp,
+                                  p.dal_gemm, M, (int)M, (int)M, p.nbp, splits, true, p.hdr, s,
+                                  nullptr)) != cudaSuccess)
+            return err;
         ++*nl;
         prof_mark(s, "gemm_dalpha");
     }

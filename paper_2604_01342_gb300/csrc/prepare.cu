@@ -18,6 +18,7 @@ __global__ void k_init(Problem p, double* acc, int64_t n_acc) {
         p.hdr->status = 0;
         p.hdr->validated = 0;
         p.hdr->nb = 0;
+        p.hdr->pad[8] = 0;   // work counter of the forward pair kernel
         if (p.single) {
             p.hdr->pad[0] = 0;
             p.hdr->pad[1] = p.N;

@@ -1,24 +1,27 @@
 // Tensor-core GEMM for sm_103a:  D[m][n] (+)= sum_k A[m][k] B[n][k]
-// with FP32-class accuracy from BF16 operands split in two:
-//     A = Ah + Al,  B = Bh + Bl  (Ah = bf16(A), Al = bf16(A - Ah))
-//     A B^T ~= Ah Bh^T + Ah Bl^T + Al Bh^T        (the Al Bl^T term is ~2^-18 relative)
-// All three products accumulate into one FP32 accumulator in tensor memory.
+// with FP32-class accuracy from TF32 operands split in two:
+//     A = Ah + Al,  B = Bh + Bl  (Ah = tf32(A), Al = tf32(A - Ah), both rounded to nearest)
+//     A B^T ~= Ah Bh^T + Ah Bl^T + Al Bh^T        (the Al Bl^T term is ~2^-22 relative)
+// All three products accumulate into one FP32 accumulator in tensor memory.  (A bf16
+// split would run twice as fast but leaves ~1e-5 relative error per product, too much
+// for the shared-decay gradient, which is a small difference of large sums.)
 //
 // Used for the two dense contractions of the chunk-GEMM path: alpha . S^_b over
 // all chunk-start states, and the dalpha contraction W^T S^ over all chunks.
 //
 // One CTA computes one 128 x 256 output tile over a slice of K (split-K with
-// atomic accumulation when there is more than one slice).  Thread 0 issues the TMA
-// loads (cp.async.bulk.tensor, 128-byte swizzle, 64 bf16 of K per row) into a
-// two-stage ring and the tcgen05.mma instructions (kind::f16, bf16 in, f32
-// accumulate, M=128, N=256, K=16); tcgen05.commit arrives on the stage's "empty"
-// mbarrier when the MMAs that read it are done.  All four warps then read the
-// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows) and
-// store it.  Every mbarrier wait is bounded; on timeout the kernel records an
+// atomic accumulation when there is more than one slice).  One thread issues the TMA
+// loads (cp.async.bulk.tensor, 128-byte swizzle, 32 fp32 of K per row) into a
+// two-stage ring and the tcgen05.mma instructions (kind::tf32, f32 accumulate,
+// M=128, N=256, K=8); tcgen05.commit arrives on the stage's "empty"
+// mbarrier when the MMAs that read it are done.  The tensor-core accumulator
+// loses precision with the number of accumulation steps (measured: ~1.6e-6 after 64
+// of K, ~2.6e-5 after 1024), so every 64 of K is accumulated into one of two TMEM
+// banks and then promoted: eight warps read the finished bank with tcgen05.ld and
+// add it to FP32 registers while the MMAs fill the other bank.  Every mbarrier wait is bounded; on timeout the kernel records an
 // error in the status word, waits (bounded) for its MMAs, frees its tensor memory
 // and returns.
 #include <cuda.h>
-#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
@@ -30,13 +33,13 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BN = 256;
-constexpr int BK = 64;                  // bf16 elements = 128 bytes = one swizzle row
+constexpr int BK = 32;                  // fp32 elements = 128 bytes = one swizzle row
 constexpr int STAGES = 2;
-constexpr int A_TILE = BM * BK * 2;     // 16 KB
-constexpr int B_TILE = BN * BK * 2;     // 32 KB
+constexpr int A_TILE = BM * BK * 4;     // 16 KB
+constexpr int B_TILE = BN * BK * 4;     // 32 KB
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // Ah, Al, Bh, Bl
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 512;      // two accumulator banks of BN columns
 constexpr uint32_t kSpinLimit = 1u << 26;   // bounded waits (~ seconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -92,17 +95,17 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* tile) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: f32 accumulate, bf16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+// Instruction descriptor, kind::tf32: f32 accumulate, tf32 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
@@ -134,14 +137,24 @@ struct Maps {
     CUtensorMap ah, al, bh, bl;
 };
 
-__global__ void __launch_bounds__(128, 1)
-k_gemm_bf16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim, int Ndim,
-              int k_tiles_total, int k_tiles_per_split, int atomic_out, WsHeader* hdr) {
+// Threads: warps 0-7 read and promote the accumulator (warp w owns TMEM lanes
+// 32 (w % 4) .. +31 = rows, and columns (w / 4) * 128 .. +127); warp 8 allocates the
+// tensor memory and one of its threads issues the TMA loads and the MMAs.
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (kEpiWarps + 1) * 32;
+constexpr int kGroupTiles = 2;          // k-tiles accumulated in TMEM before promotion
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim, int Ndim,
+              int k_tiles_total, int k_tiles_per_split, int atomic_out, const float* bias,
+              WsHeader* hdr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
+    uint64_t* bank_full = empty + STAGES;     // [2] accumulator bank holds a finished group
+    uint64_t* bank_empty = bank_full + 2;     // [2] bank has been read by all epilogue warps
+    uint64_t* done = bank_empty + 2;          // every MMA of this block has completed
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -151,17 +164,22 @@ k_gemm_bf16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
     int kt1 = kt0 + k_tiles_per_split;
     if (kt1 > k_tiles_total) kt1 = k_tiles_total;
     const int KT = kt1 > kt0 ? kt1 - kt0 : 0;
+    const int ngroups = (KT + kGroupTiles - 1) / kGroupTiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&bank_full[q], 1);
+            mbar_init(&bank_empty[q], kEpiWarps);
+        }
         mbar_init(done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == kEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(TMEM_COLS));
@@ -172,87 +190,120 @@ k_gemm_bf16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (threadIdx.x == 0 && KT > 0) {
-        const uint32_t idesc = idesc_bf16(BM, BN);
-        auto load_stage = [&](int s, int kt) {
-            uint8_t* st = smem + s * STAGE_BYTES;
-            mbar_expect_tx(&full[s], STAGE_BYTES);
-            const int kx = kt * BK;
-            tma_load_2d(st, &maps.ah, &full[s], kx, m0);
-            tma_load_2d(st + A_TILE, &maps.al, &full[s], kx, m0);
-            tma_load_2d(st + 2 * A_TILE, &maps.bh, &full[s], kx, n0);
-            tma_load_2d(st + 2 * A_TILE + B_TILE, &maps.bl, &full[s], kx, n0);
-        };
-        // per stage: index of the k-tile whose load is in flight and not yet consumed
-        int inflight[STAGES];
-        for (int s2 = 0; s2 < STAGES; ++s2) inflight[s2] = -1;
-        for (int i = 0; i < STAGES && i < KT; ++i) { load_stage(i, kt0 + i); inflight[i] = i; }
-        bool ok = true;
-        for (int i = 0; i < KT && ok; ++i) {
-            const int s = i % STAGES;
-            if (!mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1))) { ok = false; break; }
-            inflight[s] = -1;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint8_t* st = smem + s * STAGE_BYTES;
-            const uint64_t dah = sw128_desc(st), dal = sw128_desc(st + A_TILE);
-            const uint64_t dbh = sw128_desc(st + 2 * A_TILE);
-            const uint64_t dbl = sw128_desc(st + 2 * A_TILE + B_TILE);
+    if (warp == kEpiWarps) {
+        if (lane == 0 && KT > 0) {
+            const uint32_t idesc = idesc_tf32(BM, BN);
+            auto load_stage = [&](int s, int kt) {
+                uint8_t* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                const int kx = kt * BK;
+                tma_load_2d(st, &maps.ah, &full[s], kx, m0);
+                tma_load_2d(st + A_TILE, &maps.al, &full[s], kx, m0);
+                tma_load_2d(st + 2 * A_TILE, &maps.bh, &full[s], kx, n0);
+                tma_load_2d(st + 2 * A_TILE + B_TILE, &maps.bl, &full[s], kx, n0);
+            };
+            int inflight[STAGES];
+            for (int s2 = 0; s2 < STAGES; ++s2) inflight[s2] = -1;
+            for (int i = 0; i < STAGES && i < KT; ++i) { load_stage(i, kt0 + i); inflight[i] = i; }
+            bool ok = true;
+            for (int i = 0; i < KT && ok; ++i) {
+                const int s = i % STAGES;
+                const int g = i / kGroupTiles, bank = g & 1;
+                const bool first_in_group = (i % kGroupTiles) == 0;
+                if (first_in_group && g >= 2) {
+                    // the epilogue must have read this bank's previous group
+                    if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                }
+                if (!mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1))) { ok = false; break; }
+                inflight[s] = -1;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint8_t* st = smem + s * STAGE_BYTES;
+                const uint64_t dah = sw128_desc(st), dal = sw128_desc(st + A_TILE);
+                const uint64_t dbh = sw128_desc(st + 2 * A_TILE);
+                const uint64_t dbl = sw128_desc(st + 2 * A_TILE + B_TILE);
+                const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes
-                const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
-                mma_bf16(tmem, dah + off, dbh + off, idesc, acc0);
-                mma_bf16(tmem, dah + off, dbl + off, idesc, 1u);
-                mma_bf16(tmem, dal + off, dbh + off, idesc, 1u);
-            }
-            mma_commit(&empty[s]);
-            // refill the stage the previous k-tile used once its MMAs are done
-            if (i >= 1) {
-                const int ps = (i - 1) % STAGES;
-                const int nxt = i - 1 + STAGES;
-                if (nxt < KT) {
-                    if (!mbar_wait(&empty[ps], (uint32_t)(((i - 1) / STAGES) & 1))) {
-                        ok = false;
-                        break;
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 8 fp32 = 32 bytes
+                    const uint32_t acc0 = (!first_in_group || kk > 0) ? 1u : 0u;
+                    mma_tf32(acc_t, dah + off, dbh + off, idesc, acc0);
+                    mma_tf32(acc_t, dah + off, dbl + off, idesc, 1u);
+                    mma_tf32(acc_t, dal + off, dbh + off, idesc, 1u);
+                }
+                mma_commit(&empty[s]);
+                if ((i % kGroupTiles) == kGroupTiles - 1 || i == KT - 1) mma_commit(&bank_full[bank]);
+                // refill the stage the previous k-tile used once its MMAs are done
+                if (i >= 1) {
+                    const int ps = (i - 1) % STAGES;
+                    const int nxt = i - 1 + STAGES;
+                    if (nxt < KT) {
+                        if (!mbar_wait(&empty[ps], (uint32_t)(((i - 1) / STAGES) & 1))) { ok = false; break; }
+                        load_stage(ps, kt0 + nxt);
+                        inflight[ps] = nxt;
                     }
-                    load_stage(ps, kt0 + nxt);
-                    inflight[ps] = nxt;
                 }
             }
+            if (!ok) {
+                for (int s2 = 0; s2 < STAGES; ++s2)
+                    if (inflight[s2] >= 0) mbar_wait(&full[s2], (uint32_t)((inflight[s2] / STAGES) & 1));
+                *abort_flag = 1;
+                if (hdr) set_status(hdr, HAWKES_ERR_CUDA);
+                // release the epilogue warps waiting on the banks
+                mma_commit(&bank_full[0]);
+                mma_commit(&bank_full[1]);
+            }
+            // no MMA may still be writing tensor memory when it is freed
+            mma_commit(done);
+            mbar_wait(done, 0);
         }
-        mma_commit(done);
-        if (!ok) {
-            // let the copies still in flight land before the block's smem is released
-            for (int s2 = 0; s2 < STAGES; ++s2)
-                if (inflight[s2] >= 0) mbar_wait(&full[s2], (uint32_t)((inflight[s2] / STAGES) & 1));
-            *abort_flag = 1;
-            if (hdr) set_status(hdr, HAWKES_ERR_CUDA);
-        }
-    }
-    __syncthreads();
-    bool have = KT > 0 && !*abort_flag;
-    if (KT > 0) {
-        // all issued MMAs complete before the accumulator is read or freed
-        if (!mbar_wait(done, 0)) {
-            have = false;
-            if (lane == 0 && hdr) set_status(hdr, HAWKES_ERR_CUDA);
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    if (have) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            float v[32];
-            tmem_ld32(tbase + (uint32_t)c0, v);
-            if (row < Mdim) {
-                float* drow = D + (int64_t)row * ldd + n0 + c0;
+    } else if (KT > 0) {
+        // epilogue warps: promote each group's partial sum into FP32 registers
+        const int lane_base = 32 * (warp & 3);
+        const int col_base = 128 * (warp >> 2);
+        float run[128];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (n0 + c0 + j < Ndim) {
-                        if (atomic_out) atomicAdd(drow + j, v[j]);
-                        else drow[j] = v[j];
+        for (int j = 0; j < 128; ++j) run[j] = 0.f;
+        bool good = true;
+        for (int g = 0; g < ngroups && good; ++g) {
+            const int bank = g & 1;
+            if (!mbar_wait(&bank_full[bank], (uint32_t)((g >> 1) & 1))) { good = false; break; }
+            if (*abort_flag) { good = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t tb = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(bank * BN + col_base);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float v[32];
+                tmem_ld32(tb + (uint32_t)(32 * c), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) run[32 * c + j] += v[j];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                            smem_u32(&bank_empty[bank]))
+                                        : "memory");
+        }
+        if (!good && lane == 0 && hdr) set_status(hdr, HAWKES_ERR_CUDA);
+        const int row = m0 + lane_base + lane;
+        if (bias && blockIdx.z == 0) {
+#pragma unroll
+            for (int j = 0; j < 128; ++j)
+                run[j] += (n0 + col_base + j < Ndim) ? __ldg(bias + n0 + col_base + j) : 0.f;
+        }
+        if (good && row < Mdim) {
+            float* drow = D + (int64_t)row * ldd + n0 + col_base;
+            if (!atomic_out && (ldd & 3) == 0 && n0 + col_base + 128 <= Ndim &&
+                ((uintptr_t)drow & 15) == 0) {
+#pragma unroll
+                for (int j = 0; j < 128; j += 4)
+                    *(float4*)(drow + j) = make_float4(run[j], run[j + 1], run[j + 2], run[j + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 128; ++j) {
+                    if (n0 + col_base + j < Ndim) {
+                        if (atomic_out) atomicAdd(drow + j, run[j]);
+                        else drow[j] = run[j];
                     }
                 }
             }
@@ -260,7 +311,7 @@ k_gemm_bf16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == kEpiWarps)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
 }
@@ -281,16 +332,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D bf16 tensor [rows][k] with row stride ld (elements), box {64, box_rows}.
+// 2-D fp32 tensor [rows][k] with row stride ld (elements), box {32, box_rows}.
 static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t k, int64_t ld,
                      int box_rows) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -300,21 +351,22 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t k, 
 }  // namespace tc
 
 // D[m][n] (+)= sum_k A[m][k] B[n][k] over m < Mdim, n < Ndim, k < Kdim; A and B given as
-// bf16 hi/lo pairs with row strides lda, ldb (elements, multiples of 8; bases 16-byte aligned).
-cudaError_t tc_gemm_bf16x3(const __nv_bfloat16* Ah, const __nv_bfloat16* Al, int64_t lda,
-                           const __nv_bfloat16* Bh, const __nv_bfloat16* Bl, int64_t ldb,
-                           float* D, int64_t ldd, int Mdim, int Ndim, int64_t Kdim, int splits,
-                           bool accumulate, WsHeader* hdr, cudaStream_t s) {
+// tf32 hi/lo pairs (fp32 containers) with row strides lda, ldb (elements, multiples of 4;
+// bases 16-byte aligned).
+cudaError_t tc_gemm_tf32x3(const float* Ah, const float* Al, int64_t lda, const float* Bh,
+                           const float* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
+                           int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
+                           cudaStream_t s, const float* bias) {
     using namespace tc;
     if (Mdim <= 0 || Ndim <= 0 || Kdim <= 0) return cudaSuccess;
-    if ((lda % 8) || (ldb % 8)) return cudaErrorInvalidValue;
+    if ((lda % 4) || (ldb % 4)) return cudaErrorInvalidValue;
     Maps maps;
     if (!make_map(&maps.ah, Ah, Mdim, Kdim, lda, BM) || !make_map(&maps.al, Al, Mdim, Kdim, lda, BM) ||
         !make_map(&maps.bh, Bh, Ndim, Kdim, ldb, BN) || !make_map(&maps.bl, Bl, Ndim, Kdim, ldb, BN))
         return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16x3,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tf32x3,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM_BYTES);
         if (e != cudaSuccess) return e;
@@ -327,32 +379,79 @@ cudaError_t tc_gemm_bf16x3(const __nv_bfloat16* Ah, const __nv_bfloat16* Al, int
     splits = (kt_total + per - 1) / per;
     dim3 grid((unsigned)((Ndim + BN - 1) / BN), (unsigned)((Mdim + BM - 1) / BM), (unsigned)splits);
     const int atomic_out = (splits > 1 || accumulate) ? 1 : 0;
-    k_gemm_bf16x3<<<grid, 128, SMEM_BYTES, s>>>(maps, D, ldd, Mdim, Ndim, kt_total, per,
-                                                 atomic_out, hdr);
+    k_gemm_tf32x3<<<grid, kThreads, SMEM_BYTES, s>>>(maps, D, ldd, Mdim, Ndim, kt_total, per,
+                                                 atomic_out, bias, hdr);
     return cudaGetLastError();
 }
 
-// Split an FP32 matrix [rows][cols] (row stride lds) into bf16 hi/lo [rows][ldd].
-__global__ void k_split_bf16(const float* __restrict__ src, int64_t lds, __nv_bfloat16* hi,
-                             __nv_bfloat16* lo, int64_t ldd, int64_t rows, int64_t cols) {
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - hi);
+}
+
+// Split an FP32 matrix [rows][cols] (row stride lds), minus an optional per-column
+// centre, into tf32 hi/lo [rows][ldd].
+__global__ void k_split_tf32(const float* __restrict__ src, int64_t lds, float* hi, float* lo,
+                             int64_t ldd, int64_t rows, int64_t cols, const float* centre) {
     const int64_t n = rows * cols;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / cols, c = i % cols;
-        const float x = src[r * lds + c];
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        float h, l;
+        split_tf32(src[r * lds + c] - (centre ? centre[c] : 0.f), h, l);
         hi[r * ldd + c] = h;
-        lo[r * ldd + c] = __float2bfloat16_rn(x - __bfloat162float(h));
+        lo[r * ldd + c] = l;
     }
 }
 
-cudaError_t split_bf16(const float* src, int64_t lds, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                       int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
+cudaError_t split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd,
+                       int64_t rows, int64_t cols, cudaStream_t s, const float* centre) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     int64_t n = rows * cols;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_split_bf16<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols);
+    k_split_tf32<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, centre);
+    return cudaGetLastError();
+}
+
+// dst[c][r] = split(src[r][c] - centre[c]) for r < rows_pad (zero for r >= *rows_valid):
+// transposes a chunk-major [rows][cols] FP32 matrix into cols x rows tf32 hi/lo with
+// chunks contiguous.
+__global__ void k_transpose_split_tf32(const float* __restrict__ src, int64_t cols,
+                                       const int64_t* rows_valid, int64_t rows_pad, float* hi,
+                                       float* lo, int64_t ldd, const float* centre) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int64_t nvalid = *rows_valid;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] =
+            (r < nvalid && c < cols) ? src[r * cols + c] - (centre ? centre[c] : 0.f) : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows_pad) {
+            float h, l;
+            split_tf32(tile[threadIdx.x][i], h, l);
+            hi[c * ldd + r] = h;
+            lo[c * ldd + r] = l;
+        }
+    }
+}
+
+cudaError_t transpose_split_tf32(const float* src, int64_t cols, const int64_t* rows_valid,
+                                 int64_t rows_pad, float* hi, float* lo, int64_t ldd,
+                                 cudaStream_t s, const float* centre) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows_pad + 31) / 32));
+    k_transpose_split_tf32<<<grid, dim3(32, 8), 0, s>>>(src, cols, rows_valid, rows_pad, hi, lo,
+                                                        ldd, centre);
     return cudaGetLastError();
 }
 
@@ -360,20 +459,21 @@ cudaError_t split_bf16(const float* src, int64_t lds, __nv_bfloat16* hi, __nv_bf
 
 // Test hook (declared in no public header): the same GEMM on caller buffers, so a GPU
 // test can compare it with a reference product.  D[m][n] = sum_k A[m][k] B[n][k] from
-// FP32 A [M][K] and B [N][K]; scratch must hold 2*(M+N)*K bf16 (row stride K rounded up
-// to 8).  Returns 0 on success.
+// FP32 A [M][K] and B [N][K]; scratch must hold 2*(M+N)*ld floats (ld = K rounded up to
+// 4).  Returns 0 on success.
 extern "C" int hawkes_test_tc_gemm(const float* A, const float* B, float* D, int M, int N,
                                    int K, int splits, void* scratch, void* stream) {
     using namespace hk;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t ld = (K + 7) / 8 * 8;
-    __nv_bfloat16* p = (__nv_bfloat16*)scratch;
-    __nv_bfloat16 *Ah = p, *Al = Ah + (int64_t)M * ld, *Bh = Al + (int64_t)M * ld,
-                  *Bl = Bh + (int64_t)N * ld;
-    if (split_bf16(A, K, Ah, Al, ld, M, K, s) != cudaSuccess) return 1;
-    if (split_bf16(B, K, Bh, Bl, ld, N, K, s) != cudaSuccess) return 1;
+    const int64_t ld = (K + 3) / 4 * 4;
+    float* p = (float*)scratch;
+    float *Ah = p, *Al = Ah + (int64_t)M * ld, *Bh = Al + (int64_t)M * ld,
+          *Bl = Bh + (int64_t)N * ld;
+    if (split_tf32(A, K, Ah, Al, ld, M, K, s, nullptr) != cudaSuccess) return 1;
+    if (split_tf32(B, K, Bh, Bl, ld, N, K, s, nullptr) != cudaSuccess) return 1;
     if (splits > 1) cudaMemsetAsync(D, 0, sizeof(float) * (size_t)M * N, s);
-    return tc_gemm_bf16x3(Ah, Al, ld, Bh, Bl, ld, D, N, M, N, K, splits, false, nullptr, s) ==
+    return tc_gemm_tf32x3(Ah, Al, ld, Bh, Bl, ld, D, N, M, N, K, splits, false, nullptr, s,
+                          nullptr) ==
                    cudaSuccess
                ? 0
                : 2;

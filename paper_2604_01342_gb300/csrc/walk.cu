@@ -17,7 +17,7 @@
 // event e.  The gradient needs w_k, so the 32 events are walked a second time
 // from the saved batch-start state (recomputing the decays is cheaper than
 // keeping 32 states per lane).  dt_k and T - t_k are FP64 differences rounded to
-// FP32; log lambda is FP32 and its sum FP64.
+// FP32; the log-sum is taken as the log of an FP64 product (LogProd).
 #include "common.cuh"
 
 namespace hk {
@@ -40,7 +40,7 @@ __device__ __forceinline__ float warp_transpose_reduce(float (&v)[32], int lane)
 
 template <int R, bool GRAD>
 __device__ void flush(const Problem& p, int32_t seq, float* E_s, float* F_s, float* dmu_s,
-                      float* dal_s, float (&dbr)[R], double& ll, int lane) {
+                      float* dal_s, float (&dbr)[R], LogProd& lp, int lane) {
     const int M = p.M;
     for (int j = lane; j < M; j += 32) {
         float e = E_s[j], f = F_s[j];
@@ -67,10 +67,11 @@ __device__ void flush(const Problem& p, int32_t seq, float* E_s, float* F_s, flo
             dbr[r] = 0.f;
         }
     }
+    double ll = lp.log_value();
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) ll += __shfl_xor_sync(HK_FULL, ll, o);
     if (lane == 0 && ll != 0.0) atomicAdd(&p.ll_acc[seq], ll);
-    ll = 0.0;
+    lp = LogProd();
     __syncwarp();
 }
 
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
 
     int32_t cur = -1;
     float bj[R], dbr[R];
-    double ll = 0.0;
+    LogProd lp;
     double T = 0.0;
     const float* mu = nullptr;
     const float* alpha = nullptr;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
     for (; b < b_end; ++b) {
         const int32_t seq = p.chunk_seq[b];
         if (seq != cur) {
-            if (cur >= 0) flush<R, GRAD>(p, cur, E_s, F_s, dmu_s, dal_s, dbr, ll, lane);
+            if (cur >= 0) flush<R, GRAD>(p, cur, E_s, F_s, dmu_s, dal_s, dbr, lp, lane);
             cur = seq;
             T = p.Tarr[seq];
             mu = p.mu + (int64_t)seq * M;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
             if (valid) {
                 const float lam = __ldg(mu + ck) + exc;
                 if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
-                ll += (double)logf(lam);
+                lp.mul(lam);
                 w = 1.f / lam;
                 const float bc = p.shared ? bj[0] : __ldg(beta_row + ck);
                 const float x = (float)(T - tk);
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
             __syncwarp();
         }
     }
-    if (cur >= 0) flush<R, GRAD>(p, cur, E_s, F_s, dmu_s, dal_s, dbr, ll, lane);
+    if (cur >= 0) flush<R, GRAD>(p, cur, E_s, F_s, dmu_s, dal_s, dbr, lp, lane);
 }
 
 cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nl) {
