@@ -31,6 +31,7 @@ enum Path { PATH_WALK = 1, PATH_GEMM = 2 };
 struct Plan {
     int path;
     int C;
+    int P;
     int Gc;
     int64_t nb_max, ng_max;
     size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
@@ -57,6 +58,14 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     if (path == PATH_GEMM && M > 128 * 128) return HAWKES_ERR_UNSUPPORTED;
     pl->path = path;
     pl->C = C;
+    // mark blocks for the pair kernels: at most 128 marks per block, and about 26 events
+    // of a chunk per block so that one bucket mostly fits one 32-lane group
+    {
+        int64_t Pm = ((int64_t)M + 127) / 128, Pc = ((int64_t)C + 25) / 26;
+        int64_t P = Pm > Pc ? Pm : Pc;
+        if (P > M) P = M;
+        pl->P = (int)P;
+    }
     pl->nb_max = (N + C - 1) / C + B;
     int64_t target_groups = 1216;  // ~8 blocks per SM on 152 SMs
     int64_t gc = (pl->nb_max + target_groups - 1) / target_groups;
@@ -90,7 +99,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->off_cen = pl->off_wsum = pl->off_at = 0;
     if (path == PATH_GEMM) {
         const size_t h = sizeof(float);
-        const size_t P = ((size_t)M + 127) / 128;
+        const size_t P = (size_t)pl->P;
         pl->off_recs = take(16 * (size_t)(N > 0 ? N : 1));
         pl->off_at = take(sizeof(float) * P * P * 128 * 128);
         pl->off_bstart = take(sizeof(int32_t) * (size_t)pl->nb_max * (P + 1));
@@ -175,6 +184,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.ldk = pl.ldk;
     p.nbp = pl.nbp;
     p.C = pl.C;
+    p.P = pl.P;
     p.Gc = pl.Gc;
     p.nb_max = pl.nb_max;
     p.ng_max = pl.ng_max;

@@ -40,6 +40,7 @@ struct Problem {
     double T_single;
     // chunking
     int32_t C;               // events per chunk
+    int32_t P;               // mark blocks of the pair kernels (chunk-GEMM path)
     int32_t Gc;              // chunks per scan group
     int64_t nb_max;          // upper bound on the number of chunks
     int64_t ng_max;          // upper bound on the number of groups

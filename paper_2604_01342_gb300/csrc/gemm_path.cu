@@ -90,6 +90,7 @@ constexpr int kTile = 128;
 constexpr int kTileLd = kTile + 1;      // padded row stride against bank conflicts
 constexpr float kWideLimit = 80.f;      // beta * span above which exp(+beta delta) may overflow
 constexpr int kFwdChunksPerItem = 64;
+constexpr int kStage = 64;              // source records staged per warp at a time
 
 __device__ __forceinline__ int rec_idx(float4 r) { return __float_as_int(r.w) >> 16; }
 __device__ __forceinline__ int rec_pos(float4 r) { return __float_as_int(r.w) & 0xffff; }
@@ -97,7 +98,7 @@ __device__ __forceinline__ int rec_pos(float4 r) { return __float_as_int(r.w) & 
 // alpha in tile-major order: at[((I * P + J) * 128 + r) * 128 + q] = alpha[I + P r][J + P q]
 // (zero outside the matrix).
 __global__ void k_alpha_tiles(Problem p, float* at) {
-    const int M = p.M, P = (M + kTile - 1) / kTile;
+    const int M = p.M, P = p.P;
     const int64_t total = (int64_t)P * P * kTile * kTile;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -109,14 +110,16 @@ __global__ void k_alpha_tiles(Problem p, float* at) {
     }
 }
 
-// One block per chunk: bucket the chunk's events by mark block (unordered inside a
-// bucket: pairs compare the in-chunk index explicitly).
+// One block per chunk: bucket the chunk's events by mark block, each bucket sorted by
+// (position of the mark in its block, index in the chunk).
 __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t* bstart,
                                                 uint8_t* wide) {
-    extern __shared__ int32_t cnt[];      // [P] counters, then [P+1] bases
+    extern __shared__ int32_t sm_i[];
+    const int P = p.P;
+    int32_t* cnt = sm_i;                  // [P]
+    int32_t* base = cnt + P;              // [P+1]
+    int32_t* ukey = base + P + 1;         // [C] keys in unordered bucket slots
     if (failed(p.hdr)) return;
-    const int P = (p.M + kTile - 1) / kTile;
-    int32_t* base = cnt + P;
     const float beta = p.beta[0];
     const int64_t nb = num_chunks(p);
     for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -140,15 +143,24 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t
             bstart[b * (P + 1) + P] = acc;
         }
         __syncthreads();
+        // unordered placement of the sort keys (position << 16 | index)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int ck = p.c[s0 + i];
+            const int q = ck % P;
+            ukey[base[q] + atomicAdd(&cnt[q], 1)] = ((ck / P) << 16) | i;
+        }
+        __syncthreads();
         const bool isw = beta * (float)(p.t[s1 - 1] - tau) > kWideLimit;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int ck = p.c[s0 + i];
+            const int q = ck % P;
+            const int key = ((ck / P) << 16) | i;
+            int rank = 0;
+            for (int j = base[q]; j < base[q + 1]; ++j) rank += ukey[j] < key;
             const float d = (float)(p.t[s0 + i] - tau);
             const float em = expf(-beta * d);
             const float ep = isw ? 0.f : expf(beta * d);
-            const int q = ck % P;
-            const int pos = base[q] + atomicAdd(&cnt[q], 1);
-            recs[s0 + pos] = make_float4(d, em, ep, __int_as_float((i << 16) | (ck / P)));
+            recs[s0 + base[q] + rank] = make_float4(d, em, ep, __int_as_float((i << 16) | (ck / P)));
         }
         if (threadIdx.x == 0) wide[b] = isw ? 1 : 0;
         __syncthreads();
@@ -157,16 +169,20 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t
 
 // Forward pairs: for every event k,
 //   A_k = sum_{l<k in chunk} P_kl alpha[c_k][c_l],  B_k = sum (t_k - t_l) P_kl alpha[c_k][c_l].
-__global__ void __launch_bounds__(256) k_pairs_fwd(Problem p, const float4* __restrict__ recs,
+constexpr int kPairThreads = 1024;
+constexpr int kPairWarps = kPairThreads / 32;
+
+__global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const float4* __restrict__ recs,
                                                    const int32_t* __restrict__ bstart,
                                                    const uint8_t* __restrict__ wide,
                                                    const float* __restrict__ at, float* Aout,
                                                    float* Bout, int* counter) {
-    extern __shared__ float tile[];       // [kTile][kTileLd]
+    extern __shared__ float tile[];       // [kTile][kTileLd], then per-warp staging
     __shared__ int item_sh;
     if (failed(p.hdr)) return;
-    const int M = p.M, P = (M + kTile - 1) / kTile;
+    const int P = p.P;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    float4* stage = (float4*)(tile + kTile * kTileLd) + warp * kStage;
     const int nb = (int)num_chunks(p);
     const int nranges = (nb + kFwdChunksPerItem - 1) / kFwdChunksPerItem;
     const int nitems = nranges * P;
@@ -183,16 +199,18 @@ __global__ void __launch_bounds__(256) k_pairs_fwd(Problem p, const float4* __re
         const int b1 = min(b0 + kFwdChunksPerItem, nb);
         for (int J = 0; J < P; ++J) {
             __syncthreads();
-            const float* src = at + (int64_t)(I * P + J) * kTile * kTile;
-            for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x)
-                tile[(e >> 7) * kTileLd + (e & 127)] = src[e];
+            const float4* src = (const float4*)(at + (int64_t)(I * P + J) * kTile * kTile);
+            for (int e = threadIdx.x; e < kTile * kTile / 4; e += blockDim.x) {
+                const float4 v = __ldg(src + e);
+                float* d = tile + (e >> 5) * kTileLd + ((e & 31) << 2);
+                d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+            }
             __syncthreads();
             for (int b = b0 + warp; b < b1; b += nwarps) {
                 const int64_t s0 = (int64_t)b * C;
                 const int32_t* bs = bstart + (int64_t)b * (P + 1);
                 const int k0 = bs[I], k1 = bs[I + 1];
                 const int l0 = bs[J], nJ = bs[J + 1] - l0;
-                const float4* lrec = recs + s0 + l0;
                 const bool isw = wide[b] != 0;
                 for (int kb = k0; kb < k1; kb += 32) {
                     const int kk = kb + lane;
@@ -201,25 +219,31 @@ __global__ void __launch_bounds__(256) k_pairs_fwd(Problem p, const float4* __re
                     const int ik = have ? rec_idx(rk) : -1;
                     const float* trow = tile + rec_pos(rk) * kTileLd;
                     float a = 0.f, bb = 0.f;
-                    if (!isw) {
+                    for (int lb = 0; lb < nJ; lb += kStage) {
+                        const int ns = min(kStage, nJ - lb);
+                        __syncwarp();
+                        for (int q = lane; q < ns; q += 32) stage[q] = __ldg(recs + s0 + l0 + lb + q);
+                        __syncwarp();
+                        if (!isw) {
 #pragma unroll 4
-                        for (int l = 0; l < nJ; ++l) {
-                            const float4 rl = __ldg(lrec + l);
-                            const int key = __float_as_int(rl.w);
-                            float v = rk.y * rl.z * trow[key & 0xffff];
-                            v = (key >> 16) < ik ? v : 0.f;
-                            a += v;
-                            bb = fmaf(rk.x - rl.x, v, bb);
-                        }
-                    } else {
-                        for (int l = 0; l < nJ; ++l) {
-                            const float4 rl = __ldg(lrec + l);
-                            const int key = __float_as_int(rl.w);
-                            if ((key >> 16) < ik) {
-                                const float dt = rk.x - rl.x;
-                                const float v = expf(-beta * dt) * trow[key & 0xffff];
+                            for (int l = 0; l < ns; ++l) {
+                                const float4 rl = stage[l];
+                                const int key = __float_as_int(rl.w);
+                                float v = rk.y * rl.z * trow[key & 0xffff];
+                                v = (key >> 16) < ik ? v : 0.f;
                                 a += v;
-                                bb = fmaf(dt, v, bb);
+                                bb = fmaf(rk.x - rl.x, v, bb);
+                            }
+                        } else {
+                            for (int l = 0; l < ns; ++l) {
+                                const float4 rl = stage[l];
+                                const int key = __float_as_int(rl.w);
+                                if ((key >> 16) < ik) {
+                                    const float dt = rk.x - rl.x;
+                                    const float v = expf(-beta * dt) * trow[key & 0xffff];
+                                    a += v;
+                                    bb = fmaf(dt, v, bb);
+                                }
                             }
                         }
                     }
@@ -235,16 +259,22 @@ __global__ void __launch_bounds__(256) k_pairs_fwd(Problem p, const float4* __re
 }
 
 // Backward pairs: dalpha_intra[c_k][c_l] += w_k P_kl over the pairs of tile (I, J).
-__global__ void __launch_bounds__(256) k_pairs_bwd(Problem p, const float4* __restrict__ recs,
+// Bucket I is sorted by (row, index), so lanes holding events of the same row are
+// adjacent.  With u_k = w_k em_k and U_k = sum of u over the lane's row group from k on
+// (inside the 32-lane group), the lane of k adds U_k ep_l for the sources l with
+// index in [index of the previous event of its row, index of k): every (row, l) gets one
+// add per lane group, so frequent marks do not serialise shared-memory atomics.
+__global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const float4* __restrict__ recs,
                                                    const int32_t* __restrict__ bstart,
                                                    const uint8_t* __restrict__ wide,
                                                    const float* __restrict__ wbuf,
                                                    int chunks_per_cta) {
-    extern __shared__ float dtile[];      // [kTile][kTileLd]
+    extern __shared__ float dtile[];      // [kTile][kTileLd], then per-warp staging
     if (failed(p.hdr)) return;
-    const int M = p.M, P = (M + kTile - 1) / kTile;
+    const int M = p.M, P = p.P;
     const int I = blockIdx.x / P, J = blockIdx.x % P;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    float4* stage = (float4*)(dtile + kTile * kTileLd) + warp * kStage;
     const int nb = (int)num_chunks(p);
     const int b0 = blockIdx.y * chunks_per_cta;
     const int b1 = min(b0 + chunks_per_cta, nb);
@@ -259,29 +289,53 @@ __global__ void __launch_bounds__(256) k_pairs_bwd(Problem p, const float4* __re
         const int k0 = bs[I], k1 = bs[I + 1];
         const int l0 = bs[J], nJ = bs[J + 1] - l0;
         if (k0 == k1 || nJ == 0) continue;
-        const float4* lrec = recs + s0 + l0;
         const bool isw = wide[b] != 0;
         for (int kb = k0; kb < k1; kb += 32) {
             const int kk = kb + lane;
             const bool have = kk < k1;
             const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
             const int ik = have ? rec_idx(rk) : -1;
-            const float uk = have ? wbuf[s0 + ik] * rk.y : 0.f;
-            float* drow = dtile + rec_pos(rk) * kTileLd;
+            const int row = have ? rec_pos(rk) : -1 - lane;   // distinct for idle lanes
+            const float wk = have ? wbuf[s0 + ik] : 0.f;
             if (!isw) {
+                // segmented suffix sum of u over equal rows inside the lane group
+                float U = wk * rk.y;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float up = __shfl_down_sync(HK_FULL, U, o);
+                    const int rowo = __shfl_down_sync(HK_FULL, row, o);
+                    if (lane + o < 32 && rowo == row) U += up;
+                }
+                const int prow = __shfl_up_sync(HK_FULL, row, 1);
+                const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
+                const int lo = (lane > 0 && prow == row) ? pidx : -1;
+                float* drow = dtile + (have ? row : 0) * kTileLd;
+                for (int lb = 0; lb < nJ; lb += kStage) {
+                    const int ns = min(kStage, nJ - lb);
+                    __syncwarp();
+                    for (int q = lane; q < ns; q += 32) stage[q] = __ldg(recs + s0 + l0 + lb + q);
+                    __syncwarp();
 #pragma unroll 4
-                for (int l = 0; l < nJ; ++l) {
-                    const float4 rl = __ldg(lrec + l);
-                    const int key = __float_as_int(rl.w);
-                    if ((key >> 16) < ik) atomicAdd(drow + (key & 0xffff), uk * rl.z);
+                    for (int l = 0; l < ns; ++l) {
+                        const float4 rl = stage[l];
+                        const int key = __float_as_int(rl.w);
+                        const int il = key >> 16;
+                        if (il < ik && il >= lo) atomicAdd(drow + (key & 0xffff), U * rl.z);
+                    }
                 }
             } else {
-                const float wk = have ? wbuf[s0 + ik] : 0.f;
-                for (int l = 0; l < nJ; ++l) {
-                    const float4 rl = __ldg(lrec + l);
-                    const int key = __float_as_int(rl.w);
-                    if ((key >> 16) < ik)
-                        atomicAdd(drow + (key & 0xffff), wk * expf(-beta * (rk.x - rl.x)));
+                float* drow = dtile + (have ? row : 0) * kTileLd;
+                for (int lb = 0; lb < nJ; lb += kStage) {
+                    const int ns = min(kStage, nJ - lb);
+                    __syncwarp();
+                    for (int q = lane; q < ns; q += 32) stage[q] = __ldg(recs + s0 + l0 + lb + q);
+                    __syncwarp();
+                    for (int l = 0; l < ns; ++l) {
+                        const float4 rl = stage[l];
+                        const int key = __float_as_int(rl.w);
+                        if ((key >> 16) < ik)
+                            atomicAdd(drow + (key & 0xffff), wk * expf(-beta * (rk.x - rl.x)));
+                    }
                 }
             }
         }
@@ -419,7 +473,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int P = (int)((M + kTile - 1) / kTile);
+    const int P = p.P;
     {
         // alpha in tile-major order, and the events of every chunk bucketed by mark block
         int64_t total = (int64_t)P * P * kTile * kTile;
@@ -427,7 +481,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         k_alpha_tiles<<<(unsigned)blocks, 256, 0, s>>>(p, p.at);
         ++*nl;
-        size_t smem = sizeof(int32_t) * (2 * (size_t)P + 1);
+        size_t smem = sizeof(int32_t) * (2 * (size_t)P + 1 + (size_t)p.C);
         int64_t grid = nb < (int64_t)sms * 16 ? nb : (int64_t)sms * 16;
         k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 256, smem, s>>>(p, p.recs, p.bstart, p.wide);
         ++*nl;
@@ -436,10 +490,10 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     }
     {
         // forward pairs: work items (row block, 64 chunks) from a counter in the header
-        const size_t smem = sizeof(float) * kTile * kTileLd;
+        const size_t smem = sizeof(float) * kTile * kTileLd + sizeof(float4) * kStage * kPairWarps;
         err = cudaFuncSetAttribute(k_pairs_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        k_pairs_fwd<<<(unsigned)(sms * 3), 256, smem, s>>>(p, p.recs, p.bstart, p.wide, p.at,
+        k_pairs_fwd<<<(unsigned)(sms * 2), kPairThreads, smem, s>>>(p, p.recs, p.bstart, p.wide, p.at,
                                                            p.Aint, p.Bint,
                                                            (int*)&p.hdr->pad[8]);
         ++*nl;
@@ -464,15 +518,15 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     }
     if (p.grad) {
         // backward pairs: tile (I, J) x chunk range
-        const size_t smem = sizeof(float) * kTile * kTileLd;
+        const size_t smem = sizeof(float) * kTile * kTileLd + sizeof(float4) * kStage * kPairWarps;
         err = cudaFuncSetAttribute(k_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        int64_t R = ((int64_t)sms * 3 + P * P - 1) / (P * P);
+        int64_t R = ((int64_t)sms * 2 + P * P - 1) / (P * P);
         int64_t per = (nb + R - 1) / R;
         if (per < 1) per = 1;
         R = (nb + per - 1) / per;
         if (R < 1) R = 1;
-        k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), 256, smem, s>>>(p, p.recs, p.bstart,
+        k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), kPairThreads, smem, s>>>(p, p.recs, p.bstart,
                                                                          p.wide, p.wbuf, (int)per);
         ++*nl;
         prof_mark(s, "pairs_bwd");
