@@ -440,7 +440,7 @@ def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
     """Dominant kernel's achieved rate against its bound (units stated in the design doc)."""
     if not kern_ms:
         return None
-    C = args.chunk or 256
+    C = args.chunk or 192
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, FMA = 2 flops
     tf32_peak = bf16 / 2.0                                # dense TF32 = BF16 / 2 (nominal ratio)

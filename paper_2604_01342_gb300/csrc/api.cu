@@ -24,7 +24,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 constexpr int kDefaultChunkWalk = 128;
-constexpr int kDefaultChunkGemm = 256;
+constexpr int kDefaultChunkGemm = 192;
 
 enum Path { PATH_WALK = 1, PATH_GEMM = 2 };
 
