@@ -123,6 +123,36 @@ hawkes_status hawkes_loglik_grad_varlen(const double* t, const int32_t* c,
                                         size_t workspace_bytes, double* out_ll, float* d_mu,
                                         float* d_alpha, float* d_beta, void* stream);
 
+/* Slices of one long sequence, for splitting its events over several devices (paper,
+ * Section 3.3: a batch of events depends on the previous ones only through one carried
+ * state, so the contributions of consecutive slices add up exactly).
+ *
+ * hawkes_slice_aggregate: the state that the slice's events [t, c] (device, N events) leave
+ * at time t_next >= t[N-1] (the first event time of the next slice), from a zero start:
+ *     agg_S[j] = sum_{l: c_l = j} exp(-beta_j (t_next - t_l)),
+ *     agg_G[j] = sum_{l: c_l = j} (t_next - t_l) exp(-beta_j (t_next - t_l))
+ * (device outputs [M]).  The carried state of slice r+1 is then
+ *     S_{r+1} = d_r S_r + agg_S_r,  G_{r+1} = d_r (G_r + D_r S_r) + agg_G_r,
+ * D_r = t_next - (first event time of slice r), d_r = exp(-beta D_r) (host-side exchange).
+ * The workspace only needs its 256-byte header.  The inputs are not validated here.
+ *
+ * hawkes_loglik_grad_slice: hawkes_loglik_grad for a slice whose first event sees the
+ * carried state carry_S, carry_G (device [M] each; both NULL = zero state, i.e. the first
+ * slice).  T is the observation end of the whole sequence.  base_term = 1 adds the
+ * -T sum(mu) term to L and -T to dL/dmu; set it in exactly one slice.  L and the gradients
+ * of all slices sum to those of the whole sequence. */
+hawkes_status hawkes_slice_aggregate(const double* t, const int32_t* c, int64_t N, int32_t M,
+                                     const float* beta, const hawkes_opts* opts, double t_next,
+                                     void* workspace, size_t workspace_bytes, float* agg_S,
+                                     float* agg_G, void* stream);
+hawkes_status hawkes_loglik_grad_slice(const double* t, const int32_t* c, int64_t N, double T,
+                                       int32_t M, const float* mu, const float* alpha,
+                                       const float* beta, const hawkes_opts* opts,
+                                       const float* carry_S, const float* carry_G,
+                                       int32_t base_term, void* workspace,
+                                       size_t workspace_bytes, double* out_ll, float* d_mu,
+                                       float* d_alpha, float* d_beta, void* stream);
+
 /* End-to-end form of hawkes_loglik_grad with HOST buffers: copies t, c and the
  * parameters from host memory (pinned memory makes the copies asynchronous) into the
  * device workspace, runs the same kernels, copies L and the gradients back into host

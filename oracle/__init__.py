@@ -71,6 +71,11 @@ def _load():
             lib.oracle_loglik_grad_varlen.argtypes = [p, p, p, i32, p, i32, p, p, p, p, p, p, p]
             lib.oracle_mark_counts.argtypes = [i64, p, i32, p]
             lib.oracle_condition.argtypes = [i64, p, p, d, i32, p, p, p, p, p]
+            lib.oracle_loglik_grad_carry.argtypes = [i64, p, p, d, i32, p, p, p, p, p,
+                                                     ctypes.c_int, p, p, p, p, p]
+            lib.oracle_loglik_grad_carry.restype = ctypes.c_int
+            lib.oracle_slice_aggregate.argtypes = [i64, p, p, i32, p, d, p, p]
+            lib.oracle_slice_aggregate.restype = ctypes.c_int
             lib.oracle_condition.restype = ctypes.c_int
             for f in (lib.oracle_loglik_grad, lib.oracle_grad_adjoint, lib.oracle_paper_grad_shared,
                       lib.oracle_loglik_grad_varlen, lib.oracle_mark_counts):
@@ -187,3 +192,31 @@ def condition(t, c, T, mu, alpha, beta):
     if rc:
         raise OracleError(rc)
     return {"ll": float(sl[0]), "dbeta": sb}
+
+
+def loglik_grad_carry(t, c, T, mu, alpha, beta, S0=None, G0=None, base_term=True):
+    """L and gradients of a slice whose first event sees the carried state (S0, G0)."""
+    t, c, mu, alpha, beta, M = _prep(t, c, mu, alpha, beta)
+    S0 = None if S0 is None else np.ascontiguousarray(S0, dtype=np.float64)
+    G0 = None if G0 is None else np.ascontiguousarray(G0, dtype=np.float64)
+    ll, dmu, dal, dbe = np.zeros(1), np.zeros(M), np.zeros((M, M)), np.zeros(M)
+    rc = _load().oracle_loglik_grad_carry(t.shape[0], _ptr(t), _ptr(c), float(T), M, _ptr(mu),
+                                          _ptr(alpha), _ptr(beta), _ptr(S0), _ptr(G0),
+                                          int(bool(base_term)), _ptr(ll), None, _ptr(dmu),
+                                          _ptr(dal), _ptr(dbe))
+    if rc:
+        raise OracleError(rc)
+    return {"ll": float(ll[0]), "dmu": dmu, "dalpha": dal, "dbeta": dbe}
+
+
+def slice_aggregate(t, c, M, beta, t_next):
+    """(aggS, aggG): the slice's state contributions at time t_next."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    beta = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, np.float64), (M,)))
+    aS, aG = np.zeros(M), np.zeros(M)
+    rc = _load().oracle_slice_aggregate(t.shape[0], _ptr(t), _ptr(c), M, _ptr(beta),
+                                        float(t_next), _ptr(aS), _ptr(aG))
+    if rc:
+        raise OracleError(rc)
+    return aS, aG

@@ -79,10 +79,15 @@ static int check_inputs(int64_t N, const double* t, const int32_t* c, double T,
 /* Log-likelihood and gradient in one forward pass (forward-mode G state).
  * Any of lam, dmu, dalpha, dbeta may be NULL.  dbeta is per source (length M);
  * for a shared decay the caller sums it.  Memory O(M^2 + M); time O(N M). */
-int oracle_loglik_grad(int64_t N, const double* t, const int32_t* c, double T,
-                       int32_t M, const double* mu, const double* alpha,
-                       const double* beta, double* out_ll, double* lam,
-                       double* dmu, double* dalpha, double* dbeta)
+/* The same for a slice of a longer sequence: its first event sees the state S0, G0
+ * (the paper, Section 3.3: a batch depends on the events before it only through one
+ * carried state; NULL = zero state).  base_term = 0 leaves out -T sum(mu) from L and -T
+ * from dL/dmu, so that the slices of a sequence add up to the whole. */
+int oracle_loglik_grad_carry(int64_t N, const double* t, const int32_t* c, double T,
+                             int32_t M, const double* mu, const double* alpha,
+                             const double* beta, const double* S0, const double* G0,
+                             int base_term, double* out_ll, double* lam,
+                             double* dmu, double* dalpha, double* dbeta)
 {
     int rc = check_inputs(N, t, c, T, M, mu, alpha, beta);
     if (rc) return rc;
@@ -91,6 +96,8 @@ int oracle_loglik_grad(int64_t N, const double* t, const int32_t* c, double T,
     double* E = calloc((size_t)M, sizeof(double));
     double* F = calloc((size_t)M, sizeof(double));
     if (!S || !G || !E || !F) { free(S); free(G); free(E); free(F); return OR_INVALID; }
+    if (S0) memcpy(S, S0, sizeof(double) * (size_t)M);
+    if (G0) memcpy(G, G0, sizeof(double) * (size_t)M);
     if (dmu) memset(dmu, 0, sizeof(double) * (size_t)M);
     if (dalpha) memset(dalpha, 0, sizeof(double) * (size_t)M * (size_t)M);
     if (dbeta) memset(dbeta, 0, sizeof(double) * (size_t)M);
@@ -138,14 +145,41 @@ int oracle_loglik_grad(int64_t N, const double* t, const int32_t* c, double T,
             comp += cs * E[j];
             if (dbeta) dbeta[j] -= cs * F[j];
         }
-        if (out_ll) *out_ll = logsum - T * summu - comp;
-        if (dmu) for (int32_t i = 0; i < M; ++i) dmu[i] -= T;
+        if (out_ll) *out_ll = logsum - (base_term ? T * summu : 0.0) - comp;
+        if (dmu && base_term) for (int32_t i = 0; i < M; ++i) dmu[i] -= T;
         if (dalpha)
             for (int32_t i = 0; i < M; ++i)
                 for (int32_t j = 0; j < M; ++j) dalpha[(size_t)i * M + j] -= E[j];
     }
     free(S); free(G); free(E); free(F);
     return rc;
+}
+
+int oracle_loglik_grad(int64_t N, const double* t, const int32_t* c, double T,
+                       int32_t M, const double* mu, const double* alpha,
+                       const double* beta, double* out_ll, double* lam,
+                       double* dmu, double* dalpha, double* dbeta)
+{
+    return oracle_loglik_grad_carry(N, t, c, T, M, mu, alpha, beta, NULL, NULL, 1, out_ll,
+                                    lam, dmu, dalpha, dbeta);
+}
+
+/* State contributions of a slice's events at time t_next (for the carry exchange):
+ * aggS[j] = sum_{l: c_l = j} exp(-beta_j (t_next - t_l)), aggG the same times (t_next - t_l). */
+int oracle_slice_aggregate(int64_t N, const double* t, const int32_t* c, int32_t M,
+                           const double* beta, double t_next, double* aggS, double* aggG)
+{
+    memset(aggS, 0, sizeof(double) * (size_t)M);
+    memset(aggG, 0, sizeof(double) * (size_t)M);
+    for (int64_t k = 0; k < N; ++k) {
+        if (c[k] < 0 || c[k] >= M) return OR_MARK;
+        if (t[k] > t_next) return OR_TIME;
+        double x = t_next - t[k];
+        double e = exp(-beta[c[k]] * x);
+        aggS[c[k]] += e;
+        aggG[c[k]] += x * e;
+    }
+    return OR_OK;
 }
 
 /* Gradient by the reverse-time adjoint of the same transitions (small N:

@@ -31,6 +31,7 @@ EXPORTED = (
     "hawkes_loglik_grad_host", "hawkes_last_device_status", "hawkes_mark_counts",
     "hawkes_status_str", "hawkes_last_launch_count", "hawkes_profile_enable",
     "hawkes_profile_read", "hawkes_static_scratch_bytes", "hawkes_loglik_grad_static",
+    "hawkes_slice_aggregate", "hawkes_loglik_grad_slice",
 )
 
 
@@ -89,10 +90,14 @@ def lib():
         L.hawkes_profile_read.argtypes = [ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_char_p), i32]
         L.hawkes_profile_read.restype = i32
+        L.hawkes_slice_aggregate.argtypes = [p, p, i64, i32, p, op, d, p, sz, p, p, p]
+        L.hawkes_loglik_grad_slice.argtypes = [p, p, i64, d, i32, p, p, p, op, p, p, i32, p, sz,
+                                               p, p, p, p, p]
         L.hawkes_static_scratch_bytes.argtypes = []
         L.hawkes_static_scratch_bytes.restype = sz
         L.hawkes_loglik_grad_static.argtypes = [p, p, i64, d, i32, p, p, p, op, p, p, p, p, p]
-        for name in ("hawkes_loglik_grad_static", "hawkes_loglik", "hawkes_loglik_grad",
+        for name in ("hawkes_slice_aggregate", "hawkes_loglik_grad_slice",
+                     "hawkes_loglik_grad_static", "hawkes_loglik", "hawkes_loglik_grad",
                      "hawkes_loglik_varlen",
                      "hawkes_loglik_grad_varlen", "hawkes_loglik_grad_host",
                      "hawkes_last_device_status"):
@@ -201,3 +206,17 @@ def hawkes_loglik_grad_static(t, c, N, T, M, mu, alpha, beta, opts, out_ll, d_mu
     _check(lib().hawkes_loglik_grad_static(t, c, int(N), float(T), int(M), mu, alpha, beta,
                                            ctypes.byref(opts), out_ll, d_mu, d_alpha, d_beta,
                                            stream), "hawkes_loglik_grad_static")
+
+
+def hawkes_slice_aggregate(t, c, N, M, beta, opts, t_next, ws, ws_bytes, agg_S, agg_G, stream):
+    _check(lib().hawkes_slice_aggregate(t, c, int(N), int(M), beta, ctypes.byref(opts),
+                                        float(t_next), ws, int(ws_bytes), agg_S, agg_G, stream),
+           "hawkes_slice_aggregate")
+
+
+def hawkes_loglik_grad_slice(t, c, N, T, M, mu, alpha, beta, opts, carry_S, carry_G, base_term,
+                             ws, ws_bytes, out_ll, d_mu, d_alpha, d_beta, stream):
+    _check(lib().hawkes_loglik_grad_slice(t, c, int(N), float(T), int(M), mu, alpha, beta,
+                                          ctypes.byref(opts), carry_S, carry_G,
+                                          int(bool(base_term)), ws, int(ws_bytes), out_ll, d_mu,
+                                          d_alpha, d_beta, stream), "hawkes_loglik_grad_slice")

@@ -259,7 +259,9 @@ size_t hawkes_workspace_size(int64_t N, int32_t M, int32_t B, int32_t grad,
 static hawkes_status single(const double* t, const int32_t* c, int64_t N, double T, int32_t M,
                             const float* mu, const float* alpha, const float* beta,
                             const hawkes_opts* opts, void* ws, size_t ws_bytes, double* out_ll,
-                            float* d_mu, float* d_alpha, float* d_beta, int grad, void* stream) {
+                            float* d_mu, float* d_alpha, float* d_beta, int grad, void* stream,
+                            const float* carry_S = nullptr, const float* carry_G = nullptr,
+                            int base_term = 1) {
     if (N < 0 || M <= 0 || !(T >= 0.0)) return HAWKES_ERR_INVALID_ARG;
     if (bad_ptrs({mu, alpha, beta, out_ll})) return HAWKES_ERR_INVALID_ARG;
     if (N > 0 && bad_ptrs({t, c})) return HAWKES_ERR_INVALID_ARG;
@@ -276,6 +278,9 @@ static hawkes_status single(const double* t, const int32_t* c, int64_t N, double
     p.t = t; p.c = c; p.off = (const int64_t*)&hdr->pad[0]; p.Tarr = (const double*)&hdr->pad[2];
     p.N = N; p.B = 1; p.M = M;
     p.single = 1; p.T_single = T;
+    p.base_term = base_term;
+    p.init_S = carry_S;
+    p.init_G = carry_G;
     p.mu = mu; p.alpha = alpha; p.beta = beta;
     p.shared = opts ? opts->beta_shared : 0;
     p.grad = grad;
@@ -312,6 +317,7 @@ static hawkes_status varlen(const double* t, const int32_t* c, const int64_t* of
     hk::Problem p{};
     p.t = t; p.c = c; p.off = offsets; p.Tarr = T;
     p.N = N; p.B = B; p.M = M;
+    p.base_term = 1;
     p.mu = mu; p.alpha = alpha; p.beta = beta;
     p.shared = opts ? opts->beta_shared : 0;
     p.grad = grad;
@@ -337,6 +343,42 @@ hawkes_status hawkes_loglik_grad_varlen(const double* t, const int32_t* c,
                                         float* d_alpha, float* d_beta, void* stream) {
     return varlen(t, c, offsets, B, N, T, M, mu, alpha, beta, opts, workspace, workspace_bytes,
                   out_ll, d_mu, d_alpha, d_beta, 1, stream);
+}
+
+hawkes_status hawkes_loglik_grad_slice(const double* t, const int32_t* c, int64_t N, double T,
+                                       int32_t M, const float* mu, const float* alpha,
+                                       const float* beta, const hawkes_opts* opts,
+                                       const float* carry_S, const float* carry_G,
+                                       int32_t base_term, void* workspace,
+                                       size_t workspace_bytes, double* out_ll, float* d_mu,
+                                       float* d_alpha, float* d_beta, void* stream) {
+    if ((carry_S == nullptr) != (carry_G == nullptr)) return HAWKES_ERR_INVALID_ARG;
+    return single(t, c, N, T, M, mu, alpha, beta, opts, workspace, workspace_bytes, out_ll, d_mu,
+                  d_alpha, d_beta, 1, stream, carry_S, carry_G, base_term ? 1 : 0);
+}
+
+hawkes_status hawkes_slice_aggregate(const double* t, const int32_t* c, int64_t N, int32_t M,
+                                     const float* beta, const hawkes_opts* opts, double t_next,
+                                     void* workspace, size_t workspace_bytes, float* agg_S,
+                                     float* agg_G, void* stream) {
+    if (N < 0 || M <= 0 || !beta || !agg_S || !agg_G) return HAWKES_ERR_INVALID_ARG;
+    if (N > 0 && (!t || !c)) return HAWKES_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 ||
+        workspace_bytes < align_up(sizeof(hk::WsHeader)))
+        return HAWKES_ERR_WORKSPACE;
+    hk::Problem p{};
+    p.t = t; p.c = c; p.N = N; p.B = 1; p.M = M;
+    p.beta = beta;
+    p.shared = opts ? opts->beta_shared : 0;
+    p.hdr = (hk::WsHeader*)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the header's status word is cleared here; the events are assumed to have been
+    // validated by the caller's hawkes_loglik_grad_slice on the same slice
+    if (cudaMemsetAsync(workspace, 0, sizeof(int32_t), s) != cudaSuccess) return HAWKES_ERR_CUDA;
+    int nl = 0;
+    cudaError_t e = hk::launch_slice_aggregate(p, t_next, agg_S, agg_G, s, &nl);
+    g_last_launches = nl;
+    return e == cudaSuccess ? HAWKES_OK : HAWKES_ERR_CUDA;
 }
 
 // Host-buffer form: staging for inputs and outputs sits after the device workspace.

@@ -37,6 +37,9 @@ struct Problem {
     int32_t grad;
     int32_t single;          // 1: one sequence; off/Tarr point at header words set by k_init
     int32_t validated;       // 1: the device checks (and mark counts) run in this call
+    const float* init_S;     // [M] state just before the first event (NULL = zero state)
+    const float* init_G;     // [M] derivative state at the same time (NULL = zero)
+    int32_t base_term;       // 1: include -T sum(mu) in L and -T in dL/dmu
     double T_single;
     // chunking
     int32_t C;               // events per chunk
@@ -148,6 +151,8 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_finalize(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_slice_aggregate(const Problem& p, double t_next, float* agg_S, float* agg_G,
+                                   cudaStream_t s, int* nlaunch);
 int walk_max_m(int grad);
 // Optional per-kernel timing: when enabled, records a CUDA event on the launch
 // stream after each kernel (names are static strings).

@@ -49,7 +49,8 @@ __global__ void k_finalize_vec(Problem p, const double* colsum) {
             if (p.shared) dbsum += db;
             else p.d_beta[(int64_t)s * M + j] = bad ? (float)nanv : (float)db;
             p.d_mu[(int64_t)s * M + j] =
-                bad ? (float)nanv : (float)(p.dmu_acc[(int64_t)s * M + j] - T);
+                bad ? (float)nanv
+                    : (float)(p.dmu_acc[(int64_t)s * M + j] - (p.base_term ? T : 0.0));
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -63,7 +64,7 @@ __global__ void k_finalize_vec(Problem p, const double* colsum) {
     if (threadIdx.x == 0) {
         double c = 0.0, m = 0.0, b = 0.0;
         for (int w = 0; w < nw; ++w) { c += red_comp[w]; m += red_mu[w]; b += red_be[w]; }
-        p.out_ll[s] = bad ? nanv : p.ll_acc[s] - T * m - c;
+        p.out_ll[s] = bad ? nanv : p.ll_acc[s] - (p.base_term ? T * m : 0.0) - c;
         if (p.grad && p.shared) p.d_beta[s] = bad ? (float)nanv : (float)b;
     }
 }

