@@ -88,37 +88,54 @@ __global__ void k_centres(Problem p, int have_counts) {
 // ---------------------------------------------------------------------------
 constexpr int kTile = 128;
 constexpr int kTileLd = kTile + 1;      // padded row stride against bank conflicts
-constexpr float kWideLimit = 80.f;      // beta * span above which exp(+beta delta) may overflow
+constexpr float kWideLimit = 64.f;      // beta * span above which sums of exp(+beta delta) may overflow
 constexpr int kFwdChunksPerItem = 64;
 constexpr int kStage = 64;              // source records staged per warp at a time
+constexpr int kFlushChunks = 64;       // cost of flushing one dalpha tile, in chunks of work
+// backward per-warp scratch: 32 item ranges, then up to kLStage staged sources (the
+// staging of wide chunks reuses the same bytes)
+constexpr int kLStage = 256;
+constexpr size_t kBwdWarpScratch = 32 * sizeof(int4) + kLStage * sizeof(float2);
+static_assert(kBwdWarpScratch >= kStage * sizeof(float4), "wide-chunk staging fits the scratch");
 
 __device__ __forceinline__ int rec_idx(float4 r) { return __float_as_int(r.w) >> 16; }
 __device__ __forceinline__ int rec_pos(float4 r) { return __float_as_int(r.w) & 0xffff; }
+// a source record as the pair loops read it: (delta, ep, column, index)
+__device__ __forceinline__ float4 unpack_rec(float4 r) {
+    return make_float4(r.x, r.z, __int_as_float(rec_pos(r)), __int_as_float(rec_idx(r)));
+}
 
-// alpha in tile-major order: at[((I * P + J) * 128 + r) * 128 + q] = alpha[I + P r][J + P q]
+// alpha in tile-major order, arranged for conflict-free staging into shared memory:
+// float4 number e = rr * 128 + q of tile (I, J) holds column q of rows rr, rr + 32, rr + 64,
+// rr + 96, that is at[(((I * P + J) * 4096 + e) * 4 + s] = alpha[I + P (rr + 32 s)][J + P q]
 // (zero outside the matrix).
 __global__ void k_alpha_tiles(Problem p, float* at) {
     const int M = p.M, P = p.P;
     const int64_t total = (int64_t)P * P * kTile * kTile;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int q = (int)(e % kTile), r = (int)((e / kTile) % kTile);
+        const int s = (int)(e & 3);
+        const int f = (int)((e >> 2) % (kTile * kTile / 4));
         const int tile = (int)(e / ((int64_t)kTile * kTile));
+        const int rr = f >> 7, q = f & 127;
         const int I = tile / P, J = tile % P;
-        const int i = I + P * r, j = J + P * q;
+        const int i = I + P * (rr + 32 * s), j = J + P * q;
         at[e] = (i < M && j < M) ? p.alpha[(int64_t)i * M + j] : 0.f;
     }
 }
 
 // One block per chunk: bucket the chunk's events by mark block, each bucket sorted by
-// (position of the mark in its block, index in the chunk).
-__global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t* bstart,
-                                                uint8_t* wide) {
+// (position of the mark in its block, index in the chunk) in recs; the same buckets in
+// index order in lrec (source side of the backward pairs), and the membership bits of
+// every bucket over the chunk's event indices in bmask.
+__global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2* lrec,
+                                                uint32_t* bmask, int32_t* bstart, uint8_t* wide) {
     extern __shared__ int32_t sm_i[];
-    const int P = p.P;
+    const int P = p.P, W = (p.C + 31) >> 5;
     int32_t* cnt = sm_i;                  // [P]
     int32_t* base = cnt + P;              // [P+1]
     int32_t* ukey = base + P + 1;         // [C] keys in unordered bucket slots
+    uint32_t* msk = (uint32_t*)(ukey + p.C);   // [P * W] membership bits
     if (failed(p.hdr)) return;
     const float beta = p.beta[0];
     const int64_t nb = num_chunks(p);
@@ -128,8 +145,13 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t
         const int n = (int)(s1 - s0);
         const double tau = p.t[s0];
         for (int q = threadIdx.x; q < P; q += blockDim.x) cnt[q] = 0;
+        for (int q = threadIdx.x; q < P * W; q += blockDim.x) msk[q] = 0u;
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[p.c[s0 + i] % P], 1);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int q = p.c[s0 + i] % P;
+            atomicAdd(&cnt[q], 1);
+            atomicOr(&msk[q * W + (i >> 5)], 1u << (i & 31));
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             int acc = 0;
@@ -142,6 +164,7 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t
             base[P] = acc;
             bstart[b * (P + 1) + P] = acc;
         }
+        for (int q = threadIdx.x; q < P * W; q += blockDim.x) bmask[b * P * W + q] = msk[q];
         __syncthreads();
         // unordered placement of the sort keys (position << 16 | index)
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -157,10 +180,14 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t
             const int key = ((ck / P) << 16) | i;
             int rank = 0;
             for (int j = base[q]; j < base[q + 1]; ++j) rank += ukey[j] < key;
+            const uint32_t* mq = msk + q * W;
+            int irank = __popc(mq[i >> 5] & ((1u << (i & 31)) - 1u));
+            for (int w = 0; w < (i >> 5); ++w) irank += __popc(mq[w]);
             const float d = (float)(p.t[s0 + i] - tau);
             const float em = expf(-beta * d);
             const float ep = isw ? 0.f : expf(beta * d);
             recs[s0 + base[q] + rank] = make_float4(d, em, ep, __int_as_float((i << 16) | (ck / P)));
+            lrec[s0 + base[q] + irank] = make_float2(ep, __int_as_float(ck / P));
         }
         if (threadIdx.x == 0) wide[b] = isw ? 1 : 0;
         __syncthreads();
@@ -169,8 +196,25 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, int32_t
 
 // Forward pairs: for every event k,
 //   A_k = sum_{l<k in chunk} P_kl alpha[c_k][c_l],  B_k = sum (t_k - t_l) P_kl alpha[c_k][c_l].
-constexpr int kPairThreads = 1024;
+// With P_kl = em_k ep_l the lane of k sums a = sum ep_l alpha and d = sum delta_l ep_l alpha
+// and returns A_k = em_k a, B_k = em_k (delta_k a - d).  One thread owns A_k and B_k for all
+// column blocks J, so its updates for J > 0 (reductions without a returned value, issued
+// in J order) keep a fixed summation order.
+constexpr int kPairThreads = 512;
 constexpr int kPairWarps = kPairThreads / 32;
+
+// Stage tile (I, J) of alpha (laid out by k_alpha_tiles) into rows of kTileLd floats.
+__device__ __forceinline__ void load_alpha_tile(float* tile, const float* __restrict__ at, int tile_id) {
+    const float4* src = (const float4*)(at + (int64_t)tile_id * kTile * kTile);
+    for (int e = threadIdx.x; e < kTile * kTile / 4; e += blockDim.x) {
+        const float4 v = __ldg(src + e);
+        float* d = tile + (e >> 7) * kTileLd + (e & 127);
+        d[0] = v.x;
+        d[32 * kTileLd] = v.y;
+        d[64 * kTileLd] = v.z;
+        d[96 * kTileLd] = v.w;
+    }
+}
 
 __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const float4* __restrict__ recs,
                                                    const int32_t* __restrict__ bstart,
@@ -199,12 +243,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const 
         const int b1 = min(b0 + kFwdChunksPerItem, nb);
         for (int J = 0; J < P; ++J) {
             __syncthreads();
-            const float4* src = (const float4*)(at + (int64_t)(I * P + J) * kTile * kTile);
-            for (int e = threadIdx.x; e < kTile * kTile / 4; e += blockDim.x) {
-                const float4 v = __ldg(src + e);
-                float* d = tile + (e >> 5) * kTileLd + ((e & 31) << 2);
-                d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-            }
+            load_alpha_tile(tile, at, I * P + J);
             __syncthreads();
             for (int b = b0 + warp; b < b1; b += nwarps) {
                 const int64_t s0 = (int64_t)b * C;
@@ -218,39 +257,40 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const 
                     const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const int ik = have ? rec_idx(rk) : -1;
                     const float* trow = tile + rec_pos(rk) * kTileLd;
-                    float a = 0.f, bb = 0.f;
+                    float a = 0.f, d = 0.f;
                     for (int lb = 0; lb < nJ; lb += kStage) {
                         const int ns = min(kStage, nJ - lb);
                         __syncwarp();
-                        for (int q = lane; q < ns; q += 32) stage[q] = __ldg(recs + s0 + l0 + lb + q);
+                        for (int q = lane; q < ns; q += 32)
+                            stage[q] = unpack_rec(__ldg(recs + s0 + l0 + lb + q));
                         __syncwarp();
                         if (!isw) {
 #pragma unroll 4
                             for (int l = 0; l < ns; ++l) {
-                                const float4 rl = stage[l];
-                                const int key = __float_as_int(rl.w);
-                                float v = rk.y * rl.z * trow[key & 0xffff];
-                                v = (key >> 16) < ik ? v : 0.f;
-                                a += v;
-                                bb = fmaf(rk.x - rl.x, v, bb);
+                                const float4 rl = stage[l];          // (delta, ep, column, index)
+                                const float v = rl.y * trow[__float_as_int(rl.z)];
+                                if (__float_as_int(rl.w) < ik) {
+                                    a += v;
+                                    d = fmaf(rl.x, v, d);
+                                }
                             }
                         } else {
                             for (int l = 0; l < ns; ++l) {
                                 const float4 rl = stage[l];
-                                const int key = __float_as_int(rl.w);
-                                if ((key >> 16) < ik) {
-                                    const float dt = rk.x - rl.x;
-                                    const float v = expf(-beta * dt) * trow[key & 0xffff];
+                                if (__float_as_int(rl.w) < ik) {
+                                    const float v = expf(-beta * (rk.x - rl.x)) * trow[__float_as_int(rl.z)];
                                     a += v;
-                                    bb = fmaf(dt, v, bb);
+                                    d = fmaf(rl.x, v, d);
                                 }
                             }
                         }
                     }
                     if (have) {
+                        const float em = isw ? 1.f : rk.y;
+                        const float A = em * a, B = em * fmaf(rk.x, a, -d);
                         const int64_t k = s0 + ik;
-                        if (J == 0) { Aout[k] = a; Bout[k] = bb; }
-                        else { Aout[k] += a; Bout[k] += bb; }
+                        if (J == 0) { Aout[k] = A; Bout[k] = B; }
+                        else { atomicAdd(Aout + k, A); atomicAdd(Bout + k, B); }
                     }
                 }
             }
@@ -261,26 +301,36 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const 
 // Backward pairs: dalpha_intra[c_k][c_l] += w_k P_kl over the pairs of tile (I, J).
 // Bucket I is sorted by (row, index), so lanes holding events of the same row are
 // adjacent.  With u_k = w_k em_k and U_k = sum of u over the lane's row group from k on
-// (inside the 32-lane group), the lane of k adds U_k ep_l for the sources l with
-// index in [index of the previous event of its row, index of k): every (row, l) gets one
-// add per lane group, so frequent marks do not serialise shared-memory atomics.
+// (inside the 32-lane group), the lane of k owes U_k ep_l to (row_k, column_l) for the
+// sources l of bucket J with index in [index of the previous event of its row, index of
+// k): every (row, l) gets one add per lane group.  In index order those sources are the
+// contiguous ranks [a_k, b_k) of bucket J (counted from its membership bits), so the
+// (k, l) items of a lane group are numbered 0 .. T-1 and every lane takes a contiguous
+// run of about T / 32 of them: each shared-memory add carries one item, whatever the
+// spread of the intervals.  Chunks too wide for the factorised weights take one exp per
+// pair over all (k, l) instead.
 __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const float4* __restrict__ recs,
+                                                   const float2* __restrict__ lrec,
+                                                   const uint32_t* __restrict__ bmask,
                                                    const int32_t* __restrict__ bstart,
                                                    const uint8_t* __restrict__ wide,
                                                    const float* __restrict__ wbuf,
                                                    int chunks_per_cta) {
-    extern __shared__ float dtile[];      // [kTile][kTileLd], then per-warp staging
+    extern __shared__ float dtile[];      // [kTile][kTileLd], then per-warp scratch
     if (failed(p.hdr)) return;
     const int M = p.M, P = p.P;
     const int I = blockIdx.x / P, J = blockIdx.x % P;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    float4* stage = (float4*)(dtile + kTile * kTileLd) + warp * kStage;
+    char* scratch = (char*)(dtile + kTile * kTileLd) + warp * kBwdWarpScratch;
+    int4* kd = (int4*)scratch;                          // [32] per-lane item ranges
+    float2* lst = (float2*)(kd + 32);                   // [kLStage] sources of bucket J
+    float4* stage = (float4*)scratch;                   // wide chunks: [kStage] records
     const int nb = (int)num_chunks(p);
     const int b0 = blockIdx.y * chunks_per_cta;
     const int b1 = min(b0 + chunks_per_cta, nb);
     if (b0 >= b1) return;
     const float beta = p.beta[0];
-    const int C = p.C;
+    const int C = p.C, W = (C + 31) >> 5;
     for (int e = threadIdx.x; e < kTile * kTileLd; e += blockDim.x) dtile[e] = 0.f;
     __syncthreads();
     for (int b = b0 + warp; b < b1; b += nwarps) {
@@ -290,6 +340,21 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
         const int l0 = bs[J], nJ = bs[J + 1] - l0;
         if (k0 == k1 || nJ == 0) continue;
         const bool isw = wide[b] != 0;
+        // membership bits of bucket J (word w on lane w) and the counts before each word
+        const uint32_t mw = lane < W ? __ldg(bmask + ((int64_t)b * P + J) * W + lane) : 0u;
+        int cw = __popc(mw);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(HK_FULL, cw, o);
+            if (lane >= o) cw += x;
+        }
+        cw -= __popc(mw);
+        const bool staged = !isw && nJ <= kLStage;
+        if (staged) {
+            __syncwarp();
+            for (int q = lane; q < nJ; q += 32) lst[q] = __ldg(lrec + s0 + l0 + q);
+            __syncwarp();
+        }
         for (int kb = k0; kb < k1; kb += 32) {
             const int kk = kb + lane;
             const bool have = kk < k1;
@@ -309,32 +374,77 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                 const int prow = __shfl_up_sync(HK_FULL, row, 1);
                 const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
                 const int lo = (lane > 0 && prow == row) ? pidx : -1;
-                float* drow = dtile + (have ? row : 0) * kTileLd;
-                for (int lb = 0; lb < nJ; lb += kStage) {
-                    const int ns = min(kStage, nJ - lb);
-                    __syncwarp();
-                    for (int q = lane; q < ns; q += 32) stage[q] = __ldg(recs + s0 + l0 + lb + q);
-                    __syncwarp();
-#pragma unroll 4
-                    for (int l = 0; l < ns; ++l) {
-                        const float4 rl = stage[l];
-                        const int key = __float_as_int(rl.w);
-                        const int il = key >> 16;
-                        if (il < ik && il >= lo) atomicAdd(drow + (key & 0xffff), U * rl.z);
+                // ranks in bucket J (index order) of the sources before ik and before lo
+                const int xh = have ? ik : 0, xl = lo > 0 ? lo : 0;
+                const int bk = __shfl_sync(HK_FULL, cw, xh >> 5) +
+                               __popc(__shfl_sync(HK_FULL, mw, xh >> 5) & ((1u << (xh & 31)) - 1u));
+                const int ak = __shfl_sync(HK_FULL, cw, xl >> 5) +
+                               __popc(__shfl_sync(HK_FULL, mw, xl >> 5) & ((1u << (xl & 31)) - 1u));
+                const int n = have ? bk - (lo >= 0 ? ak : 0) : 0;
+                int incl = n;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int x = __shfl_up_sync(HK_FULL, incl, o);
+                    if (lane >= o) incl += x;
+                }
+                const int excl = incl - n;
+                const int T = __shfl_sync(HK_FULL, incl, 31);
+                if (T == 0) continue;
+                // owners: the lanes with items, compacted in lane order (each has >= 1 item,
+                // so consecutive items advance by at most one owner)
+                const uint32_t amask = __ballot_sync(HK_FULL, n > 0);
+                __syncwarp();
+                if (n > 0)
+                    kd[__popc(amask & ((1u << lane) - 1u))] =
+                        make_int4(row * kTileLd, __float_as_int(U), (lo >= 0 ? ak : 0) - excl, incl);
+                __syncwarp();
+                // items [g0, g1) of this lane, L per lane; the owner of g0 is the first lane
+                // whose last item is >= g0
+                const int L = (T + 31) >> 5;
+                const int g0 = lane * L;
+                const int g1 = min(g0 + L, T);
+                int pos = 0;
+#pragma unroll
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const int in = __shfl_sync(HK_FULL, incl, pos + st - 1);
+                    if (in <= g0) pos += st;
+                }
+                int j = pos < 32 ? __popc(amask & ((1u << pos) - 1u)) : 0;
+                if (staged) {
+                    int4 ko = kd[j];
+                    for (int i = 0; i < L; ++i) {
+                        const int gi = g0 + i;
+                        j += gi >= ko.w ? 1 : 0;
+                        ko = kd[min(j, 31)];
+                        if (gi < g1)
+                            atomicAdd(dtile + ko.x + __float_as_int(lst[gi + ko.z].y),
+                                      __int_as_float(ko.y) * lst[gi + ko.z].x);
+                    }
+                } else {
+                    int4 ko = kd[j];
+                    for (int i = 0; i < L; ++i) {
+                        const int gi = g0 + i;
+                        j += gi >= ko.w ? 1 : 0;
+                        ko = kd[min(j, 31)];
+                        if (gi < g1) {
+                            const float2 l = __ldg(lrec + s0 + l0 + gi + ko.z);
+                            atomicAdd(dtile + ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x);
+                        }
                     }
                 }
+                __syncwarp();
             } else {
                 float* drow = dtile + (have ? row : 0) * kTileLd;
                 for (int lb = 0; lb < nJ; lb += kStage) {
                     const int ns = min(kStage, nJ - lb);
                     __syncwarp();
-                    for (int q = lane; q < ns; q += 32) stage[q] = __ldg(recs + s0 + l0 + lb + q);
+                    for (int q = lane; q < ns; q += 32)
+                        stage[q] = unpack_rec(__ldg(recs + s0 + l0 + lb + q));
                     __syncwarp();
                     for (int l = 0; l < ns; ++l) {
                         const float4 rl = stage[l];
-                        const int key = __float_as_int(rl.w);
-                        if ((key >> 16) < ik)
-                            atomicAdd(drow + (key & 0xffff), wk * expf(-beta * (rk.x - rl.x)));
+                        if (__float_as_int(rl.w) < ik)
+                            atomicAdd(drow + __float_as_int(rl.z), wk * expf(-beta * (rk.x - rl.x)));
                     }
                 }
             }
@@ -481,9 +591,11 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         k_alpha_tiles<<<(unsigned)blocks, 256, 0, s>>>(p, p.at);
         ++*nl;
-        size_t smem = sizeof(int32_t) * (2 * (size_t)P + 1 + (size_t)p.C);
+        const size_t W = ((size_t)p.C + 31) / 32;
+        size_t smem = sizeof(int32_t) * (2 * (size_t)P + 1 + (size_t)p.C + (size_t)P * W);
         int64_t grid = nb < (int64_t)sms * 16 ? nb : (int64_t)sms * 16;
-        k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 256, smem, s>>>(p, p.recs, p.bstart, p.wide);
+        k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 256, smem, s>>>(p, p.recs, p.lrec, p.bmask,
+                                                                     p.bstart, p.wide);
         ++*nl;
         prof_mark(s, "bucket");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -518,16 +630,29 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     }
     if (p.grad) {
         // backward pairs: tile (I, J) x chunk range
-        const size_t smem = sizeof(float) * kTile * kTileLd + sizeof(float4) * kStage * kPairWarps;
+        const size_t smem = sizeof(float) * kTile * kTileLd + kBwdWarpScratch * kPairWarps;
         err = cudaFuncSetAttribute(k_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        int64_t R = ((int64_t)sms * 2 + P * P - 1) / (P * P);
+        // Blocks of equal work: pick the number R of chunk ranges per tile that minimises
+        // (waves of resident blocks) x (chunks per block + the cost of one tile flush,
+        // counted as kFlushChunks chunks).
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_bwd, kPairThreads, smem);
+        if (err != cudaSuccess) return err;
+        const int64_t slots = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+        const int64_t tiles = (int64_t)P * P;
+        int64_t R = 1, best = -1;
+        for (int64_t r = 1; r <= 8 * slots / tiles + 1 && r <= (nb > 0 ? nb : 1); ++r) {
+            const int64_t waves = (tiles * r + slots - 1) / slots;
+            const int64_t cost = waves * ((nb + r - 1) / r + kFlushChunks);
+            if (best < 0 || cost < best) { best = cost; R = r; }
+        }
         int64_t per = (nb + R - 1) / R;
         if (per < 1) per = 1;
         R = (nb + per - 1) / per;
         if (R < 1) R = 1;
-        k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), kPairThreads, smem, s>>>(p, p.recs, p.bstart,
-                                                                         p.wide, p.wbuf, (int)per);
+        k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), kPairThreads, smem, s>>>(
+            p, p.recs, p.lrec, p.bmask, p.bstart, p.wide, p.wbuf, (int)per);
         ++*nl;
         prof_mark(s, "pairs_bwd");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
