@@ -38,7 +38,7 @@ struct Plan {
         off_grp_dt, off_grp_reset, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
         off_dal_gemm, off_al_h, off_al_l, off_S_h, off_S_l, off_G_h, off_G_l, off_Wt_h, off_Wt_l,
         off_St_h, off_St_l, off_recs, off_lrec, off_bmask, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf,
-        off_cen, off_wsum, off_colsum, off_at, total;
+        off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
     int64_t ldk, nbp;
 };
 
@@ -90,15 +90,15 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     size_t n_acc = (size_t)B * (1 + 4 * (size_t)M) + (grad ? (size_t)B * M * M : 0);
     pl->off_acc = take(sizeof(double) * n_acc);
     pl->off_colsum = take(sizeof(double) * (size_t)B * M);
-    pl->ldk = ((int64_t)M + 3) / 4 * 4;
-    pl->nbp = (pl->nb_max + 3) / 4 * 4;
+    pl->ldk = ((int64_t)M + 7) / 8 * 8;
+    pl->nbp = (pl->nb_max + 7) / 8 * 8;
     pl->off_Y = pl->off_Z = pl->off_W = pl->off_dal_gemm = 0;
     pl->off_al_h = pl->off_al_l = pl->off_S_h = pl->off_S_l = pl->off_G_h = pl->off_G_l = 0;
     pl->off_Wt_h = pl->off_Wt_l = pl->off_St_h = pl->off_St_l = 0;
     pl->off_recs = pl->off_lrec = pl->off_bmask = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
-    pl->off_cen = pl->off_wsum = pl->off_at = 0;
+    pl->off_cen = pl->off_wsum = pl->off_at = pl->off_isc = pl->off_colmax = 0;
     if (path == PATH_GEMM) {
-        const size_t h = sizeof(float);
+        const size_t h = 2;   // fp16 operand halves
         const size_t P = (size_t)pl->P;
         pl->off_recs = take(16 * (size_t)(N > 0 ? N : 1));
         pl->off_lrec = take(8 * (size_t)(N > 0 ? N : 1));
@@ -112,6 +112,8 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_cen = take(sizeof(float) * 4 * (size_t)M);
         pl->off_wsum = take(sizeof(double) * (size_t)M);
         pl->off_Y = take(sizeof(float) * nbM);
+        pl->off_isc = take(sizeof(float) * (3 * (size_t)M + 2 * (size_t)pl->nb_max));
+        pl->off_colmax = take(sizeof(uint32_t) * (size_t)M);
         pl->off_al_h = take(h * (size_t)M * pl->ldk);
         pl->off_al_l = take(h * (size_t)M * pl->ldk);
         pl->off_S_h = take(h * (size_t)pl->nb_max * pl->ldk);
@@ -161,16 +163,16 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.Z = at<float>(ws, pl.off_Z);
     p.W = at<float>(ws, pl.off_W);
     p.dal_gemm = at<float>(ws, pl.off_dal_gemm);
-    p.al_h = at<float>(ws, pl.off_al_h);
-    p.al_l = at<float>(ws, pl.off_al_l);
-    p.S_h = at<float>(ws, pl.off_S_h);
-    p.S_l = at<float>(ws, pl.off_S_l);
-    p.G_h = at<float>(ws, pl.off_G_h);
-    p.G_l = at<float>(ws, pl.off_G_l);
-    p.Wt_h = at<float>(ws, pl.off_Wt_h);
-    p.Wt_l = at<float>(ws, pl.off_Wt_l);
-    p.St_h = at<float>(ws, pl.off_St_h);
-    p.St_l = at<float>(ws, pl.off_St_l);
+    p.al_h = at<__half>(ws, pl.off_al_h);
+    p.al_l = at<__half>(ws, pl.off_al_l);
+    p.S_h = at<__half>(ws, pl.off_S_h);
+    p.S_l = at<__half>(ws, pl.off_S_l);
+    p.G_h = at<__half>(ws, pl.off_G_h);
+    p.G_l = at<__half>(ws, pl.off_G_l);
+    p.Wt_h = at<__half>(ws, pl.off_Wt_h);
+    p.Wt_l = at<__half>(ws, pl.off_Wt_l);
+    p.St_h = at<__half>(ws, pl.off_St_h);
+    p.St_l = at<__half>(ws, pl.off_St_l);
     p.recs = at<float4>(ws, pl.off_recs);
     p.lrec = at<float2>(ws, pl.off_lrec);
     p.bmask = at<uint32_t>(ws, pl.off_bmask);
@@ -185,6 +187,12 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.bias_Y = p.cen_S ? p.cen_S + 2 * M : nullptr;
     p.bias_Z = p.cen_S ? p.cen_S + 3 * M : nullptr;
     p.wsum_acc = at<double>(ws, pl.off_wsum);
+    p.isc_al = at<float>(ws, pl.off_isc);
+    p.isc_S = p.isc_al ? p.isc_al + M : nullptr;
+    p.isc_G = p.isc_S ? p.isc_S + pl.nb_max : nullptr;
+    p.isc_Wt = p.isc_G ? p.isc_G + pl.nb_max : nullptr;
+    p.isc_St = p.isc_Wt ? p.isc_Wt + M : nullptr;
+    p.colmax = at<uint32_t>(ws, pl.off_colmax);
     p.ldk = pl.ldk;
     p.nbp = pl.nbp;
     p.C = pl.C;

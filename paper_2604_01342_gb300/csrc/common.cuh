@@ -2,6 +2,7 @@
 // the public C ABI, which is include/hawkes_gb300.h).
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "hawkes_gb300.h"
@@ -72,12 +73,14 @@ struct Problem {
     float* Z;                // [nb_max*M]  alpha . Ghat_b
     float* W;                // [nb_max*M]  per-chunk weights of the dalpha GEMM
     float* dal_gemm;         // [M*M]
-    // tf32 hi/lo operands of the tensor-core GEMMs (fp32 containers)
-    float *al_h, *al_l;      // [M][ldk]       alpha
-    float *S_h, *S_l;        // [nb_max][ldk]  chunk-start states
-    float *G_h, *G_l;        // [nb_max][ldk]
-    float *Wt_h, *Wt_l;      // [M][nbp]       W transposed (chunks contiguous)
-    float *St_h, *St_l;      // [M][nbp]       S^ transposed
+    // fp16 hi/lo operands of the tensor-core GEMMs (rows scaled by powers of two)
+    __half *al_h, *al_l;     // [M][ldk]       alpha
+    __half *S_h, *S_l;       // [nb_max][ldk]  chunk-start states
+    __half *G_h, *G_l;       // [nb_max][ldk]
+    __half *Wt_h, *Wt_l;     // [M][nbp]       W transposed (chunks contiguous)
+    __half *St_h, *St_l;     // [M][nbp]       S^ transposed
+    float *isc_al, *isc_S, *isc_G, *isc_Wt, *isc_St;   // inverse row scales of the operands
+    uint32_t* colmax;        // [M] column maxima scratch of the transposed operands
     // intra-chunk pair kernels
     float4* recs;            // [N]  events bucketed by mark block inside each chunk
     float2* lrec;            // [N]  (ep, column) of the same buckets, each in index order
@@ -95,8 +98,8 @@ struct Problem {
     float* bias_Y;           // [M] alpha . cen_S  (FP64-accumulated)
     float* bias_Z;           // [M] alpha . cen_G
     double* wsum_acc;        // [M] sum_b W[b][i]
-    int64_t ldk;             // M rounded up to 4
-    int64_t nbp;             // nb_max rounded up to 4
+    int64_t ldk;             // M rounded up to 8
+    int64_t nbp;             // nb_max rounded up to 8
     // outputs
     double* out_ll;          // [B]
     float* d_mu;

@@ -21,16 +21,19 @@ namespace hk {
 
 cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int* nl);
 
-// Tensor-core GEMM and tf32 hi/lo splitting (tc_gemm.cu).
-cudaError_t tc_gemm_tf32x3(const float* Ah, const float* Al, int64_t lda, const float* Bh,
-                           const float* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
-                           int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
-                           cudaStream_t s, const float* bias);
-cudaError_t split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd,
-                       int64_t rows, int64_t cols, cudaStream_t s, const float* centre);
-cudaError_t transpose_split_tf32(const float* src, int64_t cols, const int64_t* rows_valid,
-                                 int64_t rows_pad, float* hi, float* lo, int64_t ldd,
-                                 cudaStream_t s, const float* centre);
+// Tensor-core GEMM and fp16 hi/lo splitting of row-scaled operands (tc_gemm.cu).
+cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const __half* Bh,
+                          const __half* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
+                          int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
+                          cudaStream_t s, const float* bias, const float* inv_sa,
+                          const float* inv_sb);
+cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo, int64_t ldd,
+                           int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
+                           const int64_t* rows_valid, float* inv_scale);
+cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
+                                int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
+                                cudaStream_t s, const float* centre, uint32_t* amax_bits,
+                                float* inv_scale);
 
 // Centres of the GEMM operands: the stationary means m_j = n_j / (beta T) of S_j and
 // m_j / beta of G_j (n_j = events of mark j), and the exact products alpha . m in FP64.
@@ -555,26 +558,31 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     ++*nl;
     prof_mark(s, "centres");
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    if ((err = split_tf32(p.alpha, M, p.al_h, p.al_l, p.ldk, M, M, s, nullptr)) != cudaSuccess)
+    const int64_t* nb_dev = p.chunk_base + p.B;   // number of chunks, on the device
+    if ((err = split_f16_rows(p.alpha, M, p.al_h, p.al_l, p.ldk, M, M, s, nullptr, nullptr,
+                              p.isc_al)) != cudaSuccess)
         return err;
     ++*nl;
     prof_mark(s, "split_alpha");
-    if ((err = split_tf32(p.Shat, M, p.S_h, p.S_l, p.ldk, nb, M, s, p.cen_S)) != cudaSuccess)
+    if ((err = split_f16_rows(p.Shat, M, p.S_h, p.S_l, p.ldk, nb, M, s, p.cen_S, nb_dev,
+                              p.isc_S)) != cudaSuccess)
         return err;
     ++*nl;
     prof_mark(s, "split_S");
-    if ((err = tc_gemm_tf32x3(p.S_h, p.S_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Y,
-                              M, (int)nb, (int)M, M, 1, false, p.hdr, s, p.bias_Y)) != cudaSuccess)
+    if ((err = tc_gemm_f16x3(p.S_h, p.S_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Y, M, (int)nb,
+                             (int)M, M, 1, false, p.hdr, s, p.bias_Y, p.isc_S, p.isc_al)) !=
+        cudaSuccess)
         return err;
     ++*nl;
     prof_mark(s, "gemm_Y");
     if (p.grad) {
-        if ((err = split_tf32(p.Ghat, M, p.G_h, p.G_l, p.ldk, nb, M, s, p.cen_G)) != cudaSuccess)
+        if ((err = split_f16_rows(p.Ghat, M, p.G_h, p.G_l, p.ldk, nb, M, s, p.cen_G, nb_dev,
+                                  p.isc_G)) != cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "split_G");
-        if ((err = tc_gemm_tf32x3(p.G_h, p.G_l, p.ldk, p.al_h, p.al_l, p.ldk,
-                                  p.Z, M, (int)nb, (int)M, M, 1, false, p.hdr, s, p.bias_Z)) !=
+        if ((err = tc_gemm_f16x3(p.G_h, p.G_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Z, M, (int)nb,
+                                 (int)M, M, 1, false, p.hdr, s, p.bias_Z, p.isc_G, p.isc_al)) !=
             cudaSuccess)
             return err;
         ++*nl;
@@ -660,23 +668,31 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     if (p.grad) {
         // dalpha_gemm[i][j] = sum_b W[b][i] S^[b][j]: both operands transposed so that
         // the chunk index is the contiguous K dimension; rows past the chunk count are 0
-        const int64_t* nb_dev = p.chunk_base + p.B;
-        if ((err = transpose_split_tf32(p.W, M, nb_dev, p.nbp, p.Wt_h, p.Wt_l, p.nbp, s, nullptr)) !=
-            cudaSuccess)
+        if ((err = transpose_split_f16(p.W, M, nb_dev, p.nbp, p.Wt_h, p.Wt_l, p.nbp, s, nullptr,
+                                       p.colmax, p.isc_Wt)) != cudaSuccess)
             return err;
-        ++*nl;
+        *nl += 2;
         prof_mark(s, "transpose_W");
-        if ((err = transpose_split_tf32(p.Shat, M, nb_dev, p.nbp, p.St_h, p.St_l, p.nbp, s,
-                                        p.cen_S)) != cudaSuccess)
+        if ((err = transpose_split_f16(p.Shat, M, nb_dev, p.nbp, p.St_h, p.St_l, p.nbp, s,
+                                       p.cen_S, p.colmax, p.isc_St)) != cudaSuccess)
             return err;
-        ++*nl;
+        *nl += 2;
         prof_mark(s, "transpose_S");
         cudaMemsetAsync(p.dal_gemm, 0, sizeof(float) * (size_t)M * M, s);
-        const int tiles = (int)(((M + 127) / 128) * ((M + 255) / 256));
-        int splits = (2 * 152 + tiles - 1) / tiles;
-        if ((err = tc_gemm_tf32x3(p.Wt_h, p.Wt_l, p.nbp, p.St_h, p.St_l, p.nbp,
-                                  p.dal_gemm, M, (int)M, (int)M, p.nbp, splits, true, p.hdr, s,
-                                  nullptr)) != cudaSuccess)
+        // split K so that the blocks (one per SM) fill whole waves: minimise
+        // waves x (k-tiles per block + the cost of its atomic output, ~4 k-tiles)
+        const int64_t tiles = ((M + 127) / 128) * ((M + 255) / 256);
+        const int64_t ktiles = (p.nbp + 63) / 64;
+        int splits = 1;
+        int64_t best = -1;
+        for (int64_t sp = 1; sp <= 64 && sp <= ktiles; ++sp) {
+            const int64_t waves = (tiles * sp + sms - 1) / sms;
+            const int64_t cost = waves * ((ktiles + sp - 1) / sp + 4);
+            if (best < 0 || cost < best) { best = cost; splits = (int)sp; }
+        }
+        if ((err = tc_gemm_f16x3(p.Wt_h, p.Wt_l, p.nbp, p.St_h, p.St_l, p.nbp, p.dal_gemm, M,
+                                 (int)M, (int)M, p.nbp, splits, true, p.hdr, s, nullptr,
+                                 p.isc_Wt, p.isc_St)) != cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "gemm_dalpha");

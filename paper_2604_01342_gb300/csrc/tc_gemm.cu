@@ -1,28 +1,32 @@
 // Tensor-core GEMM for sm_103a:  D[m][n] (+)= sum_k A[m][k] B[n][k]
-// with FP32-class accuracy from TF32 operands split in two:
-//     A = Ah + Al,  B = Bh + Bl  (Ah = tf32(A), Al = tf32(A - Ah), both rounded to nearest)
-//     A B^T ~= Ah Bh^T + Ah Bl^T + Al Bh^T        (the Al Bl^T term is ~2^-22 relative)
-// All three products accumulate into one FP32 accumulator in tensor memory.  (A bf16
-// split would run twice as fast but leaves ~1e-5 relative error per product, too much
-// for the shared-decay gradient, which is a small difference of large sums.)
+// with FP32-class accuracy from FP16 operands split in two.  Every row of A and of B is
+// first scaled by a power of two 2^a_m (2^b_n) that brings its largest magnitude into
+// [2^13, 2^14), then split:
+//     A[m][k] 2^a_m = Ah + Al,  Ah = fp16(.), Al = fp16(. - Ah)   (both rounded to nearest)
+//     A B^T ~= 2^-(a_m + b_n) (Ah Bh^T + Ah Bl^T + Al Bh^T)   (the Al Bl^T term is ~2^-22)
+// FP16 carries the same 11 significant bits as TF32 and runs at twice its tensor rate;
+// the row scaling keeps every split part of an entry larger than 2^-17 of its row's
+// maximum in the normal FP16 range, and the scaling and its inverse are exact.  All three
+// products accumulate into FP32 accumulators in tensor memory.
 //
 // Used for the two dense contractions of the chunk-GEMM path: alpha . S^_b over
 // all chunk-start states, and the dalpha contraction W^T S^ over all chunks.
 //
 // One CTA computes one 128 x 256 output tile over a slice of K (split-K with
 // atomic accumulation when there is more than one slice).  One thread issues the TMA
-// loads (cp.async.bulk.tensor, 128-byte swizzle, 32 fp32 of K per row) into a
-// two-stage ring and the tcgen05.mma instructions (kind::tf32, f32 accumulate,
-// M=128, N=256, K=8); tcgen05.commit arrives on the stage's "empty"
+// loads (cp.async.bulk.tensor, 128-byte swizzle, 64 fp16 of K per row) into a
+// two-stage ring and the tcgen05.mma instructions (kind::f16, f32 accumulate,
+// M=128, N=256, K=16); tcgen05.commit arrives on the stage's "empty"
 // mbarrier when the MMAs that read it are done.  The tensor-core accumulator
-// loses precision with the number of accumulation steps (measured: ~1.6e-6 after 64
-// of K, ~2.6e-5 after 1024), so every 32 of K (one k-tile) is accumulated into one of
+// loses precision with the number of accumulation steps (measured with TF32 operands:
+// ~1.6e-6 after 64 of K, ~2.6e-5 after 1024), so every 32 of K is accumulated into one of
 // two TMEM banks and then promoted: eight warps read the finished bank with tcgen05.ld and
-// add it to FP32 registers while the MMAs fill the other bank.  Every mbarrier wait is bounded; on timeout the kernel records an
-// error in the status word, waits (bounded) for its MMAs, frees its tensor memory
-// and returns.
+// add it to FP32 registers while the MMAs fill the other bank.  Every mbarrier wait is
+// bounded; on timeout the kernel records an error in the status word, waits (bounded) for
+// its MMAs, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -33,10 +37,11 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BN = 256;
-constexpr int BK = 32;                  // fp32 elements = 128 bytes = one swizzle row
+constexpr int BK = 64;                  // fp16 elements = 128 bytes = one swizzle row
 constexpr int STAGES = 2;
-constexpr int A_TILE = BM * BK * 4;     // 16 KB
-constexpr int B_TILE = BN * BK * 4;     // 32 KB
+constexpr int A_TILE = BM * BK * 2;     // 16 KB
+constexpr int B_TILE = BN * BK * 2;     // 32 KB
+constexpr int GROUPS_PER_STAGE = 2;     // promotion every 32 of K
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // Ah, Al, Bh, Bl
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t TMEM_COLS = 512;      // two accumulator banks of BN columns
@@ -95,17 +100,17 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* tile) {
     return d;
 }
 
-// Instruction descriptor, kind::tf32: f32 accumulate, tf32 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+// Instruction descriptor, kind::f16: f32 accumulate, fp16 A and B (format 0), both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
@@ -142,12 +147,11 @@ struct Maps {
 // tensor memory and one of its threads issues the TMA loads and the MMAs.
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = (kEpiWarps + 1) * 32;
-constexpr int kGroupTiles = 1;          // k-tiles accumulated in TMEM before promotion
 
 __global__ void __launch_bounds__(kThreads, 1)
-k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim, int Ndim,
-              int k_tiles_total, int k_tiles_per_split, int atomic_out, const float* bias,
-              WsHeader* hdr) {
+k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim, int Ndim,
+             int k_tiles_total, int k_tiles_per_split, int atomic_out, const float* bias,
+             const float* __restrict__ inv_sa, const float* __restrict__ inv_sb, WsHeader* hdr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -164,7 +168,7 @@ k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
     int kt1 = kt0 + k_tiles_per_split;
     if (kt1 > k_tiles_total) kt1 = k_tiles_total;
     const int KT = kt1 > kt0 ? kt1 - kt0 : 0;
-    const int ngroups = (KT + kGroupTiles - 1) / kGroupTiles;
+    const int ngroups = KT * GROUPS_PER_STAGE;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -192,7 +196,7 @@ k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
 
     if (warp == kEpiWarps) {
         if (lane == 0 && KT > 0) {
-            const uint32_t idesc = idesc_tf32(BM, BN);
+            const uint32_t idesc = idesc_f16(BM, BN);
             auto load_stage = [&](int s, int kt) {
                 uint8_t* st = smem + s * STAGE_BYTES;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
@@ -208,13 +212,6 @@ k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
             bool ok = true;
             for (int i = 0; i < KT && ok; ++i) {
                 const int s = i % STAGES;
-                const int g = i / kGroupTiles, bank = g & 1;
-                const bool first_in_group = (i % kGroupTiles) == 0;
-                if (first_in_group && g >= 2) {
-                    // the epilogue must have read this bank's previous group
-                    if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) { ok = false; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                }
                 if (!mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1))) { ok = false; break; }
                 inflight[s] = -1;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -222,17 +219,27 @@ k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
                 const uint64_t dah = sw128_desc(st), dal = sw128_desc(st + A_TILE);
                 const uint64_t dbh = sw128_desc(st + 2 * A_TILE);
                 const uint64_t dbl = sw128_desc(st + 2 * A_TILE + B_TILE);
-                const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
+                for (int h = 0; h < GROUPS_PER_STAGE && ok; ++h) {
+                    const int g = i * GROUPS_PER_STAGE + h, bank = g & 1;
+                    if (g >= 2) {
+                        // the epilogue must have read this bank's previous group
+                        if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    }
+                    const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
+                    constexpr int kSteps = BK / 16 / GROUPS_PER_STAGE;
 #pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk) {
-                    const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 8 fp32 = 32 bytes
-                    const uint32_t acc0 = (!first_in_group || kk > 0) ? 1u : 0u;
-                    mma_tf32(acc_t, dah + off, dbh + off, idesc, acc0);
-                    mma_tf32(acc_t, dah + off, dbl + off, idesc, 1u);
-                    mma_tf32(acc_t, dal + off, dbh + off, idesc, 1u);
+                    for (int kk = 0; kk < kSteps; ++kk) {
+                        // 16 fp16 = 32 bytes along the swizzled row
+                        const uint64_t off = (uint64_t)((h * kSteps + kk) * 32) >> 4;
+                        mma_f16(acc_t, dah + off, dbh + off, idesc, kk > 0 ? 1u : 0u);
+                        mma_f16(acc_t, dah + off, dbl + off, idesc, 1u);
+                        mma_f16(acc_t, dal + off, dbh + off, idesc, 1u);
+                    }
+                    mma_commit(&bank_full[bank]);
                 }
+                if (!ok) break;
                 mma_commit(&empty[s]);
-                if ((i % kGroupTiles) == kGroupTiles - 1 || i == KT - 1) mma_commit(&bank_full[bank]);
                 // refill the stage the previous k-tile used once its MMAs are done
                 if (i >= 1) {
                     const int ps = (i - 1) % STAGES;
@@ -286,6 +293,13 @@ k_gemm_tf32x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim
         }
         if (!good && lane == 0 && hdr) set_status(hdr, HAWKES_ERR_CUDA);
         const int row = m0 + lane_base + lane;
+        // undo the row scalings (exact powers of two), then add the bias
+        const float fa = row < Mdim ? __ldg(inv_sa + row) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 128; ++j) {
+            const int col = n0 + col_base + j;
+            run[j] *= fa * (col < Ndim ? __ldg(inv_sb + col) : 0.f);
+        }
         if (bias && blockIdx.z == 0) {
 #pragma unroll
             for (int j = 0; j < 128; ++j)
@@ -332,41 +346,55 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D fp32 tensor [rows][k] with row stride ld (elements), box {32, box_rows}.
+// 2-D fp16 tensor [rows][k] with row stride ld (elements), box {64, box_rows}.
 static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t k, int64_t ld,
                      int box_rows) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims,
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
+// Power-of-two exponent a with max * 2^a in [2^13, 2^14) (0 for a zero or non-finite max).
+__device__ __forceinline__ int row_exponent(float amax) {
+    if (!(amax > 0.f) || !isfinite(amax)) return 0;
+    int e;
+    frexpf(amax, &e);                    // amax = f 2^e, f in [0.5, 1)
+    return max(-100, min(100, 14 - e));
+}
+
+__device__ __forceinline__ void split_f16(float x, __half& hi, __half& lo) {
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
+}
+
 }  // namespace tc
 
-// D[m][n] (+)= sum_k A[m][k] B[n][k] over m < Mdim, n < Ndim, k < Kdim; A and B given as
-// tf32 hi/lo pairs (fp32 containers) with row strides lda, ldb (elements, multiples of 4;
-// bases 16-byte aligned).
-cudaError_t tc_gemm_tf32x3(const float* Ah, const float* Al, int64_t lda, const float* Bh,
-                           const float* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
-                           int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
-                           cudaStream_t s, const float* bias) {
+// D[m][n] (+)= inv_sa[m] inv_sb[n] sum_k A[m][k] B[n][k] over m < Mdim, n < Ndim, k < Kdim;
+// A and B given as fp16 hi/lo pairs of the scaled rows, with row strides lda, ldb
+// (elements, multiples of 8; bases 16-byte aligned), inv_sa / inv_sb the inverse scales.
+cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const __half* Bh,
+                          const __half* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
+                          int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
+                          cudaStream_t s, const float* bias, const float* inv_sa,
+                          const float* inv_sb) {
     using namespace tc;
     if (Mdim <= 0 || Ndim <= 0 || Kdim <= 0) return cudaSuccess;
-    if ((lda % 4) || (ldb % 4)) return cudaErrorInvalidValue;
+    if ((lda % 8) || (ldb % 8)) return cudaErrorInvalidValue;
     Maps maps;
     if (!make_map(&maps.ah, Ah, Mdim, Kdim, lda, BM) || !make_map(&maps.al, Al, Mdim, Kdim, lda, BM) ||
         !make_map(&maps.bh, Bh, Ndim, Kdim, ldb, BN) || !make_map(&maps.bl, Bl, Ndim, Kdim, ldb, BN))
         return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tf32x3,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM_BYTES);
         if (e != cudaSuccess) return e;
@@ -379,56 +407,92 @@ cudaError_t tc_gemm_tf32x3(const float* Ah, const float* Al, int64_t lda, const 
     splits = (kt_total + per - 1) / per;
     dim3 grid((unsigned)((Ndim + BN - 1) / BN), (unsigned)((Mdim + BM - 1) / BM), (unsigned)splits);
     const int atomic_out = (splits > 1 || accumulate) ? 1 : 0;
-    k_gemm_tf32x3<<<grid, kThreads, SMEM_BYTES, s>>>(maps, D, ldd, Mdim, Ndim, kt_total, per,
-                                                 atomic_out, bias, hdr);
+    k_gemm_f16x3<<<grid, kThreads, SMEM_BYTES, s>>>(maps, D, ldd, Mdim, Ndim, kt_total, per,
+                                                atomic_out, bias, inv_sa, inv_sb, hdr);
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - hi);
-}
-
-// Split an FP32 matrix [rows][cols] (row stride lds), minus an optional per-column
-// centre, into tf32 hi/lo [rows][ldd].
-__global__ void k_split_tf32(const float* __restrict__ src, int64_t lds, float* hi, float* lo,
-                             int64_t ldd, int64_t rows, int64_t cols, const float* centre) {
-    const int64_t n = rows * cols;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / cols, c = i % cols;
-        float h, l;
-        split_tf32(src[r * lds + c] - (centre ? centre[c] : 0.f), h, l);
-        hi[r * ldd + c] = h;
-        lo[r * ldd + c] = l;
+// One warp per row r < rows of an FP32 matrix [rows][cols] (row stride lds), minus an
+// optional per-column centre: the row's scale exponent from its largest magnitude, the
+// fp16 hi/lo split of the scaled row into [rows][ldd], and inv_scale[r] = 2^-a.  Rows at
+// or past *rows_valid (when given) are written as zeros.
+__global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __half* hi,
+                                 __half* lo, int64_t ldd, int64_t rows, int64_t cols,
+                                 const float* __restrict__ centre, const int64_t* rows_valid,
+                                 float* inv_scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nvalid = rows_valid ? *rows_valid : rows;
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+        const float* sr = src + r * lds;
+        __half* hr = hi + r * ldd;
+        __half* lr = lo + r * ldd;
+        if (r >= nvalid) {
+            for (int64_t c = lane; c < cols; c += 32) hr[c] = lr[c] = __float2half_rn(0.f);
+            if (lane == 0) inv_scale[r] = 1.f;
+            continue;
+        }
+        float amax = 0.f;
+        for (int64_t c = lane; c < cols; c += 32)
+            amax = fmaxf(amax, fabsf(sr[c] - (centre ? centre[c] : 0.f)));
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        const int a = tc::row_exponent(amax);
+        const float sc = ldexpf(1.f, a);
+        for (int64_t c = lane; c < cols; c += 32) {
+            __half h, l;
+            tc::split_f16((sr[c] - (centre ? centre[c] : 0.f)) * sc, h, l);
+            hr[c] = h;
+            lr[c] = l;
+        }
+        if (lane == 0) inv_scale[r] = ldexpf(1.f, -a);
     }
 }
 
-cudaError_t split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd,
-                       int64_t rows, int64_t cols, cudaStream_t s, const float* centre) {
+cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo, int64_t ldd,
+                           int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
+                           const int64_t* rows_valid, float* inv_scale) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
-    int64_t n = rows * cols;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    k_split_tf32<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, centre);
+    int64_t blocks = (rows + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_split_f16_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, centre,
+                                                      rows_valid, inv_scale);
     return cudaGetLastError();
 }
 
-// dst[c][r] = split(src[r][c] - centre[c]) for r < rows_pad (zero for r >= *rows_valid):
-// transposes a chunk-major [rows][cols] FP32 matrix into cols x rows tf32 hi/lo with
-// chunks contiguous.
-__global__ void k_transpose_split_tf32(const float* __restrict__ src, int64_t cols,
-                                       const int64_t* rows_valid, int64_t rows_pad, float* hi,
-                                       float* lo, int64_t ldd, const float* centre) {
+// Largest |src[r][c] - centre[c]| over the valid rows of every column c, as the bits of a
+// non-negative float (so that an unsigned maximum orders them); amax_bits starts at 0.
+__global__ void k_colmax(const float* __restrict__ src, int64_t cols, const int64_t* rows_valid,
+                         const float* __restrict__ centre, uint32_t* amax_bits) {
+    const int64_t nvalid = *rows_valid;
+    const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    if (c >= cols) return;
+    const float cc = centre ? centre[c] : 0.f;
+    float m = 0.f;
+    for (int64_t r = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; r < nvalid;
+         r += (int64_t)gridDim.y * blockDim.y)
+        m = fmaxf(m, fabsf(src[r * cols + c] - cc));
+    if (m > 0.f) atomicMax(amax_bits + c, __float_as_uint(m));
+}
+
+// dst[c][r] = split(2^a_c (src[r][c] - centre[c])) for r < rows_pad (zero for
+// r >= *rows_valid), a_c from the column's largest magnitude: transposes a chunk-major
+// [rows][cols] FP32 matrix into cols x rows fp16 hi/lo with chunks contiguous, and
+// inv_scale[c] = 2^-a_c.
+__global__ void k_transpose_split_f16(const float* __restrict__ src, int64_t cols,
+                                      const int64_t* rows_valid, int64_t rows_pad, __half* hi,
+                                      __half* lo, int64_t ldd, const float* centre,
+                                      const uint32_t* __restrict__ amax_bits, float* inv_scale) {
     __shared__ float tile[32][33];
+    __shared__ float sc[32];
     const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
     const int64_t nvalid = *rows_valid;
+    if (threadIdx.y == 0) {
+        const int64_t c = c0 + threadIdx.x;
+        const int a = c < cols ? tc::row_exponent(__uint_as_float(amax_bits[c])) : 0;
+        sc[threadIdx.x] = ldexpf(1.f, a);
+        if (blockIdx.y == 0 && c < cols) inv_scale[c] = ldexpf(1.f, -a);
+    }
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int64_t r = r0 + i, c = c0 + threadIdx.x;
         tile[i][threadIdx.x] =
@@ -438,20 +502,29 @@ __global__ void k_transpose_split_tf32(const float* __restrict__ src, int64_t co
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int64_t c = c0 + i, r = r0 + threadIdx.x;
         if (c < cols && r < rows_pad) {
-            float h, l;
-            split_tf32(tile[threadIdx.x][i], h, l);
+            __half h, l;
+            tc::split_f16(tile[threadIdx.x][i] * sc[i], h, l);
             hi[c * ldd + r] = h;
             lo[c * ldd + r] = l;
         }
     }
 }
 
-cudaError_t transpose_split_tf32(const float* src, int64_t cols, const int64_t* rows_valid,
-                                 int64_t rows_pad, float* hi, float* lo, int64_t ldd,
-                                 cudaStream_t s, const float* centre) {
-    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows_pad + 31) / 32));
-    k_transpose_split_tf32<<<grid, dim3(32, 8), 0, s>>>(src, cols, rows_valid, rows_pad, hi, lo,
-                                                        ldd, centre);
+cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
+                                int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
+                                cudaStream_t s, const float* centre, uint32_t* amax_bits,
+                                float* inv_scale) {
+    if (cols <= 0 || rows_pad <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(amax_bits, 0, sizeof(uint32_t) * (size_t)cols, s);
+    if (e != cudaSuccess) return e;
+    const int64_t cb = (cols + 31) / 32;
+    int64_t rb = (152 * 8 + cb - 1) / cb;
+    if (rb < 1) rb = 1;
+    k_colmax<<<dim3((unsigned)cb, (unsigned)rb), dim3(32, 8), 0, s>>>(src, cols, rows_valid,
+                                                                     centre, amax_bits);
+    dim3 grid((unsigned)cb, (unsigned)((rows_pad + 31) / 32));
+    k_transpose_split_f16<<<grid, dim3(32, 8), 0, s>>>(src, cols, rows_valid, rows_pad, hi, lo,
+                                                       ldd, centre, amax_bits, inv_scale);
     return cudaGetLastError();
 }
 
@@ -459,22 +532,23 @@ cudaError_t transpose_split_tf32(const float* src, int64_t cols, const int64_t* 
 
 // Test hook (declared in no public header): the same GEMM on caller buffers, so a GPU
 // test can compare it with a reference product.  D[m][n] = sum_k A[m][k] B[n][k] from
-// FP32 A [M][K] and B [N][K]; scratch must hold 2*(M+N)*ld floats (ld = K rounded up to
-// 4).  Returns 0 on success.
+// FP32 A [M][K] and B [N][K]; scratch must hold 2*(M+N)*ld halves (ld = K rounded up to
+// 8) followed by M+N floats.  Returns 0 on success.
 extern "C" int hawkes_test_tc_gemm(const float* A, const float* B, float* D, int M, int N,
                                    int K, int splits, void* scratch, void* stream) {
     using namespace hk;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t ld = (K + 3) / 4 * 4;
-    float* p = (float*)scratch;
-    float *Ah = p, *Al = Ah + (int64_t)M * ld, *Bh = Al + (int64_t)M * ld,
-          *Bl = Bh + (int64_t)N * ld;
-    if (split_tf32(A, K, Ah, Al, ld, M, K, s, nullptr) != cudaSuccess) return 1;
-    if (split_tf32(B, K, Bh, Bl, ld, N, K, s, nullptr) != cudaSuccess) return 1;
+    const int64_t ld = (K + 7) / 8 * 8;
+    __half* p = (__half*)scratch;
+    __half *Ah = p, *Al = Ah + (int64_t)M * ld, *Bh = Al + (int64_t)M * ld,
+           *Bl = Bh + (int64_t)N * ld;
+    float* inv_a = (float*)(Bl + (int64_t)N * ld);
+    float* inv_b = inv_a + M;
+    if (split_f16_rows(A, K, Ah, Al, ld, M, K, s, nullptr, nullptr, inv_a) != cudaSuccess) return 1;
+    if (split_f16_rows(B, K, Bh, Bl, ld, N, K, s, nullptr, nullptr, inv_b) != cudaSuccess) return 1;
     if (splits > 1) cudaMemsetAsync(D, 0, sizeof(float) * (size_t)M * N, s);
-    return tc_gemm_tf32x3(Ah, Al, ld, Bh, Bl, ld, D, N, M, N, K, splits, false, nullptr, s,
-                          nullptr) ==
-                   cudaSuccess
+    return tc_gemm_f16x3(Ah, Al, ld, Bh, Bl, ld, D, N, M, N, K, splits, false, nullptr, s,
+                         nullptr, inv_a, inv_b) == cudaSuccess
                ? 0
                : 2;
 }

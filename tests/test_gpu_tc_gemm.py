@@ -1,5 +1,6 @@
-"""The tcgen05 GEMM (tf32x3 split, TMA, tensor-memory accumulator) against an
-FP64 product on the GPU.  Error bound: |D - AB^T| <= tol * (|A| |B|^T)."""
+"""The tcgen05 GEMM (row-scaled fp16 hi/lo split, three products, TMA, tensor-memory
+accumulator) against an FP64 product on the GPU.  Error bound:
+|D - AB^T| <= tol * (|A| |B|^T)."""
 import ctypes
 
 import numpy as np
@@ -32,8 +33,8 @@ def test_tc_gemm_matches_fp64(lib, M, N, K, splits, signed):
     B = (torch.rand(N, K, device="cuda", generator=g) * (1 - lo) + lo).float()
     A[0, :3] = torch.tensor([1e-6, 3.0e4, -2.5 if signed else 2.5], device="cuda")
     D = torch.full((M, N), float("nan"), device="cuda")
-    ld = (K + 3) // 4 * 4
-    scratch = torch.empty(2 * (M + N) * ld * 4 + 256, dtype=torch.uint8, device="cuda")
+    ld = (K + 7) // 8 * 8
+    scratch = torch.empty(2 * (M + N) * ld * 2 + 4 * (M + N), dtype=torch.uint8, device="cuda")
     rc = lib.hawkes_test_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, splits,
                                  scratch.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert rc == 0
