@@ -84,7 +84,9 @@ struct Problem {
     // intra-chunk pair kernels
     float4* recs;            // [N]  events bucketed by mark block inside each chunk
     float2* lrec;            // [N]  (ep, column) of the same buckets, each in index order
-    uint32_t* bmask;         // [nb_max * P * W] bucket membership bits, W = ceil(C / 32)
+    uint2* bmask;            // [nb_max * P * W] bucket membership words and the members
+                             // in the words before, W = ceil(C / 32)
+    int4* kprep;             // [N]  backward row-group data of every bucket slot
     float* at;               // [P*P*128*128] alpha in tile-major order
     int32_t* bstart;         // [nb_max * (P+1)] bucket offsets inside each chunk
     uint8_t* wide;           // [nb_max] chunk spans too wide for the factorised weights

@@ -92,7 +92,7 @@ __global__ void k_centres(Problem p, int have_counts) {
 constexpr int kTile = 128;
 constexpr int kTileLd = kTile + 1;      // padded row stride against bank conflicts
 constexpr float kWideLimit = 64.f;      // beta * span above which sums of exp(+beta delta) may overflow
-constexpr int kFwdChunksPerItem = 64;
+constexpr int kFwdChunksPerItem = 256;
 constexpr int kStage = 64;              // source records staged per warp at a time
 constexpr int kFlushChunks = 64;       // cost of flushing one dalpha tile, in chunks of work
 // backward per-warp scratch: 32 item ranges, then up to kLStage staged sources (the
@@ -130,9 +130,10 @@ __global__ void k_alpha_tiles(Problem p, float* at) {
 // One block per chunk: bucket the chunk's events by mark block, each bucket sorted by
 // (position of the mark in its block, index in the chunk) in recs; the same buckets in
 // index order in lrec (source side of the backward pairs), and the membership bits of
-// every bucket over the chunk's event indices in bmask.
+// every bucket over the chunk's event indices in bmask, each 32-bit word with the number
+// of members in the words before it.
 __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2* lrec,
-                                                uint32_t* bmask, int32_t* bstart, uint8_t* wide) {
+                                                uint2* bmask, int32_t* bstart, uint8_t* wide) {
     extern __shared__ int32_t sm_i[];
     const int P = p.P, W = (p.C + 31) >> 5;
     int32_t* cnt = sm_i;                  // [P]
@@ -167,7 +168,11 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             base[P] = acc;
             bstart[b * (P + 1) + P] = acc;
         }
-        for (int q = threadIdx.x; q < P * W; q += blockDim.x) bmask[b * P * W + q] = msk[q];
+        for (int e = threadIdx.x; e < P * W; e += blockDim.x) {
+            int before = 0;
+            for (int w = e - e % W; w < e; ++w) before += __popc(msk[w]);
+            bmask[b * P * W + e] = make_uint2(msk[e], (uint32_t)before);
+        }
         __syncthreads();
         // unordered placement of the sort keys (position << 16 | index)
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -268,15 +273,23 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const 
                             stage[q] = unpack_rec(__ldg(recs + s0 + l0 + lb + q));
                         __syncwarp();
                         if (!isw) {
-#pragma unroll 4
-                            for (int l = 0; l < ns; ++l) {
-                                const float4 rl = stage[l];          // (delta, ep, column, index)
-                                const float v = rl.y * trow[__float_as_int(rl.z)];
-                                if (__float_as_int(rl.w) < ik) {
-                                    a += v;
-                                    d = fmaf(rl.x, v, d);
-                                }
+                            float a2 = 0.f, d2 = 0.f;
+                            int l = 0;
+#pragma unroll 2
+                            for (; l + 1 < ns; l += 2) {
+                                const float4 r0 = stage[l], r1 = stage[l + 1];
+                                const float v0 = r0.y * trow[__float_as_int(r0.z)];
+                                const float v1 = r1.y * trow[__float_as_int(r1.z)];
+                                if (__float_as_int(r0.w) < ik) { a += v0; d = fmaf(r0.x, v0, d); }
+                                if (__float_as_int(r1.w) < ik) { a2 += v1; d2 = fmaf(r1.x, v1, d2); }
                             }
+                            if (l < ns) {
+                                const float4 r0 = stage[l];
+                                const float v0 = r0.y * trow[__float_as_int(r0.z)];
+                                if (__float_as_int(r0.w) < ik) { a += v0; d = fmaf(r0.x, v0, d); }
+                            }
+                            a += a2;
+                            d += d2;
                         } else {
                             for (int l = 0; l < ns; ++l) {
                                 const float4 rl = stage[l];
@@ -301,6 +314,48 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const 
     }
 }
 
+// Row groups of the backward pairs, once per (chunk, bucket) instead of once per tile:
+// for every 32-lane group of a bucket (sorted by (row, index)), u_k = w_k em_k, U_k = sum
+// of u over the lane's row group from k on, and the index of the previous event of the
+// same row in the group (-1 if none): kprep[slot] = (row * kTileLd, U_k, index, previous).
+// Chunks too wide for the factorised weights are skipped (their pairs take one exp each).
+__global__ void __launch_bounds__(256) k_bwd_prep(Problem p, const float4* __restrict__ recs,
+                                                  const int32_t* __restrict__ bstart,
+                                                  const uint8_t* __restrict__ wide,
+                                                  const float* __restrict__ wbuf, int4* kprep) {
+    if (failed(p.hdr)) return;
+    const int P = p.P, C = p.C, lane = threadIdx.x & 31;
+    const int64_t nb = num_chunks(p);
+    const int64_t nseg = nb * P;
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t sgi = blockIdx.x * wpb + (threadIdx.x >> 5); sgi < nseg; sgi += (int64_t)gridDim.x * wpb) {
+        const int64_t b = sgi / P;
+        const int I = (int)(sgi % P);
+        if (wide[b]) continue;
+        const int64_t s0 = b * C;
+        const int k0 = bstart[b * (P + 1) + I], k1 = bstart[b * (P + 1) + I + 1];
+        for (int kb = k0; kb < k1; kb += 32) {
+            const int kk = kb + lane;
+            const bool have = kk < k1;
+            const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int ik = have ? rec_idx(rk) : -1;
+            const int row = have ? rec_pos(rk) : -1 - lane;   // distinct for idle lanes
+            const float wk = have ? wbuf[s0 + ik] : 0.f;
+            float U = wk * rk.y;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float up = __shfl_down_sync(HK_FULL, U, o);
+                const int rowo = __shfl_down_sync(HK_FULL, row, o);
+                if (lane + o < 32 && rowo == row) U += up;
+            }
+            const int prow = __shfl_up_sync(HK_FULL, row, 1);
+            const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
+            const int lo = (lane > 0 && prow == row) ? pidx : -1;
+            if (have) kprep[s0 + kk] = make_int4(row * kTileLd, __float_as_int(U), ik, lo);
+        }
+    }
+}
+
 // Backward pairs: dalpha_intra[c_k][c_l] += w_k P_kl over the pairs of tile (I, J).
 // Bucket I is sorted by (row, index), so lanes holding events of the same row are
 // adjacent.  With u_k = w_k em_k and U_k = sum of u over the lane's row group from k on
@@ -314,7 +369,8 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const 
 // pair over all (k, l) instead.
 __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const float4* __restrict__ recs,
                                                    const float2* __restrict__ lrec,
-                                                   const uint32_t* __restrict__ bmask,
+                                                   const uint2* __restrict__ bmask,
+                                                   const int4* __restrict__ kprep,
                                                    const int32_t* __restrict__ bstart,
                                                    const uint8_t* __restrict__ wide,
                                                    const float* __restrict__ wbuf,
@@ -343,15 +399,10 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
         const int l0 = bs[J], nJ = bs[J + 1] - l0;
         if (k0 == k1 || nJ == 0) continue;
         const bool isw = wide[b] != 0;
-        // membership bits of bucket J (word w on lane w) and the counts before each word
-        const uint32_t mw = lane < W ? __ldg(bmask + ((int64_t)b * P + J) * W + lane) : 0u;
-        int cw = __popc(mw);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(HK_FULL, cw, o);
-            if (lane >= o) cw += x;
-        }
-        cw -= __popc(mw);
+        // membership bits of bucket J (word w on lane w) and the members before each word
+        const uint2 mwc = lane < W ? __ldg(bmask + ((int64_t)b * P + J) * W + lane) : make_uint2(0u, 0u);
+        const uint32_t mw = mwc.x;
+        const int cw = (int)mwc.y;
         const bool staged = !isw && nJ <= kLStage;
         if (staged) {
             __syncwarp();
@@ -361,22 +412,10 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
         for (int kb = k0; kb < k1; kb += 32) {
             const int kk = kb + lane;
             const bool have = kk < k1;
-            const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int ik = have ? rec_idx(rk) : -1;
-            const int row = have ? rec_pos(rk) : -1 - lane;   // distinct for idle lanes
-            const float wk = have ? wbuf[s0 + ik] : 0.f;
             if (!isw) {
-                // segmented suffix sum of u over equal rows inside the lane group
-                float U = wk * rk.y;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float up = __shfl_down_sync(HK_FULL, U, o);
-                    const int rowo = __shfl_down_sync(HK_FULL, row, o);
-                    if (lane + o < 32 && rowo == row) U += up;
-                }
-                const int prow = __shfl_up_sync(HK_FULL, row, 1);
-                const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
-                const int lo = (lane > 0 && prow == row) ? pidx : -1;
+                const int4 kp = have ? __ldg(kprep + s0 + kk) : make_int4(0, 0, -1, -1);
+                const int ik = kp.z, lo = kp.w;
+                const float U = __int_as_float(kp.y);
                 // ranks in bucket J (index order) of the sources before ik and before lo
                 const int xh = have ? ik : 0, xl = lo > 0 ? lo : 0;
                 const int bk = __shfl_sync(HK_FULL, cw, xh >> 5) +
@@ -399,7 +438,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                 __syncwarp();
                 if (n > 0)
                     kd[__popc(amask & ((1u << lane) - 1u))] =
-                        make_int4(row * kTileLd, __float_as_int(U), (lo >= 0 ? ak : 0) - excl, incl);
+                        make_int4(kp.x, __float_as_int(U), (lo >= 0 ? ak : 0) - excl, incl);
                 __syncwarp();
                 // items [g0, g1) of this lane, L per lane; the owner of g0 is the first lane
                 // whose last item is >= g0
@@ -437,7 +476,10 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                 }
                 __syncwarp();
             } else {
-                float* drow = dtile + (have ? row : 0) * kTileLd;
+                const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int ik = have ? rec_idx(rk) : -1;
+                const float wk = have ? wbuf[s0 + ik] : 0.f;
+                float* drow = dtile + (have ? rec_pos(rk) : 0) * kTileLd;
                 for (int lb = 0; lb < nJ; lb += kStage) {
                     const int ns = min(kStage, nJ - lb);
                     __syncwarp();
@@ -609,7 +651,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     {
-        // forward pairs: work items (row block, 64 chunks) from a counter in the header
+        // forward pairs: work items (row block, kFwdChunksPerItem chunks) from a counter in the header
         const size_t smem = sizeof(float) * kTile * kTileLd + sizeof(float4) * kStage * kPairWarps;
         err = cudaFuncSetAttribute(k_pairs_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
@@ -637,6 +679,15 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (p.grad) {
+        int64_t blocks = (nb * P + 7) / 8;
+        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+        k_bwd_prep<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, p.recs, p.bstart, p.wide,
+                                                                        p.wbuf, p.kprep);
+        ++*nl;
+        prof_mark(s, "bwd_prep");
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    if (p.grad) {
         // backward pairs: tile (I, J) x chunk range
         const size_t smem = sizeof(float) * kTile * kTileLd + kBwdWarpScratch * kPairWarps;
         err = cudaFuncSetAttribute(k_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -660,7 +711,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         R = (nb + per - 1) / per;
         if (R < 1) R = 1;
         k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), kPairThreads, smem, s>>>(
-            p, p.recs, p.lrec, p.bmask, p.bstart, p.wide, p.wbuf, (int)per);
+            p, p.recs, p.lrec, p.bmask, p.kprep, p.bstart, p.wide, p.wbuf, (int)per);
         ++*nl;
         prof_mark(s, "pairs_bwd");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
