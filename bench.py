@@ -410,27 +410,30 @@ def run_ours(args):
 
 
 def kernel_work(name, N, M, C):
-    """(bound, algorithmic work per launch, unit) of each kernel of one step.
+    """(bound, algorithmic work per launch) of each kernel of one step.
 
     HBM kernels count the bytes the algorithm must move; tensor kernels the flops of
-    one product (the TF32 hi/lo split issues three); ALU kernels FP32 operations."""
+    one product (the fp16 hi/lo split issues three); shared-memory kernels the bytes of
+    shared memory the pairs must touch: per forward pair one 4-byte alpha gather plus its
+    share of the broadcast 16-byte source record (32 lanes), per backward pair one 4-byte
+    read and one 4-byte write of the dalpha tile; ALU kernels FP32 operations."""
     nb = (N + C - 1) // C
     pairs = N * (C - 1) / 2.0                  # pairs (k, l) inside chunks, l before k
     table = {
         "validate_events": ("hbm", 12.0 * N),
         "scan_reduce": ("hbm", 12.0 * N),
         "scan_states": ("hbm", 12.0 * N + 8.0 * M * nb),
-        "split_S": ("hbm", 4.0 * M * nb * 3),
-        "split_G": ("hbm", 4.0 * M * nb * 3),
+        "split_S": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
+        "split_G": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
         "bucket": ("hbm", 12.0 * N + 16.0 * N),
         "epilogue": ("hbm", 12.0 * N + 8.0 * N + 12.0 * N),
-        "transpose_W": ("hbm", 4.0 * M * nb * 3),
-        "transpose_S": ("hbm", 4.0 * M * nb * 3),
+        "transpose_W": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
+        "transpose_S": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
         "gemm_Y": ("tensor", 2.0 * M * M * nb),
         "gemm_Z": ("tensor", 2.0 * M * M * nb),
         "gemm_dalpha": ("tensor", 2.0 * M * M * nb),
-        "pairs_fwd": ("alu", 5.0 * pairs),
-        "pairs_bwd": ("alu", 2.0 * pairs),
+        "pairs_fwd": ("smem", (4.0 + 16.0 / 32.0) * pairs),
+        "pairs_bwd": ("smem", 8.0 * pairs),
         "walk": ("alu", 2.0 * 3.0 * N * M),
     }
     return table.get(name)
@@ -443,7 +446,8 @@ def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
     C = args.chunk or 192
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, FMA = 2 flops
-    tf32_peak = bf16 / 2.0                                # dense TF32 = BF16 / 2 (nominal ratio)
+    f16_peak = bf16                                       # dense FP16 = BF16 (nominal ratio 1)
+    smem_peak = 152 * 128 * sm_max * 1e6 / 1e9            # GB/s: 128 B per clock per SM
     rows = {}
     for name, ms in kern_ms.items():
         w = kernel_work(name, N, M, C)
@@ -453,7 +457,9 @@ def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
         if bound == "hbm":
             ach, peak, unit = work / (ms * 1e-3) / 1e9, hbm, "GB/s"
         elif bound == "tensor":
-            ach, peak, unit = work / (ms * 1e-3) / 1e12, tf32_peak, "TFLOP/s"
+            ach, peak, unit = work / (ms * 1e-3) / 1e12, f16_peak, "TFLOP/s"
+        elif bound == "smem":
+            ach, peak, unit = work / (ms * 1e-3) / 1e9, smem_peak, "GB/s"
         else:
             ach, peak, unit = work / (ms * 1e-3) / 1e12, fp32_peak, "TFLOP/s"
         rows[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
@@ -466,7 +472,8 @@ def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
     out = {"kernel": name, "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
            "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
            "peak_source": {"hbm": f"{src} HBM copy bandwidth",
-                           "tensor": f"{src} bf16 dense / 2 (TF32), burst",
+                           "tensor": f"{src} bf16 dense (= fp16 dense), burst",
+                           "smem": "shared memory: 152 SMs x 128 B/clock x max SM clock",
                            "alu": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}[dom["bound"]],
            "per_kernel": {k: {"frac": round(v["frac"], 4), "ms": round(v["ms"], 4),
                               "bound": v["bound"]} for k, v in rows.items()}}

@@ -37,9 +37,10 @@ struct Plan {
     size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
         off_grp_dt, off_grp_reset, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
         off_dal_gemm, off_al_h, off_al_l, off_S_h, off_S_l, off_G_h, off_G_l, off_Wt_h, off_Wt_l,
-        off_St_h, off_St_l, off_recs, off_lrec, off_bmask, off_kprep, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf,
+        off_St_h, off_St_l, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf,
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
     int64_t ldk, nbp;
+    int dal_parts_max;
 };
 
 // Returns 0 and fills the plan, or a hawkes_status.
@@ -95,8 +96,9 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->off_Y = pl->off_Z = pl->off_W = pl->off_dal_gemm = 0;
     pl->off_al_h = pl->off_al_l = pl->off_S_h = pl->off_S_l = pl->off_G_h = pl->off_G_l = 0;
     pl->off_Wt_h = pl->off_Wt_l = pl->off_St_h = pl->off_St_l = 0;
-    pl->off_recs = pl->off_lrec = pl->off_bmask = pl->off_kprep = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
+    pl->off_recs = pl->off_lrec = pl->off_bmask = pl->off_kprep = pl->off_dal_part = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
     pl->off_cen = pl->off_wsum = pl->off_at = pl->off_isc = pl->off_colmax = 0;
+    pl->dal_parts_max = 0;
     if (path == PATH_GEMM) {
         const size_t h = 2;   // fp16 operand halves
         const size_t P = (size_t)pl->P;
@@ -104,6 +106,15 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_lrec = take(8 * (size_t)(N > 0 ? N : 1));
         pl->off_bmask = take(sizeof(uint2) * (size_t)pl->nb_max * P * (size_t)((C + 31) / 32));
         if (grad) pl->off_kprep = take(16 * (size_t)(N > 0 ? N : 1));
+        // backward pair tiles (ceil(M / P) square each): up to 2560 / P^2 chunk ranges per
+        // tile, at most one per chunk, at least one
+        {
+            int64_t r = 2560 / (int64_t)(P * P);
+            if (r > pl->nb_max) r = pl->nb_max;
+            pl->dal_parts_max = (int)(r > 0 ? r : 1);
+            const size_t tr = ((size_t)M + P - 1) / P;
+            if (grad) pl->off_dal_part = take(sizeof(float) * (size_t)pl->dal_parts_max * P * P * tr * tr);
+        }
         pl->off_at = take(sizeof(float) * P * P * 128 * 128);
         pl->off_bstart = take(sizeof(int32_t) * (size_t)pl->nb_max * (P + 1));
         pl->off_wide = take((size_t)pl->nb_max);
@@ -178,6 +189,9 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.lrec = at<float2>(ws, pl.off_lrec);
     p.bmask = at<uint2>(ws, pl.off_bmask);
     p.kprep = at<int4>(ws, pl.off_kprep);
+    p.dal_part = at<float>(ws, pl.off_dal_part);
+    p.dal_parts_max = pl.dal_parts_max;
+    p.dal_parts = 0;
     p.at = at<float>(ws, pl.off_at);
     p.bstart = at<int32_t>(ws, pl.off_bstart);
     p.wide = at<uint8_t>(ws, pl.off_wide);

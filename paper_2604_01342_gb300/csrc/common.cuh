@@ -64,6 +64,9 @@ struct Problem {
     double* ll_acc;          // [B]   sum of log lambda
     double* dmu_acc;         // [B*M] sum of w over events of each mark
     double* dal_acc;         // [B*M*M]
+    float* dal_part;         // [dal_parts][P*P][128*128] backward pair tiles of the chunk-GEMM path
+    int32_t dal_parts;       // chunk ranges of the backward pair kernel (set at launch)
+    int32_t dal_parts_max;   // capacity of dal_part in ranges
     double* dbe_acc;         // [B*M] excitation part of dbeta
     double* E_acc;           // [B*M] sum (1 - exp(-beta (T - t))) per source
     double* F_acc;           // [B*M] sum (T - t) exp(-beta (T - t)) per source

@@ -71,8 +71,10 @@ __global__ void k_finalize_vec(Problem p, const double* colsum) {
 
 // dalpha for all sequences, elementwise.
 // mode 0: X = dal_acc (already carries beta_j);
-// mode 1: X = beta * (dal_gemm + m_j wsum_i + dal_acc)  (chunk-GEMM path, one shared beta;
-//         the GEMM ran on S^ - m, so m_j sum_b W[b][i] restores the centre)
+// mode 1: X = beta * (dal_gemm + m_j wsum_i + sum_r part_r[i][j])  (chunk-GEMM path, one
+//         shared beta; the GEMM ran on S^ - m, so m_j sum_b W[b][i] restores the centre;
+//         part_r are the intra-chunk pair tiles of chunk range r (ceil(M / P) square,
+//         tile-major), summed in range order)
 __global__ void k_finalize_alpha(Problem p, int mode) {
     const int M = p.M;
     const bool bad = failed(p.hdr);
@@ -87,8 +89,12 @@ __global__ void k_finalize_alpha(Problem p, int mode) {
             x = p.dal_acc[e];
         } else {
             const float beta = p.beta[0];
-            x = (double)beta * ((double)p.dal_gemm[ij] +
-                                (double)p.cen_S[j] * p.wsum_acc[ij / M] + p.dal_acc[ij]);
+            const int i = (int)(ij / M), P = p.P, TR = (M + P - 1) / P;
+            const int64_t at = (((int64_t)(i % P) * P + (j % P)) * TR + (i / P)) * TR + (j / P);
+            const int64_t stride = (int64_t)P * P * TR * TR;
+            double pairs = 0.0;
+            for (int r = 0; r < p.dal_parts; ++r) pairs += (double)p.dal_part[r * stride + at];
+            x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] + pairs);
         }
         const double v = x - p.E_acc[s * M + j];
         p.d_alpha[e] = bad ? (float)nanv : (float)v;

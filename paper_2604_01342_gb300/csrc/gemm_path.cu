@@ -94,7 +94,7 @@ constexpr int kTileLd = kTile + 1;      // padded row stride against bank confli
 constexpr float kWideLimit = 64.f;      // beta * span above which sums of exp(+beta delta) may overflow
 constexpr int kFwdChunksPerItem = 256;
 constexpr int kStage = 64;              // source records staged per warp at a time
-constexpr int kFlushChunks = 64;       // cost of flushing one dalpha tile, in chunks of work
+constexpr int kFlushChunks = 64;       // cost of writing out and summing one dalpha tile, in chunks
 // backward per-warp scratch: 32 item ranges, then up to kLStage staged sources (the
 // staging of wide chunks reuses the same bytes)
 constexpr int kLStage = 256;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                                                    int chunks_per_cta) {
     extern __shared__ float dtile[];      // [kTile][kTileLd], then per-warp scratch
     if (failed(p.hdr)) return;
-    const int M = p.M, P = p.P;
+    const int P = p.P;
     const int I = blockIdx.x / P, J = blockIdx.x % P;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     char* scratch = (char*)(dtile + kTile * kTileLd) + warp * kBwdWarpScratch;
@@ -386,8 +386,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
     float4* stage = (float4*)scratch;                   // wide chunks: [kStage] records
     const int nb = (int)num_chunks(p);
     const int b0 = blockIdx.y * chunks_per_cta;
-    const int b1 = min(b0 + chunks_per_cta, nb);
-    if (b0 >= b1) return;
+    const int b1 = min(b0 + chunks_per_cta, nb);    // may be empty: the tile is still written
     const float beta = p.beta[0];
     const int C = p.C, W = (C + 31) >> 5;
     for (int e = threadIdx.x; e < kTile * kTileLd; e += blockDim.x) dtile[e] = 0.f;
@@ -496,12 +495,12 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-        const int r = e >> 7, q = e & 127;
-        const float v = dtile[r * kTileLd + q];
-        const int i = I + P * r, j = J + P * q;
-        if (v != 0.f && i < M && j < M) atomicAdd(&p.dal_acc[(int64_t)i * M + j], (double)v);
-    }
+    // this block's tile (TR = ceil(M / P) rows and columns are used), summed over the chunk
+    // ranges in a fixed order by the finalisation
+    const int TR = (p.M + P - 1) / P;
+    float* out = p.dal_part + ((int64_t)blockIdx.y * P * P + blockIdx.x) * TR * TR;
+    for (int e = threadIdx.x; e < TR * TR; e += blockDim.x)
+        out[e] = dtile[(e / TR) * kTileLd + (e % TR)];
 }
 
 // Per-event epilogue: lambda, log, w, the W rows of the dalpha GEMM, the dbeta sum and
@@ -630,6 +629,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         ++*nl;
         prof_mark(s, "gemm_Z");
     }
+    int64_t dal_parts = 0;   // chunk ranges of the backward pair kernel
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -701,7 +701,8 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         const int64_t slots = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
         const int64_t tiles = (int64_t)P * P;
         int64_t R = 1, best = -1;
-        for (int64_t r = 1; r <= 8 * slots / tiles + 1 && r <= (nb > 0 ? nb : 1); ++r) {
+        for (int64_t r = 1; r <= 8 * slots / tiles + 1 && r <= (nb > 0 ? nb : 1) && r <= p.dal_parts_max;
+             ++r) {
             const int64_t waves = (tiles * r + slots - 1) / slots;
             const int64_t cost = waves * ((nb + r - 1) / r + kFlushChunks);
             if (best < 0 || cost < best) { best = cost; R = r; }
@@ -710,6 +711,7 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         if (per < 1) per = 1;
         R = (nb + per - 1) / per;
         if (R < 1) R = 1;
+        dal_parts = R;
         k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), kPairThreads, smem, s>>>(
             p, p.recs, p.lrec, p.bmask, p.kprep, p.bstart, p.wide, p.wbuf, (int)per);
         ++*nl;
@@ -748,7 +750,9 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         ++*nl;
         prof_mark(s, "gemm_dalpha");
     }
-    return launch_finalize_mode(p, s, 1, nl);
+    Problem q = p;
+    q.dal_parts = (int32_t)dal_parts;
+    return launch_finalize_mode(q, s, 1, nl);
 }
 
 }  // namespace hk
