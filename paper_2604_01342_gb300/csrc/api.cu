@@ -35,7 +35,7 @@ struct Plan {
     int Gc;
     int64_t nb_max, ng_max;
     size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
-        off_grp_dt, off_grp_reset, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
+        off_grp_dt, off_grp_reset, off_seg_comp, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
         off_dal_gemm, off_al_h, off_al_l, off_S_h, off_S_l, off_G_h, off_G_l, off_Wt_h, off_Wt_l,
         off_St_h, off_St_l, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf,
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
@@ -86,6 +86,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->off_grp_g = grad ? take(sizeof(float) * ngM) : 0;
     pl->off_grp_dt = take(sizeof(double) * (size_t)pl->ng_max);
     pl->off_grp_reset = take(sizeof(int32_t) * (size_t)pl->ng_max);
+    pl->off_seg_comp = take(sizeof(float) * 5 * (size_t)hk::kCarrySegments * M);
     pl->off_carry_S = take(sizeof(float) * ngM);
     pl->off_carry_G = grad ? take(sizeof(float) * ngM) : 0;
     size_t n_acc = (size_t)B * (1 + 4 * (size_t)M) + (grad ? (size_t)B * M * M : 0);
@@ -161,6 +162,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.grp_dt = at<double>(ws, pl.off_grp_dt);
     p.grp_reset = at<int32_t>(ws, pl.off_grp_reset);
     p.carry_S = at<float>(ws, pl.off_carry_S);
+    p.seg_comp = at<float>(ws, pl.off_seg_comp);
     p.carry_G = at<float>(ws, pl.off_carry_G);
     double* acc = at<double>(ws, pl.off_acc);
     const size_t BM = (size_t)B * M;

@@ -12,6 +12,8 @@
 namespace hk {
 
 // Workspace header: the first 256 bytes of every workspace.
+constexpr int kCarrySegments = 64;   // at most this many segments in the carry pass
+
 struct WsHeader {
     int32_t status;      // device status word (0 = ok, else a hawkes_status)
     int32_t validated;   // 1 if the last call ran the device checks
@@ -60,6 +62,7 @@ struct Problem {
     double* grp_dt;          // [ng_max] time span of the composite after its last reset
     int32_t* grp_reset;      // [ng_max]
     float* carry_S;          // [ng_max*M]
+    float* seg_comp;         // [5][kCarrySegments][M] segment composites of the carry pass
     float* carry_G;          // [ng_max*M]
     double* ll_acc;          // [B]   sum of log lambda
     double* dmu_acc;         // [B*M] sum of w over events of each mark

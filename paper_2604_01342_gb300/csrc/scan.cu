@@ -15,7 +15,8 @@
 //
 // Three passes (reduce, scan, re-walk) instead of a serial chain:
 //   A: each block composes a group of Gc chunks from a zero state -> (v, g, span, reset)
-//   B: one thread per mark scans the group composites in order -> carry into each group
+//   B: the group composites are scanned in order per mark (in Q segments composed in
+//      parallel, then walked from the composites before them) -> carry into each group
 //   C: each block re-walks its group from the carry and writes S^_b, G^_b per chunk.
 // Within a chunk the decay is applied to the whole state once and the chunk's
 // events are added with shared-memory atomics, so S is never held per event.
@@ -101,47 +102,92 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
 }
 
 // One thread per mark j: exclusive scan of the group composites.
-template <bool GRAD>
-__global__ void k_scan_carry(Problem p) {
-    if (failed(p.hdr)) return;
-    const int64_t nb = num_chunks(p);
-    const int64_t ng = (nb + p.Gc - 1) / p.Gc;
+// Pass B in parallel: the groups are cut into Q segments.  The map of group g on the
+// state of mark j is S' = d S + v_g, G' = d (G + dt S) + g_g (or the constant map
+// S' = v_g, G' = g_g at a sequence start); maps of the form
+//     S' = a S + v,  G' = b S + c G + w
+// compose into the same form.  k_carry_compose builds every segment's composite (one
+// thread per (mark, segment)); k_carry_walk starts each (mark, segment) from the
+// composites of the segments before it and walks its groups, writing the carry into each.
+__device__ __forceinline__ void group_map(const Problem& p, int64_t g, int j, float& d,
+                                          float& dt, float& v, float& gg, bool& reset) {
     const int M = p.M;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        // a slice of a longer sequence starts from the carried-in state (single sequence)
-        float cS = p.init_S ? p.init_S[j] : 0.f;
-        float cG = (GRAD && p.init_G) ? p.init_G[j] : 0.f;
-        constexpr int U = 8;
-        for (int64_t g0 = 0; g0 < ng; g0 += U) {
-            float v[U], gg[U], dt[U];
-            int rs[U], sq[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int64_t g = g0 + u;
-                if (g < ng) {
-                    v[u] = p.grp_v[g * M + j];
-                    gg[u] = GRAD ? p.grp_g[g * M + j] : 0.f;
-                    dt[u] = (float)p.grp_dt[g];
-                    rs[u] = p.grp_reset[g];
-                    sq[u] = p.chunk_seq[g * p.Gc];
-                }
+    v = p.grp_v[g * M + j];
+    gg = p.grp_g ? p.grp_g[g * M + j] : 0.f;
+    dt = (float)p.grp_dt[g];
+    reset = p.grp_reset[g] != 0;
+    d = reset ? 0.f : expf(-beta_of(p, p.chunk_seq[g * p.Gc], j) * dt);
+}
+
+template <bool GRAD>
+__global__ void k_carry_compose(Problem p, int Q, float* comp) {
+    if (failed(p.hdr)) return;
+    const int M = p.M;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (j >= M) return;
+    const int64_t ng = (num_chunks(p) + p.Gc - 1) / p.Gc;
+    const int64_t per = (ng + Q - 1) / Q;
+    const int64_t g0 = q * per, g1 = min(ng, g0 + per);
+    float a = 1.f, b = 0.f, c = 1.f, v = 0.f, w = 0.f;
+    for (int64_t g = g0; g < g1; ++g) {
+        float d, dt, vg, gg;
+        bool reset;
+        group_map(p, g, j, d, dt, vg, gg, reset);
+        if (reset) {
+            a = b = c = 0.f;
+            v = vg;
+            w = GRAD ? gg : 0.f;
+        } else {
+            if (GRAD) {
+                b = d * (dt * a + b);
+                c = d * c;
+                w = d * (dt * v + w) + gg;
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int64_t g = g0 + u;
-                if (g < ng) {
-                    p.carry_S[g * M + j] = cS;
-                    if (GRAD) p.carry_G[g * M + j] = cG;
-                    if (rs[u]) {
-                        cS = v[u];
-                        cG = gg[u];
-                    } else {
-                        float d = expf(-beta_of(p, sq[u], j) * dt[u]);
-                        if (GRAD) cG = d * (cG + dt[u] * cS) + gg[u];
-                        cS = d * cS + v[u];
-                    }
-                }
-            }
+            a = d * a;
+            v = d * v + vg;
+        }
+    }
+    const int64_t at = (int64_t)q * M + j, st = (int64_t)Q * M;
+    comp[at] = a;
+    comp[st + at] = v;
+    if (GRAD) {
+        comp[2 * st + at] = b;
+        comp[3 * st + at] = c;
+        comp[4 * st + at] = w;
+    }
+}
+
+template <bool GRAD>
+__global__ void k_carry_walk(Problem p, int Q, const float* comp) {
+    if (failed(p.hdr)) return;
+    const int M = p.M;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (j >= M) return;
+    const int64_t ng = (num_chunks(p) + p.Gc - 1) / p.Gc;
+    const int64_t per = (ng + Q - 1) / Q;
+    const int64_t g0 = q * per, g1 = min(ng, g0 + per);
+    // a slice of a longer sequence starts from the carried-in state (single sequence)
+    float cS = p.init_S ? p.init_S[j] : 0.f;
+    float cG = (GRAD && p.init_G) ? p.init_G[j] : 0.f;
+    const int64_t st = (int64_t)Q * M;
+    for (int r = 0; r < q; ++r) {
+        const int64_t at = (int64_t)r * M + j;
+        const float a = comp[at], v = comp[st + at];
+        if (GRAD) cG = comp[2 * st + at] * cS + comp[3 * st + at] * cG + comp[4 * st + at];
+        cS = a * cS + v;
+    }
+    for (int64_t g = g0; g < g1; ++g) {
+        p.carry_S[g * M + j] = cS;
+        if (GRAD) p.carry_G[g * M + j] = cG;
+        float d, dt, vg, gg;
+        bool reset;
+        group_map(p, g, j, d, dt, vg, gg, reset);
+        if (reset) {
+            cS = vg;
+            cG = gg;
+        } else {
+            if (GRAD) cG = d * (cG + dt * cS) + gg;
+            cS = d * cS + vg;
         }
     }
 }
@@ -192,23 +238,31 @@ cudaError_t launch_slice_aggregate(const Problem& p, double t_next, float* agg_S
 cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
     size_t smem = sizeof(float) * 2 * (size_t)p.M;
     unsigned grid = (unsigned)(p.ng_max > 0 ? p.ng_max : 1);
-    unsigned cgrid = (unsigned)((p.M + 127) / 128);
+    // segments of the carry pass: enough (mark, segment) threads for every SM, at least
+    // four groups per segment
+    int64_t Q = (152 * 512 + p.M - 1) / p.M;
+    if (Q > kCarrySegments) Q = kCarrySegments;
+    if (Q > (p.ng_max + 3) / 4) Q = (p.ng_max + 3) / 4;
+    if (Q < 1) Q = 1;
+    const dim3 cgrid((unsigned)((p.M + 127) / 128), (unsigned)Q);
     if (p.grad) {
         k_scan_group<0, true><<<grid, 256, smem, s>>>(p);
         prof_mark(s, "scan_reduce");
-        k_scan_carry<true><<<cgrid, 128, 0, s>>>(p);
+        k_carry_compose<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
+        k_carry_walk<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
         k_scan_group<1, true><<<grid, 256, smem, s>>>(p);
         prof_mark(s, "scan_states");
     } else {
         k_scan_group<0, false><<<grid, 256, smem, s>>>(p);
         prof_mark(s, "scan_reduce");
-        k_scan_carry<false><<<cgrid, 128, 0, s>>>(p);
+        k_carry_compose<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
+        k_carry_walk<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
         k_scan_group<1, false><<<grid, 256, smem, s>>>(p);
         prof_mark(s, "scan_states");
     }
-    *nl += 3;
+    *nl += 4;
     return cudaGetLastError();
 }
 
