@@ -409,6 +409,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# DRAM bytes per event of the pair kernels: dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture on the first 2e6 events of the benchmark stream
+# (profiles/ncu_pair_kernels_m1024_n2m.md).  A launch processes every event of the step and
+# the kernels' traffic grows in proportion to the events, so a launch moves N times this.
+DRAM_BYTES_PER_EVENT = {"pairs_bwd": (52421376 + 16428544) / 2e6,
+                        "pairs_fwd": (36704000 + 115456) / 2e6}
+
+
 def kernel_work(name, N, M, C):
     """(bound, algorithmic work per launch) of each kernel of one step.
 
@@ -469,8 +477,10 @@ def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
     if dom is None:
         return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None}
+    traffic = DRAM_BYTES_PER_EVENT.get(name)
     out = {"kernel": name, "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
-           "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+           "unit": dom["unit"], "frac": dom["frac"],
+           "traffic": traffic * N if traffic is not None else None,
            "peak_source": {"hbm": f"{src} HBM copy bandwidth",
                            "tensor": f"{src} bf16 dense (= fp16 dense), burst",
                            "smem": "shared memory: 152 SMs x 128 B/clock x max SM clock",

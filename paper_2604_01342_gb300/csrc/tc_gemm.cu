@@ -14,8 +14,8 @@
 //
 // One CTA computes one 128 x 256 output tile over a slice of K (split-K with
 // atomic accumulation when there is more than one slice).  One thread issues the TMA
-// loads (cp.async.bulk.tensor, 128-byte swizzle, 64 fp16 of K per row) into a
-// two-stage ring and the tcgen05.mma instructions (kind::f16, f32 accumulate,
+// loads (cp.async.bulk.tensor, 64-byte swizzle, 32 fp16 of K per row) into a
+// four-stage ring and the tcgen05.mma instructions (kind::f16, f32 accumulate,
 // M=128, N=256, K=16); tcgen05.commit arrives on the stage's "empty"
 // mbarrier when the MMAs that read it are done.  The tensor-core accumulator
 // loses precision with the number of accumulation steps (measured with TF32 operands:
@@ -37,13 +37,16 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BN = 256;
-constexpr int BK = 64;                  // fp16 elements = 128 bytes = one swizzle row
-constexpr int STAGES = 2;
-constexpr int A_TILE = BM * BK * 2;     // 16 KB
-constexpr int B_TILE = BN * BK * 2;     // 32 KB
-constexpr int GROUPS_PER_STAGE = 2;     // promotion every 32 of K
+constexpr int BK = 32;                  // fp16 elements = 64 bytes = one swizzle row
+constexpr int STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;     // 8 KB
+constexpr int B_TILE = BN * BK * 2;     // 16 KB
+constexpr int GROUPS_PER_STAGE = 1;     // promotion every 32 of K
+// unused bytes between the stages and the barriers, so that no operand descriptor of the
+// last stage can reach the barriers or the end of the allocation
+constexpr int kSlack = 24 * 1024;
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // Ah, Al, Bh, Bl
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + kSlack + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t TMEM_COLS = 512;      // two accumulator banks of BN columns
 constexpr uint32_t kSpinLimit = 1u << 26;   // bounded waits (~ seconds)
 
@@ -88,15 +91,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(const void* tile) {
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(const void* tile) {
     uint64_t a = smem_u32(tile);
     uint64_t d = 0;
     d |= (a >> 4) & 0x3FFFull;          // start address
     d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset: 8 rows x 64 B
     d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    d |= (uint64_t)4 << 61;             // SWIZZLE_64B
     return d;
 }
 
@@ -154,7 +157,7 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
              const float* __restrict__ inv_sa, const float* __restrict__ inv_sb, WsHeader* hdr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES + kSlack);
     uint64_t* empty = full + STAGES;
     uint64_t* bank_full = empty + STAGES;     // [2] accumulator bank holds a finished group
     uint64_t* bank_empty = bank_full + 2;     // [2] bank has been read by all epilogue warps
@@ -216,9 +219,9 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                 inflight[s] = -1;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 uint8_t* st = smem + s * STAGE_BYTES;
-                const uint64_t dah = sw128_desc(st), dal = sw128_desc(st + A_TILE);
-                const uint64_t dbh = sw128_desc(st + 2 * A_TILE);
-                const uint64_t dbl = sw128_desc(st + 2 * A_TILE + B_TILE);
+                const uint64_t dah = sw64_desc(st), dal = sw64_desc(st + A_TILE);
+                const uint64_t dbh = sw64_desc(st + 2 * A_TILE);
+                const uint64_t dbl = sw64_desc(st + 2 * A_TILE + B_TILE);
                 for (int h = 0; h < GROUPS_PER_STAGE && ok; ++h) {
                     const int g = i * GROUPS_PER_STAGE + h, bank = g & 1;
                     if (g >= 2) {
@@ -230,7 +233,7 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                     constexpr int kSteps = BK / 16 / GROUPS_PER_STAGE;
 #pragma unroll
                     for (int kk = 0; kk < kSteps; ++kk) {
-                        // 16 fp16 = 32 bytes along the swizzled row
+                        // 16 fp16 = 32 bytes along the 64-byte swizzled row
                         const uint64_t off = (uint64_t)((h * kSteps + kk) * 32) >> 4;
                         mma_f16(acc_t, dah + off, dbh + off, idesc, kk > 0 ? 1u : 0u);
                         mma_f16(acc_t, dah + off, dbl + off, idesc, 1u);
@@ -346,7 +349,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D fp16 tensor [rows][k] with row stride ld (elements), box {64, box_rows}.
+// 2-D fp16 tensor [rows][k] with row stride ld (elements), box {32, box_rows}.
 static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t k, int64_t ld,
                      int box_rows) {
     auto enc = get_encode();
@@ -357,7 +360,7 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t k, 
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
