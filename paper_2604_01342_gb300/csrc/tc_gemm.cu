@@ -19,9 +19,9 @@
 // M=128, N=256, K=16); tcgen05.commit arrives on the stage's "empty"
 // mbarrier when the MMAs that read it are done.  The tensor-core accumulator
 // loses precision with the number of accumulation steps (measured with TF32 operands:
-// ~1.6e-6 after 64 of K, ~2.6e-5 after 1024), so every 32 of K is accumulated into one of
-// two TMEM banks and then promoted: eight warps read the finished bank with tcgen05.ld and
-// add it to FP32 registers while the MMAs fill the other bank.  Every mbarrier wait is
+// ~1.6e-6 after 64 of K, ~2.6e-5 after 1024), so every 64 of K (two k-tiles) is
+// accumulated into one of two TMEM banks and then promoted: eight warps read the finished
+// bank with tcgen05.ld and add it to FP32 registers while the MMAs fill the other bank.  Every mbarrier wait is
 // bounded; on timeout the kernel records an error in the status word, waits (bounded) for
 // its MMAs, frees its tensor memory and returns.
 #include <cuda.h>
@@ -41,7 +41,7 @@ constexpr int BK = 32;                  // fp16 elements = 64 bytes = one swizzl
 constexpr int STAGES = 4;
 constexpr int A_TILE = BM * BK * 2;     // 8 KB
 constexpr int B_TILE = BN * BK * 2;     // 16 KB
-constexpr int GROUPS_PER_STAGE = 1;     // promotion every 32 of K
+constexpr int kTilesPerGroup = 2;       // k-tiles accumulated in TMEM before promotion (64 of K)
 // unused bytes between the stages and the barriers, so that no operand descriptor of the
 // last stage can reach the barriers or the end of the allocation
 constexpr int kSlack = 24 * 1024;
@@ -171,7 +171,7 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
     int kt1 = kt0 + k_tiles_per_split;
     if (kt1 > k_tiles_total) kt1 = k_tiles_total;
     const int KT = kt1 > kt0 ? kt1 - kt0 : 0;
-    const int ngroups = KT * GROUPS_PER_STAGE;
+    const int ngroups = (KT + kTilesPerGroup - 1) / kTilesPerGroup;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -222,25 +222,24 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                 const uint64_t dah = sw64_desc(st), dal = sw64_desc(st + A_TILE);
                 const uint64_t dbh = sw64_desc(st + 2 * A_TILE);
                 const uint64_t dbl = sw64_desc(st + 2 * A_TILE + B_TILE);
-                for (int h = 0; h < GROUPS_PER_STAGE && ok; ++h) {
-                    const int g = i * GROUPS_PER_STAGE + h, bank = g & 1;
-                    if (g >= 2) {
-                        // the epilogue must have read this bank's previous group
-                        if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) { ok = false; break; }
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    }
-                    const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
-                    constexpr int kSteps = BK / 16 / GROUPS_PER_STAGE;
-#pragma unroll
-                    for (int kk = 0; kk < kSteps; ++kk) {
-                        // 16 fp16 = 32 bytes along the 64-byte swizzled row
-                        const uint64_t off = (uint64_t)((h * kSteps + kk) * 32) >> 4;
-                        mma_f16(acc_t, dah + off, dbh + off, idesc, kk > 0 ? 1u : 0u);
-                        mma_f16(acc_t, dah + off, dbl + off, idesc, 1u);
-                        mma_f16(acc_t, dal + off, dbh + off, idesc, 1u);
-                    }
-                    mma_commit(&bank_full[bank]);
+                const int g = i / kTilesPerGroup, bank = g & 1;
+                const bool first_in_group = (i % kTilesPerGroup) == 0;
+                if (first_in_group && g >= 2) {
+                    // the epilogue must have read this bank's previous group
+                    if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
+                const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    // 16 fp16 = 32 bytes along the 64-byte swizzled row
+                    const uint64_t off = (uint64_t)(kk * 32) >> 4;
+                    const uint32_t acc0 = (!first_in_group || kk > 0) ? 1u : 0u;
+                    mma_f16(acc_t, dah + off, dbh + off, idesc, acc0);
+                    mma_f16(acc_t, dah + off, dbl + off, idesc, 1u);
+                    mma_f16(acc_t, dal + off, dbh + off, idesc, 1u);
+                }
+                if ((i % kTilesPerGroup) == kTilesPerGroup - 1 || i == KT - 1) mma_commit(&bank_full[bank]);
                 if (!ok) break;
                 mma_commit(&empty[s]);
                 // refill the stage the previous k-tile used once its MMAs are done
