@@ -20,6 +20,10 @@ What pins each function (see ``tests/test_oracle_pins.py``):
   * ``grad_adjoint``: equals ``loglik_grad`` (two derivations) and FD.
   * ``paper_grad_shared``: the paper's R/K/L form, equal to the others at
     small T.
+  * ``loglik_grad_multi`` (several decay kernels): equals ``loglik_grad`` at K = 1; its
+    intensity against the brute-force double sum over kernels and pairs; two kernels
+    with one decay equal one kernel with the summed matrix; central finite differences;
+    quadrature of the compensator.
 """
 from __future__ import annotations
 
@@ -75,6 +79,8 @@ def _load():
                                                      ctypes.c_int, p, p, p, p, p]
             lib.oracle_loglik_grad_carry.restype = ctypes.c_int
             lib.oracle_slice_aggregate.argtypes = [i64, p, p, i32, p, d, p, p]
+            lib.oracle_loglik_grad_multi.argtypes = [i64, p, p, d, i32, i32, p, p, p, p, p, p, p, p]
+            lib.oracle_loglik_grad_multi.restype = ctypes.c_int
             lib.oracle_slice_aggregate.restype = ctypes.c_int
             lib.oracle_condition.restype = ctypes.c_int
             for f in (lib.oracle_loglik_grad, lib.oracle_grad_adjoint, lib.oracle_paper_grad_shared,
@@ -220,3 +226,35 @@ def slice_aggregate(t, c, M, beta, t_next):
     if rc:
         raise OracleError(rc)
     return aS, aG
+
+
+def loglik_grad_multi(t, c, T, mu, alphas, betas, want_grad=True, want_lam=False):
+    """K decay kernels: alphas [K, M, M] (row = target), betas [K] (one decay per kernel)
+    or [K, M] (per source).  Returns L and (dmu [M], dalpha [K, M, M], dbeta [K, M])."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    M = mu.shape[0]
+    alphas = np.ascontiguousarray(alphas, dtype=np.float64)
+    K = alphas.shape[0]
+    betas = np.asarray(betas, dtype=np.float64)
+    if betas.ndim == 1:
+        betas = np.repeat(betas[:, None], M, axis=1)
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    N = t.shape[0]
+    ll = np.zeros(1)
+    lam = np.zeros(N) if want_lam else None
+    dmu = np.zeros(M) if want_grad else None
+    dal = np.zeros((K, M, M)) if want_grad else None
+    dbe = np.zeros((K, M)) if want_grad else None
+    rc = _load().oracle_loglik_grad_multi(N, _ptr(t), _ptr(c), float(T), M, K, _ptr(mu),
+                                          _ptr(alphas), _ptr(betas), _ptr(ll), _ptr(lam),
+                                          _ptr(dmu), _ptr(dal), _ptr(dbe))
+    if rc:
+        raise OracleError(rc)
+    out = {"ll": float(ll[0])}
+    if want_grad:
+        out.update(dmu=dmu, dalpha=dal, dbeta=dbe)
+    if want_lam:
+        out["lam"] = lam
+    return out

@@ -426,3 +426,99 @@ int oracle_condition(int64_t N, const double* t, const int32_t* c, double T, int
     free(S); free(G); free(F);
     return rc;
 }
+
+/* Several decay kernels (paper, Section 2, Eq. hawkes_excitation with its sum over
+ * kernels k = 1..K): kernel q has its own interaction matrix alpha^(q) and decays
+ * beta^(q)_j (one per source; the paper's model has them equal within a kernel),
+ *     lambda_p(t) = mu_p + sum_q sum_{l before t} alpha^(q)[p][c_l] beta^(q)_{c_l}
+ *                          exp(-beta^(q)_{c_l} (t - t_l)).
+ * Each kernel keeps its own source-indexed state S^(q) (and G^(q)); lambda sums the
+ * kernels, and the gradients with respect to alpha^(q) and beta^(q) are the single-kernel
+ * formulas above with S^(q), G^(q), E^(q), F^(q), colsum^(q).
+ * alpha: [K][M][M], beta: [K][M]; dalpha: [K][M][M], dbeta: [K][M]; lam (optional): [N]. */
+int oracle_loglik_grad_multi(int64_t N, const double* t, const int32_t* c, double T,
+                             int32_t M, int32_t K, const double* mu, const double* alpha,
+                             const double* beta, double* out_ll, double* lam,
+                             double* dmu, double* dalpha, double* dbeta)
+{
+    if (K < 1) return OR_INVALID;
+    for (int32_t q = 0; q < K; ++q) {
+        int rc = check_inputs(N, t, c, T, M, mu, alpha + (size_t)q * M * M, beta + (size_t)q * M);
+        if (rc) return rc;
+    }
+    const size_t KM = (size_t)K * (size_t)M;
+    double* S = calloc(KM, sizeof(double));
+    double* G = calloc(KM, sizeof(double));
+    double* E = calloc(KM, sizeof(double));
+    double* F = calloc(KM, sizeof(double));
+    if (!S || !G || !E || !F) { free(S); free(G); free(E); free(F); return OR_INVALID; }
+    if (dmu) memset(dmu, 0, sizeof(double) * (size_t)M);
+    if (dalpha) memset(dalpha, 0, sizeof(double) * KM * (size_t)M);
+    if (dbeta) memset(dbeta, 0, sizeof(double) * KM);
+
+    int rc = OR_OK;
+    double logsum = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        if (k > 0) {
+            double dt = t[k] - t[k - 1];
+            int32_t prev = c[k - 1];
+            for (int32_t q = 0; q < K; ++q)
+                for (int32_t j = 0; j < M; ++j) {
+                    size_t v = (size_t)q * M + j;
+                    double d = exp(-beta[v] * dt);
+                    double P = S[v] + (j == prev ? 1.0 : 0.0);
+                    G[v] = d * (G[v] + dt * P);
+                    S[v] = d * P;
+                }
+        }
+        int32_t i = c[k];
+        double exc = 0.0;
+        for (int32_t q = 0; q < K; ++q) {
+            const double* arow = alpha + ((size_t)q * M + i) * M;
+            for (int32_t j = 0; j < M; ++j) {
+                size_t v = (size_t)q * M + j;
+                exc += arow[j] * beta[v] * S[v];
+            }
+        }
+        double lk = mu[i] + exc;
+        if (!(lk > 0.0)) { rc = OR_NONPOS; break; }
+        if (lam) lam[k] = lk;
+        logsum += log(lk);
+        double w = 1.0 / lk;
+        if (dmu) dmu[i] += w;
+        for (int32_t q = 0; q < K; ++q) {
+            const double* arow = alpha + ((size_t)q * M + i) * M;
+            for (int32_t j = 0; j < M; ++j) {
+                size_t v = (size_t)q * M + j;
+                if (dalpha) dalpha[((size_t)q * M + i) * M + j] += w * beta[v] * S[v];
+                if (dbeta) dbeta[v] += w * arow[j] * (S[v] - beta[v] * G[v]);
+            }
+            /* compensator pieces of event k as a source of kernel q */
+            size_t vi = (size_t)q * M + i;
+            double x = beta[vi] * (T - t[k]);
+            E[vi] += -expm1(-x);
+            F[vi] += (T - t[k]) * exp(-x);
+        }
+    }
+    if (rc == OR_OK) {
+        double summu = 0.0, comp = 0.0;
+        for (int32_t i = 0; i < M; ++i) summu += mu[i];
+        for (int32_t q = 0; q < K; ++q)
+            for (int32_t j = 0; j < M; ++j) {
+                size_t v = (size_t)q * M + j;
+                double cs = 0.0;
+                for (int32_t i = 0; i < M; ++i) cs += alpha[((size_t)q * M + i) * M + j];
+                comp += cs * E[v];
+                if (dbeta) dbeta[v] -= cs * F[v];
+            }
+        if (out_ll) *out_ll = logsum - T * summu - comp;
+        if (dmu) for (int32_t i = 0; i < M; ++i) dmu[i] -= T;
+        if (dalpha)
+            for (int32_t q = 0; q < K; ++q)
+                for (int32_t i = 0; i < M; ++i)
+                    for (int32_t j = 0; j < M; ++j)
+                        dalpha[((size_t)q * M + i) * M + j] -= E[(size_t)q * M + j];
+    }
+    free(S); free(G); free(E); free(F);
+    return rc;
+}

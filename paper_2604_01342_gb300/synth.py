@@ -256,3 +256,100 @@ def random_problem(m: int, n: int, seed: int, shared_beta: bool, rho: float = 0.
         p.t = p.t + time_shift
         p.T = p.T + time_shift
     return p
+
+
+# ------------------------------------------------------------------ several decay kernels
+@dataclass
+class MultiProblem:
+    """One event stream of a K-kernel process: kernel q has alphas[q] (row = target) and
+    one decay betas[q] shared by all sources (the paper's multi-kernel model)."""
+    t: np.ndarray            # float64 [N]
+    c: np.ndarray            # int32 [N]
+    T: float
+    mu: np.ndarray           # float64 [M]
+    alphas: np.ndarray       # float64 [K, M, M]
+    betas: np.ndarray        # float64 [K]
+    name: str = ""
+
+    @property
+    def N(self) -> int:
+        return int(self.t.shape[0])
+
+    @property
+    def M(self) -> int:
+        return int(self.mu.shape[0])
+
+    @property
+    def K(self) -> int:
+        return int(self.alphas.shape[0])
+
+
+def simulate_cluster_multi(mu, alphas, betas, horizon: float, rng: np.random.Generator):
+    """Cluster representation with several kernels: an event of mark j has
+    Poisson(colsum^(q)_j) children through kernel q, marks drawn from column j of
+    alphas[q], delays Exp(betas[q])."""
+    mu = np.asarray(mu, dtype=np.float64)
+    m = mu.shape[0]
+    samplers = [_column_sampler(np.asarray(a, dtype=np.float64)) for a in alphas]
+    counts = rng.poisson(mu * horizon)
+    marks = np.repeat(np.arange(m, dtype=np.int32), counts)
+    times = rng.uniform(0.0, horizon, size=marks.shape[0])
+    all_t, all_c = [times], [marks]
+    gen_t, gen_c = times, marks
+    while gen_t.shape[0] > 0:
+        new_t, new_c = [], []
+        for (colsum, flat), b in zip(samplers, betas):
+            nkids = rng.poisson(colsum[gen_c])
+            par_t = np.repeat(gen_t, nkids)
+            par_c = np.repeat(gen_c, nkids)
+            if par_t.shape[0] == 0:
+                continue
+            u = rng.random(par_t.shape[0])
+            idx = np.searchsorted(flat, par_c.astype(np.float64) + u, side="right")
+            kid_c = (idx - par_c.astype(np.int64) * m).clip(0, m - 1).astype(np.int32)
+            kid_t = par_t + rng.exponential(1.0, size=par_t.shape[0]) / float(b)
+            keep = kid_t <= horizon
+            new_t.append(kid_t[keep])
+            new_c.append(kid_c[keep])
+        if not new_t:
+            break
+        gen_t, gen_c = np.concatenate(new_t), np.concatenate(new_c)
+        all_t.append(gen_t)
+        all_c.append(gen_c)
+    t = np.concatenate(all_t)
+    c = np.concatenate(all_c)
+    order = np.argsort(t, kind="stable")
+    return t[order], c[order]
+
+
+def random_problem_multi(m: int, n: int, seed: int, kernels: int, rho: float = 0.6,
+                         density: float = 1.0, beta_range=(0.3, 3.0),
+                         mu_range=(0.05, 0.5)) -> MultiProblem:
+    """A seeded K-kernel problem: the summed interaction matrix has spectral radius rho,
+    shared among the kernels at random; decays drawn log-uniformly from beta_range."""
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(*mu_range, size=m)
+    parts = [rng.uniform(0.0, 1.0, size=(m, m)) * (rng.random((m, m)) < density)
+             for _ in range(kernels)]
+    total = sum(parts)
+    r = spectral_radius(total)
+    scale = rho / r if r > 0 else 0.0
+    alphas = np.stack([a * scale for a in parts])
+    lo, hi = np.log(beta_range[0]), np.log(beta_range[1])
+    betas = np.sort(np.exp(rng.uniform(lo, hi, size=kernels)))
+    if n == 0:
+        t, c, T = np.zeros(0), np.zeros(0, dtype=np.int32), 0.0
+    else:
+        rate = stationary_rate(mu, alphas.sum(axis=0))
+        horizon = 1.15 * n / rate + 10.0 / float(np.min(betas))
+        for _ in range(30):
+            t, c = simulate_cluster_multi(mu, alphas, betas, horizon, rng)
+            if t.shape[0] >= n:
+                t, c = t[:n].copy(), c[:n].copy()
+                break
+            horizon *= 1.5
+        else:
+            raise RuntimeError("simulation did not reach the requested number of events")
+        T = float(t[-1])
+    return MultiProblem(t=t, c=c, T=T, mu=mu, alphas=alphas, betas=betas,
+                        name=f"multi_m{m}_k{kernels}_n{n}_s{seed}")
