@@ -24,6 +24,13 @@
  *   - Ties (equal times) count the earlier-indexed event at full weight, as the
  *     state recurrence of Eq. intensity_state_recurrence does with dt = 0.
  *   - N = 0 is legal: L = -T sum mu and the gradients reduce to the compensator terms.
+ *   - Several decay kernels (opts->kernels = K > 1; paper, Eq. hawkes_excitation with its
+ *     sum over kernels k = 1..K): kernel q has its own matrix and one decay shared by all
+ *     sources,
+ *         lambda_i(t) = mu_i + sum_q sum_{l before t} alpha_q[i][c_l] beta_q exp(-beta_q (t - t_l)).
+ *     alpha is then [K][M][M] (kernel-major), beta [K], d_alpha [K][M][M] and d_beta [K];
+ *     K > 1 needs beta_shared = 1 and the single-sequence entry points (hawkes_loglik,
+ *     hawkes_loglik_grad, hawkes_workspace_size with B = 1), and runs the chunk-GEMM path.
  *
  * Memory and ownership
  *   - Every array argument of the device entry points is a DEVICE pointer owned by
@@ -75,9 +82,11 @@ typedef struct {
     int32_t validate;     /* 1: run the device input checks (default); 0: trust the inputs      */
     int32_t path;         /* 0: automatic; 1: state-walk kernels; 2: chunk-GEMM kernels
                              (shared decay only).  Both give the same result within rounding.  */
+    int32_t kernels;      /* decay kernels K: 0 or 1 = one kernel; 2..4 = several (see above)   */
 } hawkes_opts;
 
-/* Default options: per-source decay, default chunk, validation on, automatic path. */
+/* Default options: per-source decay, default chunk, validation on, automatic path, one
+ * decay kernel. */
 hawkes_opts hawkes_default_opts(void);
 
 /* Bytes of device workspace needed by a call on N events (all sequences together),

@@ -24,6 +24,8 @@ What pins each function (see ``tests/test_oracle_pins.py``):
     intensity against the brute-force double sum over kernels and pairs; two kernels
     with one decay equal one kernel with the summed matrix; central finite differences;
     quadrature of the compensator.
+  * ``condition_multi``: equals ``condition`` at K = 1; a brute-force double sum over
+    kernels and event pairs; bounds every term it sums (|dbeta| <= its scale).
 """
 from __future__ import annotations
 
@@ -81,6 +83,8 @@ def _load():
             lib.oracle_slice_aggregate.argtypes = [i64, p, p, i32, p, d, p, p]
             lib.oracle_loglik_grad_multi.argtypes = [i64, p, p, d, i32, i32, p, p, p, p, p, p, p, p]
             lib.oracle_loglik_grad_multi.restype = ctypes.c_int
+            lib.oracle_condition_multi.argtypes = [i64, p, p, d, i32, i32, p, p, p, p, p]
+            lib.oracle_condition_multi.restype = ctypes.c_int
             lib.oracle_slice_aggregate.restype = ctypes.c_int
             lib.oracle_condition.restype = ctypes.c_int
             for f in (lib.oracle_loglik_grad, lib.oracle_grad_adjoint, lib.oracle_paper_grad_shared,
@@ -228,19 +232,22 @@ def slice_aggregate(t, c, M, beta, t_next):
     return aS, aG
 
 
-def loglik_grad_multi(t, c, T, mu, alphas, betas, want_grad=True, want_lam=False):
-    """K decay kernels: alphas [K, M, M] (row = target), betas [K] (one decay per kernel)
-    or [K, M] (per source).  Returns L and (dmu [M], dalpha [K, M, M], dbeta [K, M])."""
+def _prep_multi(t, c, mu, alphas, betas):
     t = np.ascontiguousarray(t, dtype=np.float64)
     c = np.ascontiguousarray(c, dtype=np.int32)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     M = mu.shape[0]
     alphas = np.ascontiguousarray(alphas, dtype=np.float64)
-    K = alphas.shape[0]
     betas = np.asarray(betas, dtype=np.float64)
     if betas.ndim == 1:
         betas = np.repeat(betas[:, None], M, axis=1)
-    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    return t, c, mu, alphas, np.ascontiguousarray(betas, dtype=np.float64), M, alphas.shape[0]
+
+
+def loglik_grad_multi(t, c, T, mu, alphas, betas, want_grad=True, want_lam=False):
+    """K decay kernels: alphas [K, M, M] (row = target), betas [K] (one decay per kernel)
+    or [K, M] (per source).  Returns L and (dmu [M], dalpha [K, M, M], dbeta [K, M])."""
+    t, c, mu, alphas, betas, M, K = _prep_multi(t, c, mu, alphas, betas)
     N = t.shape[0]
     ll = np.zeros(1)
     lam = np.zeros(N) if want_lam else None
@@ -258,3 +265,15 @@ def loglik_grad_multi(t, c, T, mu, alphas, betas, want_grad=True, want_lam=False
     if want_lam:
         out["lam"] = lam
     return out
+
+
+def condition_multi(t, c, T, mu, alphas, betas):
+    """Conditioning scales with K decay kernels (sums of magnitudes of the terms of L and
+    of each dL/dbeta^(q)_j): {"ll": float, "dbeta": array[K, M]}."""
+    t, c, mu, alphas, betas, M, K = _prep_multi(t, c, mu, alphas, betas)
+    sl, sb = np.zeros(1), np.zeros((K, M))
+    rc = _load().oracle_condition_multi(t.shape[0], _ptr(t), _ptr(c), float(T), M, K, _ptr(mu),
+                                        _ptr(alphas), _ptr(betas), _ptr(sl), _ptr(sb))
+    if rc:
+        raise OracleError(rc)
+    return {"ll": float(sl[0]), "dbeta": sb}

@@ -522,3 +522,77 @@ int oracle_loglik_grad_multi(int64_t N, const double* t, const int32_t* c, doubl
     free(S); free(G); free(E); free(F);
     return rc;
 }
+
+/* Conditioning scales of L and of each dL/dbeta^(q)_j with several decay kernels: the
+ * sums of magnitudes of their terms, as oracle_condition does for one kernel, with the
+ * intensity (and w = 1 / lambda) summed over the kernels:
+ *   scale_ll = sum_k |log lambda_k| + T sum_i mu_i + sum_q sum_j colsum^(q)_j E^(q)_j,
+ *   scale_dbeta[q][j] = sum_k |w_k alpha^(q)[c_k][j] (S^(q)_j - beta^(q)_j G^(q)_j)|
+ *                       + colsum^(q)_j F^(q)_j.
+ * alpha: [K][M][M], beta: [K][M]; scale_dbeta: [K][M]. */
+int oracle_condition_multi(int64_t N, const double* t, const int32_t* c, double T,
+                           int32_t M, int32_t K, const double* mu, const double* alpha,
+                           const double* beta, double* scale_ll, double* scale_dbeta)
+{
+    if (K < 1) return OR_INVALID;
+    for (int32_t q = 0; q < K; ++q) {
+        int rc = check_inputs(N, t, c, T, M, mu, alpha + (size_t)q * M * M, beta + (size_t)q * M);
+        if (rc) return rc;
+    }
+    const size_t KM = (size_t)K * (size_t)M;
+    double* S = calloc(KM, sizeof(double));
+    double* G = calloc(KM, sizeof(double));
+    double* E = calloc(KM, sizeof(double));
+    double* F = calloc(KM, sizeof(double));
+    if (!S || !G || !E || !F) { free(S); free(G); free(E); free(F); return OR_INVALID; }
+    memset(scale_dbeta, 0, sizeof(double) * KM);
+    int rc = OR_OK;
+    double sabs = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        if (k > 0) {
+            double dt = t[k] - t[k - 1];
+            int32_t prev = c[k - 1];
+            for (size_t v = 0; v < KM; ++v) {
+                double d = exp(-beta[v] * dt);
+                double P = S[v] + ((int32_t)(v % (size_t)M) == prev ? 1.0 : 0.0);
+                G[v] = d * (G[v] + dt * P);
+                S[v] = d * P;
+            }
+        }
+        int32_t i = c[k];
+        double lk = mu[i];
+        for (int32_t q = 0; q < K; ++q) {
+            const double* arow = alpha + ((size_t)q * M + i) * M;
+            for (int32_t j = 0; j < M; ++j) lk += arow[j] * beta[(size_t)q * M + j] * S[(size_t)q * M + j];
+        }
+        if (!(lk > 0.0)) { rc = OR_NONPOS; break; }
+        sabs += fabs(log(lk));
+        double w = 1.0 / lk;
+        for (int32_t q = 0; q < K; ++q) {
+            const double* arow = alpha + ((size_t)q * M + i) * M;
+            for (int32_t j = 0; j < M; ++j) {
+                size_t v = (size_t)q * M + j;
+                scale_dbeta[v] += fabs(w * arow[j] * (S[v] - beta[v] * G[v]));
+            }
+            size_t vi = (size_t)q * M + i;
+            double x = beta[vi] * (T - t[k]);
+            E[vi] += -expm1(-x);
+            F[vi] += (T - t[k]) * exp(-x);
+        }
+    }
+    if (rc == OR_OK) {
+        double summu = 0.0, comp = 0.0;
+        for (int32_t i = 0; i < M; ++i) summu += mu[i];
+        for (int32_t q = 0; q < K; ++q)
+            for (int32_t j = 0; j < M; ++j) {
+                size_t v = (size_t)q * M + j;
+                double cs = 0.0;
+                for (int32_t r = 0; r < M; ++r) cs += alpha[((size_t)q * M + r) * M + j];
+                comp += cs * E[v];
+                scale_dbeta[v] += cs * F[v];
+            }
+        *scale_ll = sabs + T * summu + comp;
+    }
+    free(S); free(G); free(E); free(F);
+    return rc;
+}

@@ -37,7 +37,8 @@ EXPORTED = (
 
 class HawkesOpts(ctypes.Structure):
     _fields_ = [("beta_shared", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("validate", ctypes.c_int32), ("path", ctypes.c_int32)]
+                ("validate", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("kernels", ctypes.c_int32)]
 
 
 class HawkesError(RuntimeError):
@@ -106,8 +107,10 @@ def lib():
         return L
 
 
-def make_opts(beta_shared: bool, chunk: int = 0, validate: bool = True, path: int = 0):
-    return HawkesOpts(int(bool(beta_shared)), int(chunk), int(bool(validate)), int(path))
+def make_opts(beta_shared: bool, chunk: int = 0, validate: bool = True, path: int = 0,
+              kernels: int = 1):
+    return HawkesOpts(int(bool(beta_shared)), int(chunk), int(bool(validate)), int(path),
+                      int(kernels))
 
 
 def _check(rc: int, where: str):

@@ -21,6 +21,7 @@ struct Prof {
 thread_local Prof g_prof;
 
 constexpr size_t kAlign = 256;
+constexpr size_t kMaxDynamicSmem = 227 * 1024;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 constexpr int kDefaultChunkWalk = 128;
@@ -41,6 +42,9 @@ struct Plan {
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
     int64_t ldk, nbp;
     int dal_parts_max;
+    int K;                 // decay kernels (one workspace slice each)
+    size_t scratch_off;
+    size_t slice;          // bytes of one slice
 };
 
 // Returns 0 and fills the plan, or a hawkes_status.
@@ -48,6 +52,13 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     if (N < 0 || M <= 0 || B <= 0) return HAWKES_ERR_INVALID_ARG;
     const int shared = o ? o->beta_shared : 0;
     int path = o ? o->path : 0;
+    const int K = (o && o->kernels > 1) ? o->kernels : 1;
+    if (K > hk::kMaxKernels) return HAWKES_ERR_INVALID_ARG;
+    if (K > 1) {
+        // several kernels, each with one shared decay: chunk-GEMM path, one sequence
+        if (!shared || B != 1 || path == PATH_WALK) return HAWKES_ERR_UNSUPPORTED;
+        path = PATH_GEMM;
+    }
     if (path == 0) path = (shared && M > hk::walk_max_m(grad)) ? PATH_GEMM : PATH_WALK;
     if (path == PATH_WALK && M > hk::walk_max_m(grad)) return HAWKES_ERR_UNSUPPORTED;
     if (path == PATH_GEMM && (!shared || B != 1)) return HAWKES_ERR_UNSUPPORTED;
@@ -57,6 +68,10 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     if (C < 1 || C > 4096) return HAWKES_ERR_INVALID_ARG;
     if (path == PATH_GEMM && C > 1024) return HAWKES_ERR_INVALID_ARG;
     if (path == PATH_GEMM && M > 128 * 128) return HAWKES_ERR_UNSUPPORTED;
+    // per-mark shared-memory histograms of the epilogue: 5 M floats, or (4 K + 1) M
+    if (path == PATH_GEMM &&
+        sizeof(float) * (K > 1 ? 4 * (size_t)K + 1 : 5) * (size_t)M > kMaxDynamicSmem)
+        return HAWKES_ERR_UNSUPPORTED;
     pl->path = path;
     pl->C = C;
     // mark blocks for the pair kernels: at most 128 marks per block, and about 26 events
@@ -122,7 +137,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_Aint = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
         pl->off_Bint = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
         if (grad) pl->off_wbuf = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
-        pl->off_cen = take(sizeof(float) * 4 * (size_t)M);
+        pl->off_cen = take(sizeof(float) * 2 * (size_t)M);
         pl->off_wsum = take(sizeof(double) * (size_t)M);
         pl->off_Y = take(sizeof(float) * nbM);
         pl->off_isc = take(sizeof(float) * (3 * (size_t)M + 2 * (size_t)pl->nb_max));
@@ -143,7 +158,10 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
             pl->off_St_l = take(h * (size_t)M * pl->nbp);
         }
     }
-    pl->total = o_;
+    pl->scratch_off = path == PATH_GEMM ? take(sizeof(float) * ((size_t)M + 2)) : 0;
+    pl->K = K;
+    pl->slice = align_up(o_);
+    pl->total = (size_t)K * pl->slice;
     return 0;
 }
 
@@ -194,6 +212,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.dal_part = at<float>(ws, pl.off_dal_part);
     p.dal_parts_max = pl.dal_parts_max;
     p.dal_parts = 0;
+    p.scratch = at<float>(ws, pl.scratch_off);
     p.at = at<float>(ws, pl.off_at);
     p.bstart = at<int32_t>(ws, pl.off_bstart);
     p.wide = at<uint8_t>(ws, pl.off_wide);
@@ -201,9 +220,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.Bint = at<float>(ws, pl.off_Bint);
     p.wbuf = at<float>(ws, pl.off_wbuf);
     p.cen_S = at<float>(ws, pl.off_cen);
-    p.cen_G = p.cen_S ? p.cen_S + M : nullptr;
-    p.bias_Y = p.cen_S ? p.cen_S + 2 * M : nullptr;
-    p.bias_Z = p.cen_S ? p.cen_S + 3 * M : nullptr;
+    p.bias_Y = p.cen_S ? p.cen_S + M : nullptr;
     p.wsum_acc = at<double>(ws, pl.off_wsum);
     p.isc_al = at<float>(ws, pl.off_isc);
     p.isc_S = p.isc_al ? p.isc_al + M : nullptr;
@@ -251,6 +268,81 @@ int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStr
     return HAWKES_OK;
 }
 
+// Several decay kernels: slice q of the workspace is a complete one-kernel problem for
+// (alpha_q, beta_q); the slices run their forward parts, one epilogue combines them, they
+// run their backward parts (each writing d_alpha_q, d_beta_q), and a last kernel assembles
+// L and the status.  Slices q > 0 leave out -T sum(mu) and write L and dmu to scratch.
+int run_multi(hk::Problem& base, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {
+    Plan pl;
+    int rc = make_plan(base.N, base.M, 1, base.grad, o, &pl);
+    if (rc) return rc;
+    if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < pl.total) return HAWKES_ERR_WORKSPACE;
+    const int K = pl.K, M = base.M;
+    const int validate = o ? o->validate : 1;
+    hk::Problem p[hk::kMaxKernels];
+    hk::MultiSlices ms{};
+    ms.K = K;
+    for (int q = 0; q < K; ++q) {
+        void* wq = (char*)ws + (size_t)q * pl.slice;
+        hk::WsHeader* hdr = (hk::WsHeader*)wq;
+        p[q] = base;
+        bind(p[q], wq, pl, 1, M, base.grad);
+        p[q].off = (const int64_t*)&hdr->pad[0];
+        p[q].Tarr = (const double*)&hdr->pad[2];
+        p[q].alpha = base.alpha + (size_t)q * M * M;
+        p[q].beta = base.beta + q;
+        p[q].validated = validate ? 1 : 0;
+        if (base.grad) {
+            p[q].d_alpha = base.d_alpha + (size_t)q * M * M;
+            p[q].d_beta = base.d_beta + q;
+        }
+        if (q > 0) {
+            p[q].base_term = 0;
+            p[q].out_ll = (double*)p[q].scratch;     // 8-byte aligned: the region is 256-aligned
+            if (base.grad) p[q].d_mu = p[q].scratch + 2;
+            p[q].wbuf = p[0].wbuf;                   // one w per event, written by the epilogue
+        }
+        ms.k[q].Y = p[q].Y;
+        ms.k[q].Z = p[q].Z;
+        ms.k[q].A = p[q].Aint;
+        ms.k[q].B = p[q].Bint;
+        ms.k[q].W = p[q].W;
+        ms.k[q].E_acc = p[q].E_acc;
+        ms.k[q].F_acc = p[q].F_acc;
+        ms.k[q].dbe_acc = p[q].dbe_acc;
+        ms.k[q].wsum_acc = p[q].wsum_acc;
+        ms.k[q].beta = p[q].beta;
+        ms.k[q].hdr = p[q].hdr;
+        ms.k[q].out_ll = p[q].out_ll;
+    }
+    int nl = 0;
+    if (g_prof.on) {
+        g_prof.n = 0;
+        cudaEventRecord(g_prof.ev[0], s);
+    }
+    cudaError_t err = cudaSuccess;
+    for (int q = 0; q < K && err == cudaSuccess; ++q) {
+        err = hk::launch_prepare(p[q], s, validate, &nl);
+        if (err == cudaSuccess) err = hk::launch_scan(p[q], s, &nl);
+        if (err == cudaSuccess) err = hk::launch_gemm_forward(p[q], s, &nl);
+    }
+    if (err == cudaSuccess) err = hk::launch_epilogue_multi(p[0], ms, s, &nl);
+    for (int q = 0; q < K && err == cudaSuccess; ++q) err = hk::launch_gemm_backward(p[q], s, &nl);
+    if (err == cudaSuccess) {
+        hk::Problem caller = p[0];
+        caller.out_ll = base.out_ll;
+        caller.d_alpha = base.d_alpha;
+        caller.d_beta = base.d_beta;
+        err = hk::launch_finalize_multi(caller, ms, s, &nl);
+    }
+    g_last_launches = nl;
+    if (err != cudaSuccess) {
+        fprintf(stderr, "hawkes_gb300: CUDA error %s\n", cudaGetErrorString(err));
+        return HAWKES_ERR_CUDA;
+    }
+    return HAWKES_OK;
+}
+
 bool bad_ptrs(std::initializer_list<const void*> ps) {
     for (const void* q : ps)
         if (!q) return true;
@@ -276,6 +368,7 @@ hawkes_opts hawkes_default_opts(void) {
     o.chunk = 0;
     o.validate = 1;
     o.path = 0;
+    o.kernels = 1;
     return o;
 }
 
@@ -315,6 +408,10 @@ static hawkes_status single(const double* t, const int32_t* c, int64_t N, double
     p.shared = opts ? opts->beta_shared : 0;
     p.grad = grad;
     p.out_ll = out_ll; p.d_mu = d_mu; p.d_alpha = d_alpha; p.d_beta = d_beta;
+    if (pl.K > 1) {
+        if (carry_S || carry_G || !base_term) return HAWKES_ERR_UNSUPPORTED;
+        return (hawkes_status)run_multi(p, opts, ws, ws_bytes, s);
+    }
     return (hawkes_status)run(p, opts, ws, ws_bytes, s);
 }
 
@@ -434,6 +531,7 @@ hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t
     if (N < 0 || M <= 0) return HAWKES_ERR_INVALID_ARG;
     if (bad_ptrs({mu, alpha, beta, out_ll, d_mu, d_alpha, d_beta})) return HAWKES_ERR_INVALID_ARG;
     if (N > 0 && bad_ptrs({t, c})) return HAWKES_ERR_INVALID_ARG;
+    if (opts && opts->kernels > 1) return HAWKES_ERR_UNSUPPORTED;   // one kernel only here
     size_t dev = hawkes_workspace_size(N, M, 1, 1, opts);
     if (!dev) return HAWKES_ERR_UNSUPPORTED;
     if (!workspace || workspace_bytes < hawkes_workspace_size_host(N, M, opts))

@@ -70,19 +70,20 @@ struct Problem {
     float* dal_part;         // [dal_parts][P*P][128*128] backward pair tiles of the chunk-GEMM path
     int32_t dal_parts;       // chunk ranges of the backward pair kernel (set at launch)
     int32_t dal_parts_max;   // capacity of dal_part in ranges
+    float* scratch;          // [M + 2] outputs of a slice that the caller does not see
     double* dbe_acc;         // [B*M] excitation part of dbeta
     double* E_acc;           // [B*M] sum (1 - exp(-beta (T - t))) per source
     double* F_acc;           // [B*M] sum (T - t) exp(-beta (T - t)) per source
     double* colsum;          // [B*M] sum_i alpha[s][i][j]
     // chunk-GEMM path
     float* Y;                // [nb_max*M]  alpha . Shat_b
-    float* Z;                // [nb_max*M]  alpha . Ghat_b
+    float* Z;                // [nb_max*M]  alpha . (Shat_b - beta Ghat_b)
     float* W;                // [nb_max*M]  per-chunk weights of the dalpha GEMM
     float* dal_gemm;         // [M*M]
     // fp16 hi/lo operands of the tensor-core GEMMs (rows scaled by powers of two)
     __half *al_h, *al_l;     // [M][ldk]       alpha
     __half *S_h, *S_l;       // [nb_max][ldk]  chunk-start states
-    __half *G_h, *G_l;       // [nb_max][ldk]
+    __half *G_h, *G_l;       // [nb_max][ldk]  Shat - beta Ghat
     __half *Wt_h, *Wt_l;     // [M][nbp]       W transposed (chunks contiguous)
     __half *St_h, *St_l;     // [M][nbp]       S^ transposed
     float *isc_al, *isc_S, *isc_G, *isc_Wt, *isc_St;   // inverse row scales of the operands
@@ -102,9 +103,7 @@ struct Problem {
     // centering of the GEMM operands (the tensor-core accumulation error is one-signed
     // for same-signed operands; centred operands make it unbiased)
     float* cen_S;            // [M] m_j = n_j / (beta T): stationary mean of S_j
-    float* cen_G;            // [M] m_j / beta:           stationary mean of G_j
     float* bias_Y;           // [M] alpha . cen_S  (FP64-accumulated)
-    float* bias_Z;           // [M] alpha . cen_G
     double* wsum_acc;        // [M] sum_b W[b][i]
     int64_t ldk;             // M rounded up to 8
     int64_t nbp;             // nb_max rounded up to 8
@@ -121,6 +120,38 @@ __device__ __forceinline__ void set_status(WsHeader* h, int code) {
 
 __device__ __forceinline__ bool failed(const WsHeader* h) {
     return *((volatile const int32_t*)&h->status) != 0;
+}
+
+// exp(x) in FP32 arithmetic whose rounding error has no systematic sign.  The decay
+// factors exp(-beta dt) are multiplied along the chain of chunk (and event) steps, so a
+// one-signed error of a fraction of an ulp per factor grows with the chain length, and
+// the decay gradient (a small difference of state sums) amplifies it; an error of
+// either sign at random does neither.  Method: Cody-Waite reduction x = k ln2 + r with
+// ln2 split as 355/512 + c2 (k * 355/512 is exact for |k| < 2^15) and |r| <= ln2 / 2
+// (k = 0 for |x| < ln2 / 2), the Taylor series e^r - 1 = r + r^2 (1/2! + r/3! + ... +
+// r^6/8!) (truncation below 2.2e-10), one rounding of 1 + (e^r - 1), and the exact
+// scaling by 2^k.  Exact 1 at x = 0, 0 below -104, +inf above 88.8.
+__device__ __forceinline__ float exp_unbiased(float x) {
+    float k = 0.f, r = x;
+    if (!(fabsf(x) < 0.34657359f)) {
+        if (x < -104.f) return 0.f;
+        if (x > 88.8f) return __int_as_float(0x7f800000);
+        k = rintf(x * 1.44269504f);
+        r = fmaf(-k, 0.693359375f, x);
+        r = fmaf(-k, -2.12194440e-4f, r);
+    }
+    float q = fmaf(r, 1.f / 40320.f, 1.f / 5040.f);
+    q = fmaf(q, r, 1.f / 720.f);
+    q = fmaf(q, r, 1.f / 120.f);
+    q = fmaf(q, r, 1.f / 24.f);
+    q = fmaf(q, r, 1.f / 6.f);
+    q = fmaf(q, r, 0.5f);
+    const float y = 1.f + fmaf(r * r, q, r);
+    int ki = (int)k;
+    if (ki == 0) return y;
+    if (ki < -126) return (y * 0x1p-64f) * __int_as_float((ki + 64 + 127) << 23);
+    if (ki > 127) return (y * 2.f) * __int_as_float((ki - 1 + 127) << 23);
+    return y * __int_as_float((ki + 127) << 23);
 }
 
 __device__ __forceinline__ float beta_of(const Problem& p, int32_t seq, int32_t j) {
@@ -163,6 +194,35 @@ cudaError_t launch_prepare(const Problem& p, cudaStream_t s, int validate, int* 
 cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nlaunch);
+
+// Several decay kernels: one workspace slice per kernel, each a complete single-kernel
+// problem; the epilogue and the last step of the finalisation combine the slices.
+constexpr int kMaxKernels = 4;
+struct KernelSlice {
+    const float* Y;
+    const float* Z;
+    const float* A;          // intra-chunk pair sums A_k, B_k of this kernel
+    const float* B;
+    float* W;                // rows of this kernel's dalpha GEMM
+    double* E_acc;
+    double* F_acc;
+    double* dbe_acc;
+    double* wsum_acc;
+    const float* beta;       // this kernel's decay (one value)
+    WsHeader* hdr;
+    double* out_ll;          // this slice's partial log-likelihood
+};
+struct MultiSlices {
+    int32_t K;
+    KernelSlice k[kMaxKernels];
+};
+cudaError_t launch_epilogue_multi(const Problem& p0, const MultiSlices& ms, cudaStream_t s,
+                                  int* nlaunch);
+cudaError_t launch_finalize_multi(const Problem& p0, const MultiSlices& ms, cudaStream_t s,
+                                  int* nlaunch);
 cudaError_t launch_finalize(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_slice_aggregate(const Problem& p, double t_next, float* agg_S, float* agg_G,
                                    cudaStream_t s, int* nlaunch);

@@ -120,4 +120,48 @@ cudaError_t launch_finalize(const Problem& p, cudaStream_t s, int* nl) {
     return launch_finalize_mode(p, s, 0, nl);
 }
 
+// Last step for several decay kernels: L = slice 0's value (its log-sum, -T sum mu and its
+// compensator) + every other slice's (minus its compensator); the first (smallest) error
+// code of any slice becomes the caller's, and then every output is NaN.
+__global__ void k_finalize_multi(Problem p, MultiSlices ms) {
+    __shared__ int code_sh;
+    if (threadIdx.x == 0) {
+        int code = 0;
+        for (int q = 0; q < ms.K; ++q) {
+            const int s = ms.k[q].hdr->status;
+            if (s != 0 && (code == 0 || s < code)) code = s;
+        }
+        code_sh = code;
+        if (code != 0) p.hdr->status = code;
+        if (blockIdx.x == 0 && code == 0) {
+            double ll = ms.k[0].out_ll[0];
+            for (int q = 1; q < ms.K; ++q) ll += ms.k[q].out_ll[0];
+            p.out_ll[0] = ll;
+        }
+    }
+    __syncthreads();
+    if (code_sh == 0) return;
+    const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+    const float nanf = (float)nanv;
+    const int64_t M = p.M, KM2 = (int64_t)ms.K * M * M;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i0 == 0) p.out_ll[0] = nanv;
+    if (p.grad) {
+        for (int64_t i = i0; i < M; i += stride) p.d_mu[i] = nanf;
+        for (int64_t i = i0; i < KM2; i += stride) p.d_alpha[i] = nanf;
+        for (int64_t i = i0; i < ms.K; i += stride) p.d_beta[i] = nanf;
+    }
+}
+
+// p: the caller's view (slice 0's workspace, all K kernels' gradient outputs).
+cudaError_t launch_finalize_multi(const Problem& p, const MultiSlices& ms, cudaStream_t s, int* nl) {
+    int64_t total = (int64_t)ms.K * p.M * p.M;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_finalize_multi<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, ms);
+    ++*nl;
+    return cudaGetLastError();
+}
+
 }  // namespace hk

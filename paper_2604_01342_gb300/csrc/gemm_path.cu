@@ -29,14 +29,15 @@ cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const
                           const float* inv_sb);
 cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo, int64_t ldd,
                            int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
-                           const int64_t* rows_valid, float* inv_scale);
+                           const int64_t* rows_valid, float* inv_scale, const float* sub,
+                           const float* coef);
 cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
                                 int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
                                 cudaStream_t s, const float* centre, uint32_t* amax_bits,
                                 float* inv_scale);
 
-// Centres of the GEMM operands: the stationary means m_j = n_j / (beta T) of S_j and
-// m_j / beta of G_j (n_j = events of mark j), and the exact products alpha . m in FP64.
+// Centre of the Y GEMM operand: the stationary means m_j = n_j / (beta T) of S_j, and the
+// exact products alpha . m in FP64.  (The Z operand S - beta G has stationary mean 0.)
 // One warp per row of alpha.
 __global__ void k_centres(Problem p, int have_counts) {
     const int M = p.M;
@@ -44,31 +45,16 @@ __global__ void k_centres(Problem p, int have_counts) {
     const double T = p.Tarr[0];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    auto centre = [&](int j) -> double {
-        return (have_counts && T > 0.0) ? (double)p.counts[j] / ((double)beta * T) : 0.0;
+    auto centre = [&](int j) -> float {
+        return (have_counts && T > 0.0) ? (float)((double)p.counts[j] / ((double)beta * T)) : 0.f;
     };
     if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < M; j += blockDim.x) {
-            const double m = centre(j);
-            p.cen_S[j] = (float)m;
-            p.cen_G[j] = (float)(m / beta);
-        }
+        for (int j = threadIdx.x; j < M; j += blockDim.x) p.cen_S[j] = centre(j);
     for (int i = warp; i < M; i += nwarps) {
-        double y = 0.0, z = 0.0;
-        for (int j = lane; j < M; j += 32) {
-            const double a = (double)p.alpha[(int64_t)i * M + j];
-            const double m = (double)(float)centre(j);
-            y += a * m;
-            z += a * (double)(float)(centre(j) / beta);
-        }
-        for (int o = 16; o >= 1; o >>= 1) {
-            y += __shfl_xor_sync(HK_FULL, y, o);
-            z += __shfl_xor_sync(HK_FULL, z, o);
-        }
-        if (lane == 0) {
-            p.bias_Y[i] = (float)y;
-            p.bias_Z[i] = (float)z;
-        }
+        double y = 0.0;
+        for (int j = lane; j < M; j += 32) y += (double)p.alpha[(int64_t)i * M + j] * (double)centre(j);
+        for (int o = 16; o >= 1; o >>= 1) y += __shfl_xor_sync(HK_FULL, y, o);
+        if (lane == 0) p.bias_Y[i] = (float)y;
     }
 }
 
@@ -192,8 +178,8 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             int irank = __popc(mq[i >> 5] & ((1u << (i & 31)) - 1u));
             for (int w = 0; w < (i >> 5); ++w) irank += __popc(mq[w]);
             const float d = (float)(p.t[s0 + i] - tau);
-            const float em = expf(-beta * d);
-            const float ep = isw ? 0.f : expf(beta * d);
+            const float em = exp_unbiased(-beta * d);
+            const float ep = isw ? 0.f : exp_unbiased(beta * d);
             recs[s0 + base[q] + rank] = make_float4(d, em, ep, __int_as_float((i << 16) | (ck / P)));
             lrec[s0 + base[q] + irank] = make_float2(ep, __int_as_float(ck / P));
         }
@@ -537,7 +523,7 @@ __global__ void __launch_bounds__(256) k_epilogue(Problem p, const float* Aint, 
             const double tk = p.t[k];
             const int ck = p.c[k];
             const float delta = (float)(tk - tau);
-            const float ek = expf(-beta * delta);
+            const float ek = exp_unbiased(-beta * delta);
             const float y = p.Y[b * M + ck];
             const float aS = ek * y + Aint[k];
             const float lam = p.mu[ck] + beta * aS;
@@ -547,13 +533,12 @@ __global__ void __launch_bounds__(256) k_epilogue(Problem p, const float* Aint, 
             atomicAdd(&hE[ck], -expm1f(-beta * xT));
             if (GRAD) {
                 const float w = 1.f / lam;
-                const float z = p.Z[b * M + ck];
-                const float aG = ek * (delta * y + z) + Bint[k];
-                db += (double)(w * (aS - beta * aG));
+                const float x = p.Z[b * M + ck];
+                db += (double)(w * (ek * (x - beta * delta * y) + (Aint[k] - beta * Bint[k])));
                 wbuf[k] = w;
                 atomicAdd(&Wrow[ck], w * ek);
                 atomicAdd(&hmu[ck], w);
-                atomicAdd(&hF[ck], xT * expf(-beta * xT));
+                atomicAdd(&hF[ck], xT * exp_unbiased(-beta * xT));
             }
         }
         if (GRAD) {
@@ -589,10 +574,12 @@ __global__ void __launch_bounds__(256) k_epilogue(Problem p, const float* Aint, 
     }
 }
 
-cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
+// Everything of the chunk-GEMM path before the per-event epilogue: operand centres and
+// splits, Y and Z on the tensor cores, bucketing and the forward pairs.
+cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     cudaError_t err;
     const int64_t M = p.M, nb = p.nb_max;
-    // Y = S^ alpha^T and Z = G^ alpha^T on the tensor cores (rows = chunks)
+    // Y = S^ alpha^T and Z = (S^ - beta G^) alpha^T on the tensor cores (rows = chunks)
     // mark counts exist only when the inputs were validated; without them the centre is 0
     cudaMemsetAsync(p.wsum_acc, 0, sizeof(double) * (size_t)M, s);
     k_centres<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(p, p.validated);
@@ -601,12 +588,12 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int64_t* nb_dev = p.chunk_base + p.B;   // number of chunks, on the device
     if ((err = split_f16_rows(p.alpha, M, p.al_h, p.al_l, p.ldk, M, M, s, nullptr, nullptr,
-                              p.isc_al)) != cudaSuccess)
+                              p.isc_al, nullptr, nullptr)) != cudaSuccess)
         return err;
     ++*nl;
     prof_mark(s, "split_alpha");
     if ((err = split_f16_rows(p.Shat, M, p.S_h, p.S_l, p.ldk, nb, M, s, p.cen_S, nb_dev,
-                              p.isc_S)) != cudaSuccess)
+                              p.isc_S, nullptr, nullptr)) != cudaSuccess)
         return err;
     ++*nl;
     prof_mark(s, "split_S");
@@ -617,19 +604,22 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     ++*nl;
     prof_mark(s, "gemm_Y");
     if (p.grad) {
-        if ((err = split_f16_rows(p.Ghat, M, p.G_h, p.G_l, p.ldk, nb, M, s, p.cen_G, nb_dev,
-                                  p.isc_G)) != cudaSuccess)
+        // Z = (S^ - beta G^) alpha^T: the decay-gradient term of an event is
+        // e (Z - beta delta Y) + (A - beta B), so the near-cancelling difference of the
+        // forward state and its beta-derivative is formed once per chunk and element from
+        // the scan's states, before any rounding of the tensor-core product
+        if ((err = split_f16_rows(p.Shat, M, p.G_h, p.G_l, p.ldk, nb, M, s, nullptr, nb_dev,
+                                  p.isc_G, p.Ghat, p.beta)) != cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "split_G");
         if ((err = tc_gemm_f16x3(p.G_h, p.G_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Z, M, (int)nb,
-                                 (int)M, M, 1, false, p.hdr, s, p.bias_Z, p.isc_G, p.isc_al)) !=
+                                 (int)M, M, 1, false, p.hdr, s, nullptr, p.isc_G, p.isc_al)) !=
             cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "gemm_Z");
     }
-    int64_t dal_parts = 0;   // chunk ranges of the backward pair kernel
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -662,6 +652,16 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         prof_mark(s, "pairs_fwd");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
+    return cudaSuccess;
+}
+
+// The per-event epilogue of one kernel.
+cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nl) {
+    cudaError_t err;
+    const int64_t M = p.M, nb = p.nb_max;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     {
         const size_t smem = sizeof(float) * 5 * (size_t)M;
         auto kern = p.grad ? k_epilogue<true> : k_epilogue<false>;
@@ -678,6 +678,20 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
         prof_mark(s, "epilogue");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
+    return cudaSuccess;
+}
+
+// Everything after the epilogue: row groups and backward pairs, the dalpha GEMM and the
+// finalisation (mode 1).
+cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
+    cudaError_t err;
+    const int64_t M = p.M, nb = p.nb_max;
+    const int64_t* nb_dev = p.chunk_base + p.B;   // number of chunks, on the device
+    int64_t dal_parts = 0;   // chunk ranges of the backward pair kernel
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int P = p.P;
     if (p.grad) {
         int64_t blocks = (nb * P + 7) / 8;
         if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
@@ -753,6 +767,157 @@ cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
     Problem q = p;
     q.dal_parts = (int32_t)dal_parts;
     return launch_finalize_mode(q, s, 1, nl);
+}
+
+// ---------------------------------------------------------------------------
+// Several decay kernels (paper, Eq. hawkes_excitation with its sum over kernels q):
+//     lambda_k = mu_{c_k} + sum_q beta_q (e^(q)_k Y^(q)_b[c_k] + A^(q)_k),
+// every kernel's Y, Z, A, B coming from its own workspace slice.  With w_k = 1 / lambda_k
+// shared by the kernels, each kernel q gets its own W rows (w_k e^(q)_k), decay-gradient
+// sum w_k (e^(q)_k (Z^(q)_b[c_k] - beta_q delta_k Y^(q)_b[c_k]) + A^(q)_k - beta_q B^(q)_k)
+// and compensator sums, in its own slice, so that the
+// slice's backward part and finalisation then produce dalpha^(q) and dbeta_q; the
+// log-sum and dmu go to slice 0.
+// ---------------------------------------------------------------------------
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_epilogue_multi(Problem p, MultiSlices ms, float* wbuf,
+                                                        int64_t chunks_per_cta) {
+    extern __shared__ float sh[];
+    const int M = p.M, K = ms.K;
+    float* Wrow = sh;                  // [K][M]
+    float* hE = Wrow + K * M;          // [K][M]
+    float* hF = hE + K * M;            // [K][M]
+    float* hws = hF + K * M;           // [K][M]
+    float* hmu = hws + K * M;          // [M]
+    __shared__ double red_ll[8];
+    __shared__ double red_db[kMaxKernels][8];
+    for (int q = 0; q < K; ++q)
+        if (failed(ms.k[q].hdr)) return;
+    const int64_t nb = num_chunks(p);
+    const int64_t b0 = (int64_t)blockIdx.x * chunks_per_cta;
+    const int64_t b1 = b0 + chunks_per_cta < nb ? b0 + chunks_per_cta : nb;
+    if (b0 >= b1) return;
+    float beta[kMaxKernels];
+#pragma unroll
+    for (int q = 0; q < kMaxKernels; ++q) beta[q] = q < K ? ms.k[q].beta[0] : 0.f;
+    const double T = p.Tarr[0];
+    for (int j = threadIdx.x; j < (4 * K + 1) * M; j += blockDim.x) sh[j] = 0.f;
+    __syncthreads();
+    LogProd lp;
+    double db[kMaxKernels] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t b = b0; b < b1; ++b) {
+        int64_t s0, s1;
+        chunk_range(p, b, 0, s0, s1);
+        const double tau = p.t[s0];
+        for (int64_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+            const double tk = p.t[k];
+            const int ck = p.c[k];
+            const float delta = (float)(tk - tau);
+            float e[kMaxKernels], y[kMaxKernels], aS[kMaxKernels];
+            float exc = 0.f;
+#pragma unroll
+            for (int q = 0; q < kMaxKernels; ++q) {
+                if (q < K) {
+                    e[q] = exp_unbiased(-beta[q] * delta);
+                    y[q] = ms.k[q].Y[b * M + ck];
+                    aS[q] = e[q] * y[q] + ms.k[q].A[k];
+                    exc += beta[q] * aS[q];
+                }
+            }
+            const float lam = p.mu[ck] + exc;
+            if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
+            lp.mul(lam);
+            const float xT = (float)(T - tk);
+#pragma unroll
+            for (int q = 0; q < kMaxKernels; ++q)
+                if (q < K) atomicAdd(&hE[q * M + ck], -expm1f(-beta[q] * xT));
+            if (GRAD) {
+                const float w = 1.f / lam;
+                wbuf[k] = w;
+                atomicAdd(&hmu[ck], w);
+#pragma unroll
+                for (int q = 0; q < kMaxKernels; ++q) {
+                    if (q < K) {
+                        const float x = ms.k[q].Z[b * M + ck];
+                        db[q] += (double)(w * (e[q] * (x - beta[q] * delta * y[q]) +
+                                               (ms.k[q].A[k] - beta[q] * ms.k[q].B[k])));
+                        atomicAdd(&Wrow[q * M + ck], w * e[q]);
+                        atomicAdd(&hF[q * M + ck], xT * exp_unbiased(-beta[q] * xT));
+                    }
+                }
+            }
+        }
+        if (GRAD) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < K * M; e += blockDim.x) {
+                const int q = e / M, j = e % M;
+                ms.k[q].W[b * M + j] = Wrow[e];
+                hws[e] += Wrow[e];
+                Wrow[e] = 0.f;
+            }
+            __syncthreads();
+        }
+    }
+    double ll = lp.log_value();
+    for (int o = 16; o >= 1; o >>= 1) {
+        ll += __shfl_xor_sync(HK_FULL, ll, o);
+#pragma unroll
+        for (int q = 0; q < kMaxKernels; ++q) db[q] += __shfl_xor_sync(HK_FULL, db[q], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_ll[threadIdx.x >> 5] = ll;
+#pragma unroll
+        for (int q = 0; q < kMaxKernels; ++q) red_db[q][threadIdx.x >> 5] = db[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red_ll[w];
+        atomicAdd(&p.ll_acc[0], a);
+        if (GRAD)
+            for (int q = 0; q < K; ++q) {
+                double d = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) d += red_db[q][w];
+                atomicAdd(&ms.k[q].dbe_acc[0], d);
+            }
+    }
+    for (int e = threadIdx.x; e < K * M; e += blockDim.x) {
+        const int q = e / M, j = e % M;
+        if (hE[e] != 0.f) atomicAdd(&ms.k[q].E_acc[j], (double)hE[e]);
+        if (GRAD) {
+            if (hF[e] != 0.f) atomicAdd(&ms.k[q].F_acc[j], (double)hF[e]);
+            if (hws[e] != 0.f) atomicAdd(&ms.k[q].wsum_acc[j], (double)hws[e]);
+        }
+    }
+    if (GRAD)
+        for (int j = threadIdx.x; j < M; j += blockDim.x)
+            if (hmu[j] != 0.f) atomicAdd(&p.dmu_acc[j], (double)hmu[j]);
+}
+
+cudaError_t launch_epilogue_multi(const Problem& p, const MultiSlices& ms, cudaStream_t s, int* nl) {
+    const int64_t M = p.M, nb = p.nb_max;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = sizeof(float) * (4 * (size_t)ms.K + 1) * (size_t)M;
+    auto kern = p.grad ? k_epilogue_multi<true> : k_epilogue_multi<false>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int64_t blocks = (int64_t)sms * 4;
+    int64_t per = (nb + blocks - 1) / blocks;
+    if (per < 1) per = 1;
+    blocks = (nb + per - 1) / per;
+    kern<<<(unsigned)(blocks > 0 ? blocks : 1), 256, smem, s>>>(p, ms, p.wbuf, per);
+    ++*nl;
+    prof_mark(s, "epilogue");
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
+    cudaError_t err = launch_gemm_forward(p, s, nl);
+    if (err == cudaSuccess) err = launch_gemm_epilogue(p, s, nl);
+    if (err == cudaSuccess) err = launch_gemm_backward(p, s, nl);
+    return err;
 }
 
 }  // namespace hk

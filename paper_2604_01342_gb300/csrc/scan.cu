@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
         }
         const double tn = p.t[s1];            // start of the next chunk
         const float D = (float)(tn - p.t[s0]);
+        const float dsh = p.shared ? exp_unbiased(-beta_of(p, seq, 0) * D) : 0.f;
         for (int j = threadIdx.x; j < M; j += blockDim.x) {
-            float d = expf(-beta_of(p, seq, j) * D);
+            float d = p.shared ? dsh : exp_unbiased(-beta_of(p, seq, j) * D);
             float s = S[j];
             if (GRAD) G[j] = d * (G[j] + D * s);
             S[j] = d * s;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
         for (int64_t l = s0 + threadIdx.x; l < s1; l += blockDim.x) {
             int32_t cl = p.c[l];
             float x = (float)(tn - p.t[l]);
-            float e = expf(-beta_of(p, seq, cl) * x);
+            float e = exp_unbiased(-beta_of(p, seq, cl) * x);
             atomicAdd(&S[cl], e);
             if (GRAD) atomicAdd(&G[cl], x * e);
         }
@@ -116,7 +117,7 @@ __device__ __forceinline__ void group_map(const Problem& p, int64_t g, int j, fl
     gg = p.grp_g ? p.grp_g[g * M + j] : 0.f;
     dt = (float)p.grp_dt[g];
     reset = p.grp_reset[g] != 0;
-    d = reset ? 0.f : expf(-beta_of(p, p.chunk_seq[g * p.Gc], j) * dt);
+    d = reset ? 0.f : exp_unbiased(-beta_of(p, p.chunk_seq[g * p.Gc], j) * dt);
 }
 
 template <bool GRAD>
@@ -206,7 +207,7 @@ __global__ void k_slice_aggregate(Problem p, double t_next, float* agg_S, float*
          k += (int64_t)gridDim.x * blockDim.x) {
         const int ck = p.c[k];
         const float x = (float)(t_next - p.t[k]);
-        const float e = expf(-beta_of(p, 0, ck) * x);
+        const float e = exp_unbiased(-beta_of(p, 0, ck) * x);
         atomicAdd(&hS[ck], e);
         atomicAdd(&hG[ck], x * e);
     }

@@ -415,18 +415,26 @@ cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const
 }
 
 // One warp per row r < rows of an FP32 matrix [rows][cols] (row stride lds), minus an
-// optional per-column centre: the row's scale exponent from its largest magnitude, the
+// optional per-column centre and minus an optional (*coef) * sub[r][c] (same layout as
+// src; coef on the device): the row's scale exponent from its largest magnitude, the
 // fp16 hi/lo split of the scaled row into [rows][ldd], and inv_scale[r] = 2^-a.  Rows at
 // or past *rows_valid (when given) are written as zeros.
 __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __half* hi,
                                  __half* lo, int64_t ldd, int64_t rows, int64_t cols,
                                  const float* __restrict__ centre, const int64_t* rows_valid,
-                                 float* inv_scale) {
+                                 float* inv_scale, const float* __restrict__ sub,
+                                 const float* __restrict__ coef) {
     const int lane = threadIdx.x & 31;
     const int64_t nvalid = rows_valid ? *rows_valid : rows;
+    const float cf = sub ? *coef : 0.f;
     const int64_t wpb = blockDim.x >> 5;
     for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
         const float* sr = src + r * lds;
+        const float* ur = sub ? sub + r * lds : nullptr;
+        auto val = [&](int64_t c) {
+            float v = sr[c] - (centre ? centre[c] : 0.f);
+            return ur ? v - cf * ur[c] : v;
+        };
         __half* hr = hi + r * ldd;
         __half* lr = lo + r * ldd;
         if (r >= nvalid) {
@@ -436,14 +444,14 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
         }
         float amax = 0.f;
         for (int64_t c = lane; c < cols; c += 32)
-            amax = fmaxf(amax, fabsf(sr[c] - (centre ? centre[c] : 0.f)));
+            amax = fmaxf(amax, fabsf(val(c)));
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         const int a = tc::row_exponent(amax);
         const float sc = ldexpf(1.f, a);
         for (int64_t c = lane; c < cols; c += 32) {
             __half h, l;
-            tc::split_f16((sr[c] - (centre ? centre[c] : 0.f)) * sc, h, l);
+            tc::split_f16(val(c) * sc, h, l);
             hr[c] = h;
             lr[c] = l;
         }
@@ -453,12 +461,14 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
 
 cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo, int64_t ldd,
                            int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
-                           const int64_t* rows_valid, float* inv_scale) {
+                           const int64_t* rows_valid, float* inv_scale, const float* sub,
+                           const float* coef) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if ((sub == nullptr) != (coef == nullptr)) return cudaErrorInvalidValue;
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_split_f16_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, centre,
-                                                      rows_valid, inv_scale);
+                                                      rows_valid, inv_scale, sub, coef);
     return cudaGetLastError();
 }
 
@@ -546,8 +556,8 @@ extern "C" int hawkes_test_tc_gemm(const float* A, const float* B, float* D, int
            *Bl = Bh + (int64_t)N * ld;
     float* inv_a = (float*)(Bl + (int64_t)N * ld);
     float* inv_b = inv_a + M;
-    if (split_f16_rows(A, K, Ah, Al, ld, M, K, s, nullptr, nullptr, inv_a) != cudaSuccess) return 1;
-    if (split_f16_rows(B, K, Bh, Bl, ld, N, K, s, nullptr, nullptr, inv_b) != cudaSuccess) return 1;
+    if (split_f16_rows(A, K, Ah, Al, ld, M, K, s, nullptr, nullptr, inv_a, nullptr, nullptr) != cudaSuccess) return 1;
+    if (split_f16_rows(B, K, Bh, Bl, ld, N, K, s, nullptr, nullptr, inv_b, nullptr, nullptr) != cudaSuccess) return 1;
     if (splits > 1) cudaMemsetAsync(D, 0, sizeof(float) * (size_t)M * N, s);
     return tc_gemm_f16x3(Ah, Al, ld, Bh, Bl, ld, D, N, M, N, K, splits, false, nullptr, s,
                          nullptr, inv_a, inv_b) == cudaSuccess

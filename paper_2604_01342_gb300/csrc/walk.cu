@@ -18,11 +18,37 @@
 // from the saved batch-start state (recomputing the decays is cheaper than
 // keeping 32 states per lane).  dt_k and T - t_k are FP64 differences rounded to
 // FP32; the log-sum is taken as the log of an FP64 product (LogProd).
+//
+// Within a batch the recurrence is taken in factorised form from the state (S0, G0)
+// seen by its first event (time t_0; Delta_e = t_e - t_0):
+//     S_e = exp(-beta_j Delta_e) (S0_j + U_j),
+//     G_e = exp(-beta_j Delta_e) (G0_j + Delta_e (S0_j + U_j) - V_j),
+// with U_j, V_j the sums of exp(beta_j Delta_l) and Delta_l exp(beta_j Delta_l) over the
+// batch's earlier events l of mark j.  Each factor exp(-beta Delta_e) is used once, so
+// the one-signed sub-ulp error of expf does not compound along the chain of events;
+// the only chained factor is the step from one batch start to the next, taken with
+// exp_unbiased.  A batch with beta * (t_last - t_0) above kWalkFactorLimit (where the
+// growing factors exp(beta Delta) would lose range or precision) is walked event by
+// event with exp_unbiased steps.
 #include "common.cuh"
 
 namespace hk {
 
 int walk_max_m(int grad) { return grad ? 64 : 256; }
+
+// Largest beta * (t_last - t_first) of a batch walked in the factorised form: keeps
+// exp(+beta Delta) below e^64, so the sums U, V of 32 such terms and the factors
+// exp(-beta Delta) stay normal FP32 numbers (the chunk-GEMM path uses the same bound).
+// Delta_e U - V = sum_l (Delta_e - Delta_l) exp(beta Delta_l) loses about
+// beta Delta_e / (beta (t_e - t_l)) ulps for a close pair (l, e) late in a wide batch: a
+// relative error of at most ~1e-5 of that pair's term of G at beta (t_e - t_l) >= 0.01,
+// of either sign, and G enters the decay gradient only as beta G next to S.
+constexpr float kWalkFactorLimit = 64.f;
+
+// Shared memory of one warp: E, F (and dmu, dalpha with the gradient) per-mark sums.
+__host__ __device__ inline int walk_floats_per_warp(int M, bool grad) {
+    return 2 * M + (grad ? M + M * M : 0);
+}
 
 __device__ __forceinline__ float warp_transpose_reduce(float (&v)[32], int lane) {
 #pragma unroll
@@ -80,7 +106,7 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31;
     const int M = p.M;
-    const int per_warp = 2 * M + (GRAD ? M + M * M : 0);
+    const int per_warp = walk_floats_per_warp(M, GRAD);
     float* E_s = sm + (threadIdx.x >> 5) * per_warp;
     float* F_s = E_s + M;
     float* dmu_s = F_s + M;
@@ -95,7 +121,7 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
     const int64_t b_end = b + chunks_per_warp < nb ? b + chunks_per_warp : nb;
 
     int32_t cur = -1;
-    float bj[R], dbr[R];
+    float bj[R], dbr[R], bmax = 0.f;
     LogProd lp;
     double T = 0.0;
     const float* mu = nullptr;
@@ -118,96 +144,155 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
                 int j = lane + 32 * r;
                 bj[r] = p.shared ? beta_row[0] : (j < M ? beta_row[j] : 0.f);
             }
+            float bm = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) bm = fmaxf(bm, bj[r]);
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(HK_FULL, bm, o));
+            bmax = bm;
         }
         int64_t s0, s1;
         chunk_range(p, b, seq, s0, s1);
-        float S[R], G[R];
+        // S0, G0: the state seen by the first event of the current batch
+        float S0[R], G0[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             int j = lane + 32 * r;
-            S[r] = j < M ? p.Shat[b * M + j] : 0.f;
-            G[r] = (GRAD && j < M) ? p.Ghat[b * M + j] : 0.f;
+            S0[r] = j < M ? p.Shat[b * M + j] : 0.f;
+            G0[r] = (GRAD && j < M) ? p.Ghat[b * M + j] : 0.f;
         }
-        double t_carry = p.t[s0];
-        int32_t c_carry = -1;
         for (int64_t base = s0; base < s1; base += 32) {
             const int64_t k = base + lane;
             const bool valid = k < s1;
             const int nvalid = (int)(s1 - base < 32 ? s1 - base : 32);
-            const double tk = valid ? p.t[k] : t_carry;
+            const double tk = valid ? p.t[k] : p.t[base];
             const int32_t ck = valid ? p.c[k] : 0;
+            const double t0 = __shfl_sync(HK_FULL, tk, 0);
+            const double tl = __shfl_sync(HK_FULL, tk, nvalid - 1);
+            const float De = (float)(tk - t0);             // Delta_e = t_e - t_0
+            const float bc = p.shared ? bj[0] : __ldg(beta_row + ck);
+            const bool fact = bmax * (float)(tl - t0) <= kWalkFactorLimit;   // warp-uniform
+            // factorised: exp(+beta_{c_e} Delta_e) of the own mark, and (one decay) exp(-beta Delta_e)
+            const float ep = fact ? expf(bc * De) : 0.f;
+            const float emsh = (fact && p.shared) ? expf(-bj[0] * De) : 0.f;
+            // chained (batches spanning beta * span > kWalkFactorLimit): step from the previous event
             double tp = __shfl_up_sync(HK_FULL, tk, 1);
-            int32_t cp = __shfl_up_sync(HK_FULL, ck, 1);
-            if (lane == 0) { tp = t_carry; cp = c_carry; }
-            const float dt = (k == s0) ? 0.f : (float)(tk - tp);
-            const bool first = (k == s0);
-            float dsh = 0.f;
-            if (p.shared) dsh = expf(-bj[0] * dt);
-            t_carry = __shfl_sync(HK_FULL, tk, 31);
-            c_carry = __shfl_sync(HK_FULL, ck, 31);
+            const int32_t cp = __shfl_up_sync(HK_FULL, ck, 1);
+            const float dt = lane == 0 ? 0.f : (float)(tk - tp);
+            const float dsh = (!fact && p.shared) ? exp_unbiased(-bj[0] * dt) : 0.f;
 
-            float S0[R], G0[R];
+            float U[R], V[R], S[R], G[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) { S0[r] = S[r]; G0[r] = G[r]; }
-
-            float pp[32];
+            for (int r = 0; r < R; ++r) { U[r] = 0.f; V[r] = 0.f; S[r] = S0[r]; G[r] = G0[r]; }
+            float exc = 0.f;
+            if (fact) {
+                float pp[32];
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                pp[e] = 0.f;
-                const float dte = __shfl_sync(HK_FULL, dt, e);
-                const int32_t cpe = __shfl_sync(HK_FULL, cp, e);
-                const int32_t cee = __shfl_sync(HK_FULL, ck, e);
-                const bool fe = __shfl_sync(HK_FULL, first, e);
-                const float de = __shfl_sync(HK_FULL, dsh, e);
-                if (e < nvalid) {
+                for (int e = 0; e < 32; ++e) {
+                    pp[e] = 0.f;
+                    const int32_t cee = __shfl_sync(HK_FULL, ck, e);
+                    const float Dee = __shfl_sync(HK_FULL, De, e);
+                    const float epe = __shfl_sync(HK_FULL, ep, e);
+                    const float eme = p.shared ? __shfl_sync(HK_FULL, emsh, e) : 0.f;
+                    if (e < nvalid) {
+                        const float* arow = alpha + (int64_t)cee * M;
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            int j = lane + 32 * r;
+                            const float em = p.shared ? eme : expf(-bj[r] * Dee);
+                            const float Sv = em * (S0[r] + U[r]);
+                            if (j == cee) {
+                                U[r] += epe;
+                                if (GRAD) V[r] = fmaf(Dee, epe, V[r]);
+                            }
+                            if (j < M) pp[e] += __ldg(arow + j) * bj[r] * Sv;
+                        }
+                    }
+                }
+                exc = warp_transpose_reduce(pp, lane);
+            } else {
+                // event by event (rare): the dot product of event e by a warp sum
+                for (int e = 0; e < nvalid; ++e) {
+                    const int32_t cee = __shfl_sync(HK_FULL, ck, e);
+                    const float dte = __shfl_sync(HK_FULL, dt, e);
+                    const int32_t cpe = __shfl_sync(HK_FULL, cp, e);
+                    const float de = __shfl_sync(HK_FULL, dsh, e);
                     const float* arow = alpha + (int64_t)cee * M;
+                    float part = 0.f;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         int j = lane + 32 * r;
-                        if (!fe) {
-                            float d = p.shared ? de : expf(-bj[r] * dte);
-                            float P = S[r] + (j == cpe ? 1.f : 0.f);
+                        if (e > 0) {
+                            const float d = p.shared ? de : exp_unbiased(-bj[r] * dte);
+                            const float P = S[r] + (j == cpe ? 1.f : 0.f);
                             if (GRAD) G[r] = d * (G[r] + dte * P);
                             S[r] = d * P;
                         }
-                        if (j < M) pp[e] += __ldg(arow + j) * bj[r] * S[r];
+                        if (j < M) part += __ldg(arow + j) * bj[r] * S[r];
                     }
+#pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(HK_FULL, part, o);
+                    if (lane == e) exc = part;
                 }
             }
-            const float exc = warp_transpose_reduce(pp, lane);
             float w = 0.f;
             if (valid) {
                 const float lam = __ldg(mu + ck) + exc;
                 if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
                 lp.mul(lam);
                 w = 1.f / lam;
-                const float bc = p.shared ? bj[0] : __ldg(beta_row + ck);
                 const float x = (float)(T - tk);
                 atomicAdd(&E_s[ck], -expm1f(-bc * x));
                 if (GRAD) {
-                    atomicAdd(&F_s[ck], x * expf(-bc * x));
+                    atomicAdd(&F_s[ck], x * exp_unbiased(-bc * x));
                     atomicAdd(&dmu_s[ck], w);
                 }
             }
             if (GRAD) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) { S[r] = S0[r]; G[r] = G0[r]; }
+                for (int r = 0; r < R; ++r) { U[r] = 0.f; V[r] = 0.f; S[r] = S0[r]; G[r] = G0[r]; }
+                if (fact) {
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const float dte = __shfl_sync(HK_FULL, dt, e);
-                    const int32_t cpe = __shfl_sync(HK_FULL, cp, e);
-                    const int32_t cee = __shfl_sync(HK_FULL, ck, e);
-                    const bool fe = __shfl_sync(HK_FULL, first, e);
-                    const float de = __shfl_sync(HK_FULL, dsh, e);
-                    const float we = __shfl_sync(HK_FULL, w, e);
-                    if (e < nvalid) {
+                    for (int e = 0; e < 32; ++e) {
+                        const int32_t cee = __shfl_sync(HK_FULL, ck, e);
+                        const float Dee = __shfl_sync(HK_FULL, De, e);
+                        const float epe = __shfl_sync(HK_FULL, ep, e);
+                        const float eme = p.shared ? __shfl_sync(HK_FULL, emsh, e) : 0.f;
+                        const float we = __shfl_sync(HK_FULL, w, e);
+                        if (e < nvalid) {
+                            const float* arow = alpha + (int64_t)cee * M;
+#pragma unroll
+                            for (int r = 0; r < R; ++r) {
+                                int j = lane + 32 * r;
+                                const float em = p.shared ? eme : expf(-bj[r] * Dee);
+                                const float Sx = S0[r] + U[r];
+                                const float Sv = em * Sx;
+                                const float Gv = em * (G0[r] + fmaf(Dee, Sx, -V[r]));
+                                if (j == cee) {
+                                    U[r] += epe;
+                                    V[r] = fmaf(Dee, epe, V[r]);
+                                }
+                                if (j < M) {
+                                    dal_s[cee * M + j] += we * bj[r] * Sv;
+                                    dbr[r] += we * __ldg(arow + j) * (Sv - bj[r] * Gv);
+                                }
+                            }
+                        }
+                    }
+                } else {
+                    for (int e = 0; e < nvalid; ++e) {
+                        const int32_t cee = __shfl_sync(HK_FULL, ck, e);
+                        const float dte = __shfl_sync(HK_FULL, dt, e);
+                        const int32_t cpe = __shfl_sync(HK_FULL, cp, e);
+                        const float de = __shfl_sync(HK_FULL, dsh, e);
+                        const float we = __shfl_sync(HK_FULL, w, e);
                         const float* arow = alpha + (int64_t)cee * M;
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             int j = lane + 32 * r;
-                            if (!fe) {
-                                float d = p.shared ? de : expf(-bj[r] * dte);
-                                float P = S[r] + (j == cpe ? 1.f : 0.f);
+                            if (e > 0) {
+                                const float d = p.shared ? de : exp_unbiased(-bj[r] * dte);
+                                const float P = S[r] + (j == cpe ? 1.f : 0.f);
                                 G[r] = d * (G[r] + dte * P);
                                 S[r] = d * P;
                             }
@@ -216,6 +301,29 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
                                 dbr[r] += we * __ldg(arow + j) * (S[r] - bj[r] * G[r]);
                             }
                         }
+                    }
+                }
+            }
+            // advance to the first event of the next batch of this chunk
+            if (base + 32 < s1) {
+                const double tn = p.t[base + 32];
+                const int32_t cl = __shfl_sync(HK_FULL, ck, 31);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    int j = lane + 32 * r;
+                    if (fact) {
+                        // S0' = D (S0 + U), G0' = D (G0 + Dn (S0 + U) - V), one decay over t_0 -> t_n
+                        const float Dn = (float)(tn - t0);
+                        const float D = exp_unbiased(-bj[r] * Dn);
+                        const float Sx = S0[r] + U[r];
+                        if (GRAD) G0[r] = D * (G0[r] + fmaf(Dn, Sx, -V[r]));
+                        S0[r] = D * Sx;
+                    } else {
+                        const float dn = (float)(tn - tl);
+                        const float D = exp_unbiased(-bj[r] * dn);
+                        const float P = S[r] + (j == cl ? 1.f : 0.f);
+                        if (GRAD) G0[r] = D * (G[r] + dn * P);
+                        S0[r] = D * P;
                     }
                 }
             }
@@ -230,7 +338,7 @@ cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nl) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int warps_per_block = 4;
-    const int per_warp = 2 * p.M + (p.grad ? p.M + p.M * p.M : 0);
+    const int per_warp = walk_floats_per_warp(p.M, p.grad != 0);
     size_t smem = sizeof(float) * (size_t)per_warp * warps_per_block;
     int64_t warps = (int64_t)sms * 16;
     if (warps > p.nb_max) warps = p.nb_max > 0 ? p.nb_max : 1;

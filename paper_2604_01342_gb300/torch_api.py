@@ -8,6 +8,7 @@ of the computation runs in the CUDA kernels of ``libhawkes_gb300.so``.
     ll.backward()                                    # fills mu.grad, alpha.grad, beta.grad
     ll, dmu, dalpha, dbeta = loglik_grad(t, c, T, mu, alpha, beta)
     ll_b = loglik_varlen(t, c, offsets, T, mu, alpha, beta)   # [B], differentiable
+    ll = loglik_multi(t, c, T, mu, alphas, betas)     # K decay kernels: alphas [K,M,M], betas [K]
 
 Conventions follow ``include/hawkes_gb300.h``: marks 0-based, alpha[target,
 source], beta of shape [] or [1] (shared decay) or [M] (per source), gradients
@@ -126,6 +127,63 @@ def loglik_grad_varlen(t, c, offsets, T, mu, alpha, beta, beta_shared=None, chun
     if grad:
         return out_ll, dmu, dal, dbe
     return out_ll
+
+
+def loglik_grad_multi(t, c, T, mu, alphas, betas, chunk: int = 0, validate: bool = True,
+                      check: bool = True, grad: bool = True):
+    """K decay kernels (kernel q: matrix alphas[q] with row = target, one decay betas[q]):
+    L (float64 0-d) and, if ``grad``, (dmu [M], dalpha [K,M,M], dbeta [K]) as float32."""
+    t, c, mu, alphas, betas = _prep(t, c, mu, alphas, betas)
+    dev = t.device
+    N, M = t.shape[0], mu.shape[0]
+    K = alphas.numel() // (M * M)
+    if alphas.numel() != K * M * M or betas.numel() != K:
+        raise ValueError("alphas must be [K, M, M] and betas [K]")
+    opts = _b.make_opts(True, chunk, validate, 2, K)
+    nbytes = _b.hawkes_workspace_size(N, M, 1, grad, opts)
+    ws = _workspace(nbytes, dev)
+    out_ll = torch.empty((), dtype=torch.float64, device=dev)
+    s = _stream(dev)
+    if grad:
+        dmu = torch.empty(M, dtype=torch.float32, device=dev)
+        dal = torch.empty(K, M, M, dtype=torch.float32, device=dev)
+        dbe = torch.empty(K, dtype=torch.float32, device=dev)
+        _b.hawkes_loglik_grad(t.data_ptr(), c.data_ptr(), N, float(T), M, mu.data_ptr(),
+                              alphas.data_ptr(), betas.data_ptr(), opts, ws.data_ptr(),
+                              ws.numel(), out_ll.data_ptr(), dmu.data_ptr(), dal.data_ptr(),
+                              dbe.data_ptr(), s)
+    else:
+        _b.hawkes_loglik(t.data_ptr(), c.data_ptr(), N, float(T), M, mu.data_ptr(),
+                         alphas.data_ptr(), betas.data_ptr(), opts, ws.data_ptr(), ws.numel(),
+                         out_ll.data_ptr(), s)
+    if check:
+        rc = _b.hawkes_last_device_status(ws.data_ptr(), s)
+        if rc:
+            raise _b.HawkesError(rc, "device check")
+    if grad:
+        return out_ll, dmu, dal, dbe
+    return out_ll
+
+
+class HawkesLogLikMulti(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, t, c, T, mu, alphas, betas, chunk):
+        ll, dmu, dal, dbe = loglik_grad_multi(t, c, T, mu, alphas, betas, chunk)
+        ctx.save_for_backward(dmu, dal, dbe)
+        ctx.shapes = (alphas.shape, betas.shape)
+        return ll
+
+    @staticmethod
+    def backward(ctx, g):
+        dmu, dal, dbe = ctx.saved_tensors
+        g32 = g.to(torch.float32)
+        return (None, None, None, g32 * dmu, (g32 * dal).reshape(ctx.shapes[0]),
+                (g32 * dbe).reshape(ctx.shapes[1]), None)
+
+
+def loglik_multi(t, c, T, mu, alphas, betas, chunk: int = 0):
+    """Differentiable exact log-likelihood with K decay kernels (0-d float64)."""
+    return HawkesLogLikMulti.apply(t, c, T, mu, alphas, betas, chunk)
 
 
 class HawkesLogLik(torch.autograd.Function):

@@ -86,6 +86,22 @@ def test_long_gaps():
     assert_close(gpu_run(p, path=1, chunk=512), oracle_ref(p))
 
 
+@pytest.mark.parametrize("m,shared,mu_range", [(3, False, (0.1, 1.0)), (3, True, (0.1, 1.0)),
+                                               (40, False, (0.01, 0.1)),
+                                               (40, True, (0.006, 0.06))])
+def test_walk_batches_past_the_factorised_limit(m, shared, mu_range):
+    """Fast decays and sparse events: beta times the span of 32 events is above the limit
+    of the factorised batch walk (64) for part of the batches, which are then walked event
+    by event, mixed with factorised batches inside clusters."""
+    p = synth.random_problem(m, 3000, 400 + m, shared, beta_range=(4.0, 12.0), mu_range=mu_range)
+    beta = np.full(m, p.beta[0]) if shared else p.beta
+    t = p.t
+    span = np.array([t[min(i + 31, len(t) - 1)] - t[i] for i in range(0, len(t), 32)])
+    wide = np.mean(float(beta.max()) * span > 64.0)
+    assert 0.2 < wide < 0.9, wide                     # both forms occur
+    assert_close(gpu_run(p, path=1, chunk=96), oracle_ref(p), what=f"walk past limit m={m}")
+
+
 def test_chunk_invariance_gemm():
     p = synth.random_problem(64, 6000, 6, True)
     res = [gpu_run(p, path=2, chunk=C) for C in (8, 64, 256, 1024)]

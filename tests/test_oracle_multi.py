@@ -2,7 +2,8 @@
 checks it against something other than itself (the single-kernel oracle at K = 1, a
 brute-force double sum over kernels and event pairs, the identity that kernels sharing
 one decay act as one kernel with the summed matrix, adaptive quadrature of the
-compensator, central finite differences)."""
+compensator, central finite differences), and the conditioning sums of several kernels
+against the single-kernel ones and a brute-force double sum."""
 import math
 
 import numpy as np
@@ -102,3 +103,45 @@ def test_gradient_matches_finite_differences():
     for got, ref in ((out["dmu"], g_mu), (out["dalpha"], g_al), (out["dbeta"].sum(axis=1), g_be)):
         scale = max(1.0, float(np.max(np.abs(ref))))
         assert float(np.max(np.abs(got - ref))) / scale < 2e-7
+
+
+def brute_condition_multi(t, c, T, mu, alphas, betas):
+    """The conditioning sums written as double sums over kernels and event pairs."""
+    K, M = alphas.shape[0], mu.shape[0]
+    lam = brute_intensity_multi(t, c, mu, alphas, betas)
+    sb = np.zeros((K, M))
+    for k in range(len(t)):
+        for q in range(K):
+            for j in range(M):
+                d = sum(math.exp(-betas[q] * (t[k] - t[l])) * (1.0 - betas[q] * (t[k] - t[l]))
+                        for l in range(k) if c[l] == j)
+                sb[q, j] += abs(alphas[q, c[k], j] * d / lam[k])
+    for q in range(K):
+        cs = alphas[q].sum(axis=0)
+        for l in range(len(t)):
+            x = T - t[l]
+            sb[q, c[l]] += cs[c[l]] * x * math.exp(-betas[q] * x)
+    sl = float(np.sum(np.abs(np.log(lam)))) + T * float(mu.sum())
+    for q in range(K):
+        cs = alphas[q].sum(axis=0)
+        sl += sum(cs[c[l]] * (1.0 - math.exp(-betas[q] * (T - t[l]))) for l in range(len(t)))
+    return sl, sb
+
+
+def test_condition_multi_one_kernel_equals_condition():
+    p = synth.random_problem(6, 500, seed=47, shared_beta=True)
+    a = oracle.condition(p.t, p.c, p.T, p.mu, p.alpha, p.beta)
+    b = oracle.condition_multi(p.t, p.c, p.T, p.mu, p.alpha[None], p.beta[None])
+    assert abs(a["ll"] - b["ll"]) <= 1e-13 * a["ll"]
+    np.testing.assert_allclose(b["dbeta"][0], a["dbeta"], rtol=1e-13)
+
+
+def test_condition_multi_matches_brute_force_and_bounds_the_gradient():
+    p = synth.random_problem_multi(3, 120, seed=48, kernels=3)
+    got = oracle.condition_multi(p.t, p.c, p.T, p.mu, p.alphas, p.betas)
+    sl, sb = brute_condition_multi(p.t, p.c, p.T, p.mu, p.alphas, p.betas)
+    assert abs(got["ll"] - sl) <= 1e-11 * sl
+    np.testing.assert_allclose(got["dbeta"], sb, rtol=1e-10)
+    g = oracle.loglik_grad_multi(p.t, p.c, p.T, p.mu, p.alphas, p.betas)
+    assert np.all(np.abs(g["dbeta"]) <= got["dbeta"] * (1 + 1e-12))
+    assert abs(g["ll"]) <= got["ll"]
