@@ -268,3 +268,21 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
 }
 
 }  // namespace hk
+
+namespace hk {
+__global__ void k_test_exp_unbiased(const float* __restrict__ x, float* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = exp_unbiased(x[i]);
+}
+}  // namespace hk
+
+// Test hook (declared in no public header): y[i] = exp_unbiased(x[i]) for i < n on device
+// buffers, so a GPU test can measure its rounding against FP64.  Returns 0 on success.
+extern "C" int hawkes_test_exp_unbiased(const float* x, float* y, int64_t n, void* stream) {
+    if (n <= 0) return 0;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    hk::k_test_exp_unbiased<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, y, n);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}

@@ -25,9 +25,10 @@
 //     G_e = exp(-beta_j Delta_e) (G0_j + Delta_e (S0_j + U_j) - V_j),
 // with U_j, V_j the sums of exp(beta_j Delta_l) and Delta_l exp(beta_j Delta_l) over the
 // batch's earlier events l of mark j.  Each factor exp(-beta Delta_e) is used once, so
-// the one-signed sub-ulp error of expf does not compound along the chain of events;
-// the only chained factor is the step from one batch start to the next, taken with
-// exp_unbiased.  A batch with beta * (t_last - t_0) above kWalkFactorLimit (where the
+// the one-signed sub-ulp error of expf (kept for the 32 M per-source factors of a batch,
+// the walk's most frequent operation) does not compound along the chain of events; the
+// chained step from one batch start to the next, and the per-event factors, are taken
+// with exp_unbiased.  A batch with beta * (t_last - t_0) above kWalkFactorLimit (where the
 // growing factors exp(beta Delta) would lose range or precision) is walked event by
 // event with exp_unbiased steps.
 #include "common.cuh"
@@ -173,8 +174,8 @@ __global__ void __launch_bounds__(128) k_walk(Problem p, int64_t chunks_per_warp
             const float bc = p.shared ? bj[0] : __ldg(beta_row + ck);
             const bool fact = bmax * (float)(tl - t0) <= kWalkFactorLimit;   // warp-uniform
             // factorised: exp(+beta_{c_e} Delta_e) of the own mark, and (one decay) exp(-beta Delta_e)
-            const float ep = fact ? expf(bc * De) : 0.f;
-            const float emsh = (fact && p.shared) ? expf(-bj[0] * De) : 0.f;
+            const float ep = fact ? exp_unbiased(bc * De) : 0.f;
+            const float emsh = (fact && p.shared) ? exp_unbiased(-bj[0] * De) : 0.f;
             // chained (batches spanning beta * span > kWalkFactorLimit): step from the previous event
             double tp = __shfl_up_sync(HK_FULL, tk, 1);
             const int32_t cp = __shfl_up_sync(HK_FULL, ck, 1);
