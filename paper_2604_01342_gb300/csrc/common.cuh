@@ -78,7 +78,8 @@ struct Problem {
     // chunk-GEMM path
     float* Y;                // [nb_max*M]  alpha . Shat_b
     float* Z;                // [nb_max*M]  alpha . (Shat_b - beta Ghat_b)
-    float* W;                // [nb_max*M]  per-chunk weights of the dalpha GEMM
+    float* W;                // [M][nbp]  per-chunk weights of the dalpha GEMM, transposed:
+                             // W[i * nbp + b] = sum of w_k e_k over the events k of mark i in chunk b
     float* dal_gemm;         // [M*M]
     // fp16 hi/lo operands of the tensor-core GEMMs (rows scaled by powers of two)
     __half *al_h, *al_l;     // [M][ldk]       alpha
@@ -100,6 +101,10 @@ struct Problem {
     float* Aint;             // [N]  sum_{l<k in chunk} P_kl alpha[c_k][c_l]
     float* Bint;             // [N]  same, weighted by (t_k - t_l)
     float* wbuf;             // [N]  w_k = 1 / lambda_k
+    float* delta;            // [N]  t_k - t of the first event of k's chunk (chunk-GEMM path,
+                             //      written by the scan; null on the state-walk path)
+    float* xnext;            // [N]  t of the next chunk's first event - t_k (same)
+    float* Tmt;              // [nb_max] T - t of the chunk's first event (same)
     // centering of the GEMM operands (the tensor-core accumulation error is one-signed
     // for same-signed operands; centred operands make it unbiased)
     float* cen_S;            // [M] m_j = n_j / (beta T): stationary mean of S_j
@@ -172,17 +177,34 @@ __device__ __forceinline__ int64_t num_chunks(const Problem& p) { return p.chunk
 // Sum of log lambda without per-event log rounding: each thread keeps the product of its
 // lambdas as an FP64 mantissa in [0.5, 1) and an integer binary exponent, and takes one
 // FP64 log when the product is folded into a sum.
+// Running product of positive FP32 factors as an FP32 mantissa in [1, 2) and an integer
+// binary exponent (no FP64 arithmetic per factor: this part's FP64 rate is 1/64 of its
+// FP32 rate); one FP64 log per thread at the end.  Each factor adds one FP32 rounding
+// (relative 2^-24, either sign) to the product.
 struct LogProd {
-    double m = 1.0;
+    float m = 1.f;
     int e = 0;
     __device__ __forceinline__ void mul(float x) {
-        m *= (double)x;
-        int k;
-        m = frexp(m, &k);
-        e += k;
+        uint32_t bx = __float_as_uint(x);
+        const uint32_t ex = (bx >> 23) & 0xffu;
+        if (ex - 1u < 254u) {                  // positive normal: mantissa and exponent by bits
+            e += (int)ex - 127;
+            m *= __uint_as_float((bx & 0x007fffffu) | 0x3f800000u);
+        } else {                               // zero, subnormal, inf, NaN: propagate
+            int k;
+            const float f = frexpf(x, &k);
+            e += k;
+            m *= f;
+        }
+        const uint32_t bm = __float_as_uint(m);
+        const uint32_t em = (bm >> 23) & 0xffu;
+        if (em - 1u < 254u) {
+            e += (int)em - 127;
+            m = __uint_as_float((bm & 0x807fffffu) | 0x3f800000u);
+        }
     }
     __device__ __forceinline__ double log_value() const {
-        return log(m) + (double)e * 0.69314718055994530942;
+        return log((double)m) + (double)e * 0.69314718055994530942;
     }
 };
 

@@ -31,6 +31,9 @@ cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo
                            int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
                            const int64_t* rows_valid, float* inv_scale, const float* sub,
                            const float* coef);
+cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* hi, __half* lo,
+                                int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
+                                float* inv_scale, double* row_sum);
 cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
                                 int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
                                 cudaStream_t s, const float* centre, uint32_t* amax_bits,
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             const uint32_t* mq = msk + q * W;
             int irank = __popc(mq[i >> 5] & ((1u << (i & 31)) - 1u));
             for (int w = 0; w < (i >> 5); ++w) irank += __popc(mq[w]);
-            const float d = (float)(p.t[s0 + i] - tau);
+            const float d = p.delta[s0 + i];
             const float em = exp_unbiased(-beta * d);
             const float ep = isw ? 0.f : exp_unbiased(beta * d);
             recs[s0 + base[q] + rank] = make_float4(d, em, ep, __int_as_float((i << 16) | (ck / P)));
@@ -489,74 +492,78 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
         out[e] = dtile[(e / TR) * kTileLd + (e % TR)];
 }
 
-// Per-event epilogue: lambda, log, w, the W rows of the dalpha GEMM, the dbeta sum and
-// per-mark sums (dmu, compensator E and F) in shared-memory histograms flushed once per
-// block.  Blocks take contiguous ranges of chunks.
+// Per-event epilogue: lambda, log, w, the W entries of the dalpha GEMM, the dbeta sum and
+// per-mark sums in shared-memory histograms flushed once per block.  Events are taken in a
+// grid-stride loop (one sequence: event k lies in chunk k / C, which starts at event
+// C (k / C)); W (transposed, zeroed before) is accumulated by global reductions, one per
+// event, and its row sums are taken where W is split for the GEMM.  The compensator sums
+// E_j = sum_{c_l = j} (1 - exp(-beta (T - t_l))) = n_j - sum exp(-beta (T - t_l)) and
+// F_j = sum (T - t_l) exp(-beta (T - t_l)) only need the events with beta (T - t) < 104
+// (below that exp underflows to 0 in FP32); n_j comes from the validation's mark counts
+// or, without validation, from an integer histogram here.
+constexpr float kTailLimit = 104.f;
+
+__device__ __forceinline__ int64_t chunk_of(int64_t k, int C, int64_t N) {
+    return N < (int64_t(1) << 31) ? (int64_t)((uint32_t)k / (uint32_t)C) : k / C;
+}
+
 template <bool GRAD>
-__global__ void __launch_bounds__(256) k_epilogue(Problem p, const float* Aint, const float* Bint,
-                                                  float* wbuf, int64_t chunks_per_cta) {
+__global__ void __launch_bounds__(512) k_epilogue(Problem p, const float* Aint, const float* Bint,
+                                                  float* wbuf) {
     extern __shared__ float sh[];
-    const int M = p.M;
-    float* Wrow = sh;            // [M]
-    float* hE = Wrow + M;        // [M]
-    float* hF = hE + M;          // [M]
-    float* hmu = hF + M;         // [M]
-    float* hws = hmu + M;        // [M] sum over this block's chunks of W[b][:]
-    __shared__ double red_ll[8];
-    __shared__ double red_db[8];
+    const int M = p.M, C = p.C;
+    float* hEt = sh;                          // [M] sum of exp(-beta (T - t)) (tail events)
+    float* hF = hEt + M;                      // [M]
+    float* hmu = hF + M;                      // [M]
+    uint32_t* hcnt = (uint32_t*)(hmu + M);    // [M] events per mark (without validation)
+    __shared__ double red_ll[16];
+    __shared__ double red_db[16];
     if (failed(p.hdr)) return;
-    const int64_t nb = num_chunks(p);
-    const int64_t b0 = (int64_t)blockIdx.x * chunks_per_cta;
-    const int64_t b1 = b0 + chunks_per_cta < nb ? b0 + chunks_per_cta : nb;
-    if (b0 >= b1) return;
+    const int64_t N = p.N, ldw = p.nbp;
     const float beta = p.beta[0];
     const double T = p.Tarr[0];
-    for (int j = threadIdx.x; j < 5 * M; j += blockDim.x) sh[j] = 0.f;
+    const bool counted = p.validated != 0;
+    for (int j = threadIdx.x; j < 4 * M; j += blockDim.x) sh[j] = 0.f;
     __syncthreads();
     LogProd lp;
-    double db = 0.0;
-    for (int64_t b = b0; b < b1; ++b) {
-        int64_t s0, s1;
-        chunk_range(p, b, 0, s0, s1);
-        const double tau = p.t[s0];
-        for (int64_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-            const double tk = p.t[k];
-            const int ck = p.c[k];
-            const float delta = (float)(tk - tau);
-            const float ek = exp_unbiased(-beta * delta);
-            const float y = p.Y[b * M + ck];
-            const float aS = ek * y + Aint[k];
-            const float lam = p.mu[ck] + beta * aS;
-            if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
-            lp.mul(lam);
-            const float xT = (float)(T - tk);
-            atomicAdd(&hE[ck], -expm1f(-beta * xT));
-            if (GRAD) {
-                const float w = 1.f / lam;
-                const float x = p.Z[b * M + ck];
-                db += (double)(w * (ek * (x - beta * delta * y) + (Aint[k] - beta * Bint[k])));
-                wbuf[k] = w;
-                atomicAdd(&Wrow[ck], w * ek);
-                atomicAdd(&hmu[ck], w);
-                atomicAdd(&hF[ck], xT * exp_unbiased(-beta * xT));
+    float db = 0.f;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = chunk_of(k, C, N);
+        const int ck = p.c[k];
+        const float delta = p.delta[k];
+        const float ek = exp_unbiased(-beta * delta);
+        const float y = p.Y[b * M + ck];
+        const float ak = Aint[k];
+        const float aS = ek * y + ak;
+        const float lam = p.mu[ck] + beta * aS;
+        if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
+        lp.mul(lam);
+        if (!counted) atomicAdd(&hcnt[ck], 1u);
+        if (beta * (p.Tmt[b] - delta) < kTailLimit + 1.f) {     // T - t_k, to within rounding
+            const float xT = (float)(T - p.t[k]);
+            if (beta * xT < kTailLimit) {
+                const float eT = exp_unbiased(-beta * xT);
+                atomicAdd(&hEt[ck], eT);
+                if (GRAD) atomicAdd(&hF[ck], xT * eT);
             }
         }
         if (GRAD) {
-            __syncthreads();
-            for (int j = threadIdx.x; j < M; j += blockDim.x) {
-                p.W[b * M + j] = Wrow[j];
-                hws[j] += Wrow[j];
-                Wrow[j] = 0.f;
-            }
-            __syncthreads();
+            const float w = 1.f / lam;
+            const float x = p.Z[b * M + ck];
+            db += w * (ek * (x - beta * delta * y) + (ak - beta * Bint[k]));
+            wbuf[k] = w;
+            atomicAdd(&p.W[(int64_t)ck * ldw + b], w * ek);
+            atomicAdd(&hmu[ck], w);
         }
     }
     double ll = lp.log_value();
+    double dbd = (double)db;
     for (int o = 16; o >= 1; o >>= 1) {
         ll += __shfl_xor_sync(HK_FULL, ll, o);
-        db += __shfl_xor_sync(HK_FULL, db, o);
+        dbd += __shfl_xor_sync(HK_FULL, dbd, o);
     }
-    if ((threadIdx.x & 31) == 0) { red_ll[threadIdx.x >> 5] = ll; red_db[threadIdx.x >> 5] = db; }
+    if ((threadIdx.x & 31) == 0) { red_ll[threadIdx.x >> 5] = ll; red_db[threadIdx.x >> 5] = dbd; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, d = 0.0;
@@ -565,13 +572,25 @@ __global__ void __launch_bounds__(256) k_epilogue(Problem p, const float* Aint, 
         if (GRAD) atomicAdd(&p.dbe_acc[0], d);
     }
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        if (hE[j] != 0.f) atomicAdd(&p.E_acc[j], (double)hE[j]);
+        const double n = counted ? (blockIdx.x == 0 ? (double)p.counts[j] : 0.0) : (double)hcnt[j];
+        const double e = n - (double)hEt[j];
+        if (e != 0.0) atomicAdd(&p.E_acc[j], e);
         if (GRAD) {
             if (hF[j] != 0.f) atomicAdd(&p.F_acc[j], (double)hF[j]);
             if (hmu[j] != 0.f) atomicAdd(&p.dmu_acc[j], (double)hmu[j]);
-            if (hws[j] != 0.f) atomicAdd(&p.wsum_acc[j], (double)hws[j]);
         }
     }
+}
+
+// Blocks of the epilogue kernels: two per SM (512 threads, each ~32 events at N = 1e7).
+int epilogue_blocks(int64_t N) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (int64_t)sms * 2;
+    const int64_t need = (N + 511) / 512;
+    if (need < blocks) blocks = need;
+    return (int)(blocks > 0 ? blocks : 1);
 }
 
 // Everything of the chunk-GEMM path before the per-event epilogue: operand centres and
@@ -658,27 +677,18 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
 // The per-event epilogue of one kernel.
 cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nl) {
     cudaError_t err;
-    const int64_t M = p.M, nb = p.nb_max;
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    {
-        const size_t smem = sizeof(float) * 5 * (size_t)M;
-        auto kern = p.grad ? k_epilogue<true> : k_epilogue<false>;
-        if (smem > 48 * 1024) {
-            err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (err != cudaSuccess) return err;
-        }
-        int64_t blocks = (int64_t)sms * 4;
-        int64_t per = (nb + blocks - 1) / blocks;
-        if (per < 1) per = 1;
-        blocks = (nb + per - 1) / per;
-        kern<<<(unsigned)(blocks > 0 ? blocks : 1), 256, smem, s>>>(p, p.Aint, p.Bint, p.wbuf, per);
-        ++*nl;
-        prof_mark(s, "epilogue");
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int64_t M = p.M;
+    if (p.grad) cudaMemsetAsync(p.W, 0, sizeof(float) * (size_t)M * (size_t)p.nbp, s);
+    const size_t smem = sizeof(float) * 4 * (size_t)M;
+    auto kern = p.grad ? k_epilogue<true> : k_epilogue<false>;
+    if (smem > 48 * 1024) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
     }
-    return cudaSuccess;
+    kern<<<(unsigned)epilogue_blocks(p.N), 512, smem, s>>>(p, p.Aint, p.Bint, p.wbuf);
+    ++*nl;
+    prof_mark(s, "epilogue");
+    return cudaGetLastError();
 }
 
 // Everything after the epilogue: row groups and backward pairs, the dalpha GEMM and the
@@ -733,13 +743,14 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (p.grad) {
-        // dalpha_gemm[i][j] = sum_b W[b][i] S^[b][j]: both operands transposed so that
-        // the chunk index is the contiguous K dimension; rows past the chunk count are 0
-        if ((err = transpose_split_f16(p.W, M, nb_dev, p.nbp, p.Wt_h, p.Wt_l, p.nbp, s, nullptr,
-                                       p.colmax, p.isc_Wt)) != cudaSuccess)
+        // dalpha_gemm[i][j] = sum_b W[b][i] S^[b][j] with the chunk index as the contiguous
+        // K dimension: W is already transposed (columns past the chunk count are 0), S^ is
+        // transposed here
+        if ((err = split_f16_long_rows(p.W, p.nbp, p.Wt_h, p.Wt_l, p.nbp, M, p.nbp, s, p.isc_Wt,
+                                       p.wsum_acc)) != cudaSuccess)
             return err;
-        *nl += 2;
-        prof_mark(s, "transpose_W");
+        ++*nl;
+        prof_mark(s, "split_W");
         if ((err = transpose_split_f16(p.Shat, M, nb_dev, p.nbp, p.St_h, p.St_l, p.nbp, s,
                                        p.cen_S, p.colmax, p.isc_St)) != cudaSuccess)
             return err;
@@ -780,94 +791,88 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
 // log-sum and dmu go to slice 0.
 // ---------------------------------------------------------------------------
 template <bool GRAD>
-__global__ void __launch_bounds__(256) k_epilogue_multi(Problem p, MultiSlices ms, float* wbuf,
-                                                        int64_t chunks_per_cta) {
+__global__ void __launch_bounds__(512) k_epilogue_multi(Problem p, MultiSlices ms, float* wbuf) {
     extern __shared__ float sh[];
-    const int M = p.M, K = ms.K;
-    float* Wrow = sh;                  // [K][M]
-    float* hE = Wrow + K * M;          // [K][M]
-    float* hF = hE + K * M;            // [K][M]
-    float* hws = hF + K * M;           // [K][M]
-    float* hmu = hws + K * M;          // [M]
-    __shared__ double red_ll[8];
-    __shared__ double red_db[kMaxKernels][8];
+    const int M = p.M, K = ms.K, C = p.C;
+    float* hEt = sh;                           // [K][M]
+    float* hF = hEt + K * M;                   // [K][M]
+    float* hmu = hF + K * M;                   // [M]
+    uint32_t* hcnt = (uint32_t*)(hmu + M);     // [M]
+    __shared__ double red_ll[16];
+    __shared__ double red_db[kMaxKernels][16];
     for (int q = 0; q < K; ++q)
         if (failed(ms.k[q].hdr)) return;
-    const int64_t nb = num_chunks(p);
-    const int64_t b0 = (int64_t)blockIdx.x * chunks_per_cta;
-    const int64_t b1 = b0 + chunks_per_cta < nb ? b0 + chunks_per_cta : nb;
-    if (b0 >= b1) return;
-    float beta[kMaxKernels];
+    const int64_t N = p.N, ldw = p.nbp;
+    const bool counted = p.validated != 0;
+    float beta[kMaxKernels], bmin = 0.f;      // the smallest decay has the longest tail
 #pragma unroll
-    for (int q = 0; q < kMaxKernels; ++q) beta[q] = q < K ? ms.k[q].beta[0] : 0.f;
+    for (int q = 0; q < kMaxKernels; ++q) {
+        beta[q] = q < K ? ms.k[q].beta[0] : 0.f;
+        if (q < K) bmin = q == 0 ? beta[q] : fminf(bmin, beta[q]);
+    }
     const double T = p.Tarr[0];
-    for (int j = threadIdx.x; j < (4 * K + 1) * M; j += blockDim.x) sh[j] = 0.f;
+    for (int j = threadIdx.x; j < (2 * K + 2) * M; j += blockDim.x) sh[j] = 0.f;
     __syncthreads();
     LogProd lp;
-    double db[kMaxKernels] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t b = b0; b < b1; ++b) {
-        int64_t s0, s1;
-        chunk_range(p, b, 0, s0, s1);
-        const double tau = p.t[s0];
-        for (int64_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-            const double tk = p.t[k];
-            const int ck = p.c[k];
-            const float delta = (float)(tk - tau);
-            float e[kMaxKernels], y[kMaxKernels], aS[kMaxKernels];
-            float exc = 0.f;
+    float db[kMaxKernels] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = chunk_of(k, C, N);
+        const int ck = p.c[k];
+        const float delta = p.delta[k];
+        float e[kMaxKernels], y[kMaxKernels];
+        float exc = 0.f;
+#pragma unroll
+        for (int q = 0; q < kMaxKernels; ++q) {
+            if (q < K) {
+                e[q] = exp_unbiased(-beta[q] * delta);
+                y[q] = ms.k[q].Y[b * M + ck];
+                exc += beta[q] * (e[q] * y[q] + ms.k[q].A[k]);
+            }
+        }
+        const float lam = p.mu[ck] + exc;
+        if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
+        lp.mul(lam);
+        if (!counted) atomicAdd(&hcnt[ck], 1u);
+        if (bmin * (p.Tmt[b] - delta) < kTailLimit + 1.f) {       // T - t_k, to within rounding
+            const float xT = (float)(T - p.t[k]);
 #pragma unroll
             for (int q = 0; q < kMaxKernels; ++q) {
-                if (q < K) {
-                    e[q] = exp_unbiased(-beta[q] * delta);
-                    y[q] = ms.k[q].Y[b * M + ck];
-                    aS[q] = e[q] * y[q] + ms.k[q].A[k];
-                    exc += beta[q] * aS[q];
-                }
-            }
-            const float lam = p.mu[ck] + exc;
-            if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
-            lp.mul(lam);
-            const float xT = (float)(T - tk);
-#pragma unroll
-            for (int q = 0; q < kMaxKernels; ++q)
-                if (q < K) atomicAdd(&hE[q * M + ck], -expm1f(-beta[q] * xT));
-            if (GRAD) {
-                const float w = 1.f / lam;
-                wbuf[k] = w;
-                atomicAdd(&hmu[ck], w);
-#pragma unroll
-                for (int q = 0; q < kMaxKernels; ++q) {
-                    if (q < K) {
-                        const float x = ms.k[q].Z[b * M + ck];
-                        db[q] += (double)(w * (e[q] * (x - beta[q] * delta * y[q]) +
-                                               (ms.k[q].A[k] - beta[q] * ms.k[q].B[k])));
-                        atomicAdd(&Wrow[q * M + ck], w * e[q]);
-                        atomicAdd(&hF[q * M + ck], xT * exp_unbiased(-beta[q] * xT));
-                    }
+                if (q < K && beta[q] * xT < kTailLimit) {
+                    const float eT = exp_unbiased(-beta[q] * xT);
+                    atomicAdd(&hEt[q * M + ck], eT);
+                    if (GRAD) atomicAdd(&hF[q * M + ck], xT * eT);
                 }
             }
         }
         if (GRAD) {
-            __syncthreads();
-            for (int e = threadIdx.x; e < K * M; e += blockDim.x) {
-                const int q = e / M, j = e % M;
-                ms.k[q].W[b * M + j] = Wrow[e];
-                hws[e] += Wrow[e];
-                Wrow[e] = 0.f;
+            const float w = 1.f / lam;
+            wbuf[k] = w;
+            atomicAdd(&hmu[ck], w);
+#pragma unroll
+            for (int q = 0; q < kMaxKernels; ++q) {
+                if (q < K) {
+                    const float x = ms.k[q].Z[b * M + ck];
+                    db[q] += w * (e[q] * (x - beta[q] * delta * y[q]) +
+                                  (ms.k[q].A[k] - beta[q] * ms.k[q].B[k]));
+                    atomicAdd(&ms.k[q].W[(int64_t)ck * ldw + b], w * e[q]);
+                }
             }
-            __syncthreads();
         }
     }
     double ll = lp.log_value();
+    double dbd[kMaxKernels];
+#pragma unroll
+    for (int q = 0; q < kMaxKernels; ++q) dbd[q] = (double)db[q];
     for (int o = 16; o >= 1; o >>= 1) {
         ll += __shfl_xor_sync(HK_FULL, ll, o);
 #pragma unroll
-        for (int q = 0; q < kMaxKernels; ++q) db[q] += __shfl_xor_sync(HK_FULL, db[q], o);
+        for (int q = 0; q < kMaxKernels; ++q) dbd[q] += __shfl_xor_sync(HK_FULL, dbd[q], o);
     }
     if ((threadIdx.x & 31) == 0) {
         red_ll[threadIdx.x >> 5] = ll;
 #pragma unroll
-        for (int q = 0; q < kMaxKernels; ++q) red_db[q][threadIdx.x >> 5] = db[q];
+        for (int q = 0; q < kMaxKernels; ++q) red_db[q][threadIdx.x >> 5] = dbd[q];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -883,11 +888,10 @@ __global__ void __launch_bounds__(256) k_epilogue_multi(Problem p, MultiSlices m
     }
     for (int e = threadIdx.x; e < K * M; e += blockDim.x) {
         const int q = e / M, j = e % M;
-        if (hE[e] != 0.f) atomicAdd(&ms.k[q].E_acc[j], (double)hE[e]);
-        if (GRAD) {
-            if (hF[e] != 0.f) atomicAdd(&ms.k[q].F_acc[j], (double)hF[e]);
-            if (hws[e] != 0.f) atomicAdd(&ms.k[q].wsum_acc[j], (double)hws[e]);
-        }
+        const double n = counted ? (blockIdx.x == 0 ? (double)p.counts[j] : 0.0) : (double)hcnt[j];
+        const double ev = n - (double)hEt[e];
+        if (ev != 0.0) atomicAdd(&ms.k[q].E_acc[j], ev);
+        if (GRAD && hF[e] != 0.f) atomicAdd(&ms.k[q].F_acc[j], (double)hF[e]);
     }
     if (GRAD)
         for (int j = threadIdx.x; j < M; j += blockDim.x)
@@ -895,19 +899,15 @@ __global__ void __launch_bounds__(256) k_epilogue_multi(Problem p, MultiSlices m
 }
 
 cudaError_t launch_epilogue_multi(const Problem& p, const MultiSlices& ms, cudaStream_t s, int* nl) {
-    const int64_t M = p.M, nb = p.nb_max;
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = sizeof(float) * (4 * (size_t)ms.K + 1) * (size_t)M;
+    const int64_t M = p.M;
+    if (p.grad)
+        for (int q = 0; q < ms.K; ++q)
+            cudaMemsetAsync(ms.k[q].W, 0, sizeof(float) * (size_t)M * (size_t)p.nbp, s);
+    const size_t smem = sizeof(float) * (2 * (size_t)ms.K + 2) * (size_t)M;
     auto kern = p.grad ? k_epilogue_multi<true> : k_epilogue_multi<false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    int64_t blocks = (int64_t)sms * 4;
-    int64_t per = (nb + blocks - 1) / blocks;
-    if (per < 1) per = 1;
-    blocks = (nb + per - 1) / per;
-    kern<<<(unsigned)(blocks > 0 ? blocks : 1), 256, smem, s>>>(p, ms, p.wbuf, per);
+    kern<<<(unsigned)epilogue_blocks(p.N), 512, smem, s>>>(p, ms, p.wbuf);
     ++*nl;
     prof_mark(s, "epilogue");
     return cudaGetLastError();

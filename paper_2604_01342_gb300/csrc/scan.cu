@@ -61,7 +61,15 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
                 if (GRAD) p.Ghat[b * M + j] = G[j];
             }
         }
+        // chunk-GEMM path: the per-event offsets from the chunk start (and to the next
+        // chunk start) are taken here once in FP64, for the later kernels
+        const bool offsets = PHASE == 0 && p.delta != nullptr && s0 < s1;
+        const double t0 = s0 < s1 ? p.t[s0] : 0.0;
+        if (offsets && threadIdx.x == 0) p.Tmt[b] = (float)(p.Tarr[seq] - t0);
         if (last) {
+            if (offsets)
+                for (int64_t l = s0 + threadIdx.x; l < s1; l += blockDim.x)
+                    p.delta[l] = (float)(p.t[l] - t0);
             for (int j = threadIdx.x; j < M; j += blockDim.x) {
                 S[j] = 0.f;
                 if (GRAD) G[j] = 0.f;
@@ -71,7 +79,7 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
             continue;
         }
         const double tn = p.t[s1];            // start of the next chunk
-        const float D = (float)(tn - p.t[s0]);
+        const float D = (float)(tn - t0);
         const float dsh = p.shared ? exp_unbiased(-beta_of(p, seq, 0) * D) : 0.f;
         for (int j = threadIdx.x; j < M; j += blockDim.x) {
             float d = p.shared ? dsh : exp_unbiased(-beta_of(p, seq, j) * D);
@@ -79,11 +87,21 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
             if (GRAD) G[j] = d * (G[j] + D * s);
             S[j] = d * s;
         }
-        if (threadIdx.x == 0) span_sh += (tn - p.t[s0]);
+        if (threadIdx.x == 0) span_sh += (tn - t0);
         __syncthreads();
         for (int64_t l = s0 + threadIdx.x; l < s1; l += blockDim.x) {
             int32_t cl = p.c[l];
-            float x = (float)(tn - p.t[l]);
+            float x;
+            if (PHASE == 1 && p.xnext) {
+                x = p.xnext[l];
+            } else {
+                const double tl = p.t[l];
+                x = (float)(tn - tl);
+                if (offsets) {
+                    p.delta[l] = (float)(tl - t0);
+                    p.xnext[l] = x;
+                }
+            }
             float e = exp_unbiased(-beta_of(p, seq, cl) * x);
             atomicAdd(&S[cl], e);
             if (GRAD) atomicAdd(&G[cl], x * e);

@@ -459,12 +459,68 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
     }
 }
 
+// Long rows (cols >> 32): one block per row, two passes over it (the row maximum and, if
+// asked, the FP64 row sum; then the split, mostly from L2), no centre or subtrahend.
+__global__ void __launch_bounds__(256) k_split_f16_long_rows(const float* __restrict__ src,
+                                                             int64_t lds, __half* hi, __half* lo,
+                                                             int64_t ldd, int64_t rows,
+                                                             int64_t cols, float* inv_scale,
+                                                             double* row_sum) {
+    __shared__ float red[8];
+    __shared__ double reds[8];
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float* sr = src + r * lds;
+        float amax = 0.f, part = 0.f;         // FP32 partial sums per thread, FP64 across
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+            const float v = sr[c];
+            amax = fmaxf(amax, fabsf(v));
+            part += v;
+        }
+        double sum = (double)part;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        }
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = amax; reds[threadIdx.x >> 5] = sum; }
+        __syncthreads();
+        amax = 0.f;
+        sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { amax = fmaxf(amax, red[w]); sum += reds[w]; }
+        __syncthreads();                                  // red is reused by the next row
+        if (row_sum && threadIdx.x == 0) row_sum[r] = sum;
+        const int a = tc::row_exponent(amax);
+        const float sc = ldexpf(1.f, a);
+        __half* hr = hi + r * ldd;
+        __half* lr = lo + r * ldd;
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+            __half h, l;
+            tc::split_f16(sr[c] * sc, h, l);
+            hr[c] = h;
+            lr[c] = l;
+        }
+        if (threadIdx.x == 0) inv_scale[r] = ldexpf(1.f, -a);
+    }
+}
+
+cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* hi, __half* lo,
+                                int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
+                                float* inv_scale, double* row_sum) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int64_t blocks = rows < 152 * 8 ? rows : 152 * 8;
+    k_split_f16_long_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols,
+                                                           inv_scale, row_sum);
+    return cudaGetLastError();
+}
+
 cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo, int64_t ldd,
                            int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
                            const int64_t* rows_valid, float* inv_scale, const float* sub,
                            const float* coef) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if ((sub == nullptr) != (coef == nullptr)) return cudaErrorInvalidValue;
+    if (cols >= 4096 && !centre && !rows_valid && !sub)
+        return split_f16_long_rows(src, lds, hi, lo, ldd, rows, cols, s, inv_scale, nullptr);
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_split_f16_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, centre,
