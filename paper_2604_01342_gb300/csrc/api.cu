@@ -38,7 +38,7 @@ struct Plan {
     size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
         off_grp_dt, off_grp_reset, off_seg_comp, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
         off_dal_gemm, off_al_h, off_al_l, off_S_h, off_S_l, off_G_h, off_G_l, off_Wt_h, off_Wt_l,
-        off_St_h, off_St_l, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf, off_delta, off_xnext, off_Tmt,
+        off_St_h, off_St_l, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf, off_delta, off_Dspan, off_Tmt,
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
     int64_t ldk, nbp;
     int dal_parts_max;
@@ -112,7 +112,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->off_al_h = pl->off_al_l = pl->off_S_h = pl->off_S_l = pl->off_G_h = pl->off_G_l = 0;
     pl->off_Wt_h = pl->off_Wt_l = pl->off_St_h = pl->off_St_l = 0;
     pl->off_recs = pl->off_lrec = pl->off_bmask = pl->off_kprep = pl->off_dal_part = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
-    pl->off_delta = pl->off_xnext = pl->off_Tmt = 0;
+    pl->off_delta = pl->off_Dspan = pl->off_Tmt = 0;
     pl->off_cen = pl->off_wsum = pl->off_at = pl->off_isc = pl->off_colmax = 0;
     pl->dal_parts_max = 0;
     if (path == PATH_GEMM) {
@@ -138,7 +138,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_Bint = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
         if (grad) pl->off_wbuf = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
         pl->off_delta = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
-        pl->off_xnext = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
+        pl->off_Dspan = take(sizeof(float) * (size_t)pl->nb_max);
         pl->off_Tmt = take(sizeof(float) * (size_t)pl->nb_max);
         pl->off_cen = take(sizeof(float) * 2 * (size_t)M);
         pl->off_wsum = take(sizeof(double) * (size_t)M);
@@ -223,7 +223,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.Bint = at<float>(ws, pl.off_Bint);
     p.wbuf = at<float>(ws, pl.off_wbuf);
     p.delta = at<float>(ws, pl.off_delta);
-    p.xnext = at<float>(ws, pl.off_xnext);
+    p.Dspan = at<float>(ws, pl.off_Dspan);
     p.Tmt = at<float>(ws, pl.off_Tmt);
     p.cen_S = at<float>(ws, pl.off_cen);
     p.bias_Y = p.cen_S ? p.cen_S + M : nullptr;

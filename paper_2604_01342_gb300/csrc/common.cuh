@@ -103,7 +103,7 @@ struct Problem {
     float* wbuf;             // [N]  w_k = 1 / lambda_k
     float* delta;            // [N]  t_k - t of the first event of k's chunk (chunk-GEMM path,
                              //      written by the scan; null on the state-walk path)
-    float* xnext;            // [N]  t of the next chunk's first event - t_k (same)
+    float* Dspan;            // [nb_max] t of the next chunk's first event - t of its first (same)
     float* Tmt;              // [nb_max] T - t of the chunk's first event (same)
     // centering of the GEMM operands (the tensor-core accumulation error is one-signed
     // for same-signed operands; centred operands make it unbiased)

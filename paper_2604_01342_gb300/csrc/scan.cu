@@ -50,6 +50,15 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
     }
     if (threadIdx.x == 0) { span_sh = 0.0; reset_sh = 0; }
     __syncthreads();
+    // Chunk-GEMM path (p.delta set): the per-event offsets delta_l = t_l - t_0 from the chunk
+    // start are taken here once in FP64 (this part's FP64 rate is 1/64 of its FP32 rate) and
+    // stored for the later kernels, with the chunk span D = t_n - t_0 and T - t_0; the offset
+    // to the next chunk start is then D - delta_l in FP32 (an absolute error of about one ulp
+    // of D, i.e. a relative error below 1e-6 of exp(-beta x) while beta D <= 16; wider chunks
+    // take it in FP64).  The state walk's scan keeps one FP64 difference per event.
+    __shared__ float D_sh;
+    __shared__ int narrow_sh;
+    const bool fast = p.delta != nullptr;
     for (int64_t b = b0; b < b1; ++b) {
         const int32_t seq = p.chunk_seq[b];
         int64_t s0, s1;
@@ -61,15 +70,13 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
                 if (GRAD) p.Ghat[b * M + j] = G[j];
             }
         }
-        // chunk-GEMM path: the per-event offsets from the chunk start (and to the next
-        // chunk start) are taken here once in FP64, for the later kernels
-        const bool offsets = PHASE == 0 && p.delta != nullptr && s0 < s1;
         const double t0 = s0 < s1 ? p.t[s0] : 0.0;
-        if (offsets && threadIdx.x == 0) p.Tmt[b] = (float)(p.Tarr[seq] - t0);
         if (last) {
-            if (offsets)
+            if (PHASE == 0 && fast) {
+                if (threadIdx.x == 0 && s0 < s1) p.Tmt[b] = (float)(p.Tarr[seq] - t0);
                 for (int64_t l = s0 + threadIdx.x; l < s1; l += blockDim.x)
                     p.delta[l] = (float)(p.t[l] - t0);
+            }
             for (int j = threadIdx.x; j < M; j += blockDim.x) {
                 S[j] = 0.f;
                 if (GRAD) G[j] = 0.f;
@@ -79,7 +86,26 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
             continue;
         }
         const double tn = p.t[s1];            // start of the next chunk
-        const float D = (float)(tn - t0);
+        float D;
+        bool narrow;
+        if (PHASE == 1 && fast) {
+            D = p.Dspan[b];
+            narrow = beta_of(p, seq, 0) * D <= 16.f;
+        } else {
+            if (threadIdx.x == 0) {
+                const double span = tn - t0;
+                D_sh = (float)span;
+                narrow_sh = fast && beta_of(p, seq, 0) * D_sh <= 16.f;
+                span_sh += span;
+                if (PHASE == 0 && fast) {
+                    p.Dspan[b] = D_sh;
+                    p.Tmt[b] = (float)(p.Tarr[seq] - t0);
+                }
+            }
+            __syncthreads();
+            D = D_sh;
+            narrow = narrow_sh != 0;
+        }
         const float dsh = p.shared ? exp_unbiased(-beta_of(p, seq, 0) * D) : 0.f;
         for (int j = threadIdx.x; j < M; j += blockDim.x) {
             float d = p.shared ? dsh : exp_unbiased(-beta_of(p, seq, j) * D);
@@ -87,20 +113,21 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
             if (GRAD) G[j] = d * (G[j] + D * s);
             S[j] = d * s;
         }
-        if (threadIdx.x == 0) span_sh += (tn - t0);
         __syncthreads();
         for (int64_t l = s0 + threadIdx.x; l < s1; l += blockDim.x) {
             int32_t cl = p.c[l];
             float x;
-            if (PHASE == 1 && p.xnext) {
-                x = p.xnext[l];
-            } else {
-                const double tl = p.t[l];
-                x = (float)(tn - tl);
-                if (offsets) {
-                    p.delta[l] = (float)(tl - t0);
-                    p.xnext[l] = x;
+            if (fast) {
+                float dl;
+                if (PHASE == 0) {
+                    dl = (float)(p.t[l] - t0);
+                    p.delta[l] = dl;
+                } else {
+                    dl = p.delta[l];
                 }
+                x = narrow ? D - dl : (float)(tn - p.t[l]);
+            } else {
+                x = (float)(tn - p.t[l]);
             }
             float e = exp_unbiased(-beta_of(p, seq, cl) * x);
             atomicAdd(&S[cl], e);
