@@ -429,13 +429,13 @@ def kernel_work(name, N, M, C):
     pairs = N * (C - 1) / 2.0                  # pairs (k, l) inside chunks, l before k
     table = {
         "validate_events": ("hbm", 12.0 * N),
-        "scan_reduce": ("hbm", 12.0 * N),
-        "scan_states": ("hbm", 12.0 * N + 8.0 * M * nb),
+        "scan_reduce": ("hbm", 12.0 * N + 4.0 * N),             # t, c in; offsets out
+        "scan_states": ("hbm", 8.0 * N + 8.0 * M * nb),         # offsets, c in; S^, G^ out
         "split_S": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
-        "split_G": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
-        "bucket": ("hbm", 12.0 * N + 16.0 * N),
+        "split_G": ("hbm", 8.0 * M * nb + 4.0 * M * nb),         # S^, G^ in; S^ - beta G^ out
+        "bucket": ("hbm", 8.0 * N + 24.0 * N),                  # offsets, c in; records out
         "epilogue": ("hbm", 12.0 * N + 8.0 * N + 12.0 * N),
-        "transpose_W": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
+        "split_W": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
         "transpose_S": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
         "gemm_Y": ("tensor", 2.0 * M * M * nb),
         "gemm_Z": ("tensor", 2.0 * M * M * nb),

@@ -17,7 +17,8 @@
 // event e.  The gradient needs w_k, so the 32 events are walked a second time
 // from the saved batch-start state (recomputing the decays is cheaper than
 // keeping 32 states per lane).  dt_k and T - t_k are FP64 differences rounded to
-// FP32; the log-sum is taken as the log of an FP64 product (LogProd).
+// FP32; the log-sum is taken as the log of a running product (LogProd: FP32 mantissa,
+// integer exponent).
 //
 // Within a batch the recurrence is taken in factorised form from the state (S0, G0)
 // seen by its first event (time t_0; Delta_e = t_e - t_0):

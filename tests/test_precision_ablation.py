@@ -83,3 +83,32 @@ def test_log_sum_accumulation():
           f"FP64 over 1e6 terms {e64:.2e}")
     assert e_kahan < 1e-7 and e64 < 1e-12
     assert e_plain > 10 * e_kahan
+
+
+def fp32_log_product(lam, per_thread=64):
+    """The kernels' log-sum: per thread, a running product of FP32 intensities kept as an
+    FP32 mantissa in [1, 2) and an integer binary exponent (one FP32 rounding per factor),
+    one FP64 log per thread, FP64 sum over threads."""
+    total = 0.0
+    for g in range(0, lam.shape[0], per_thread):
+        m, e = f32(1.0), 0
+        for x in lam[g:g + per_thread]:
+            fx, ex = np.frexp(f32(x))                 # x = fx 2^ex, fx in [0.5, 1)
+            m = f32(m * f32(2.0 * fx))
+            e += int(ex) - 1
+            fm, em = np.frexp(m)
+            m = f32(2.0 * fm)
+            e += int(em) - 1
+        total += float(np.log(np.float64(m))) + e * np.log(2.0)
+    return total
+
+
+def test_log_product_in_fp32_mantissa():
+    rng = np.random.default_rng(6)
+    lam = rng.uniform(0.01, 5.0, 200_000).astype(f32)
+    exact = float(np.sum(np.log(lam.astype(np.float64))))
+    e = abs(fp32_log_product(lam) - exact) / abs(exact)
+    e_abs = abs(fp32_log_product(lam) - exact)
+    print(f"log-sum of 2e5 FP32 intensities as FP32-mantissa products of 64: relative {e:.2e}, "
+          f"absolute {e_abs:.2e}")
+    assert e < 1e-9
