@@ -92,9 +92,17 @@ __global__ void k_finalize_alpha(Problem p, int mode) {
             const int i = (int)(ij / M), P = p.P, TR = (M + P - 1) / P;
             const int64_t at = (((int64_t)(i % P) * P + (j % P)) * TR + (i / P)) * TR + (j / P);
             const int64_t stride = (int64_t)P * P * TR * TR;
-            double pairs = 0.0;
-            for (int r = 0; r < p.dal_parts; ++r) pairs += (double)p.dal_part[r * stride + at];
-            x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] + pairs);
+            // compensated FP32 sum of the chunk ranges' tiles (FP64 arithmetic runs at 1/64
+            // of the FP32 rate here)
+            float pairs = 0.f, comp = 0.f;
+            for (int r = 0; r < p.dal_parts; ++r) {
+                const float y = p.dal_part[r * stride + at] - comp;
+                const float t = pairs + y;
+                comp = (t - pairs) - y;
+                pairs = t;
+            }
+            x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] +
+                                (double)pairs);
         }
         const double v = x - p.E_acc[s * M + j];
         p.d_alpha[e] = bad ? (float)nanv : (float)v;

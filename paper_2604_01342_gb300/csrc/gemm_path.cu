@@ -116,37 +116,51 @@ __global__ void k_alpha_tiles(Problem p, float* at) {
     }
 }
 
-// One block per chunk: bucket the chunk's events by mark block, each bucket sorted by
-// (position of the mark in its block, index in the chunk) in recs; the same buckets in
-// index order in lrec (source side of the backward pairs), and the membership bits of
-// every bucket over the chunk's event indices in bmask, each 32-bit word with the number
-// of members in the words before it.
+// One warp per chunk (up to eight chunks per block at a time, no block-wide barrier after
+// the mark table): bucket the chunk's events by mark block, each bucket sorted by (position
+// of the mark in its block, index in the chunk) in recs; the same buckets in index order in
+// lrec (source side of the backward pairs), and the membership bits of every bucket over
+// the chunk's event indices in bmask, each 32-bit word with the number of members in the
+// words before it.
+__host__ __device__ inline int bucket_ints_per_warp(int P, int C) {
+    return 2 * P + 1 + C + P * ((C + 31) >> 5);
+}
+// shared memory of k_bucket: each warp's scratch, then the mark -> (block, position) table
+__host__ __device__ inline size_t bucket_smem_bytes(int P, int C, int M, int warps) {
+    return sizeof(int32_t) * ((size_t)warps * bucket_ints_per_warp(P, C) + (size_t)M);
+}
+
 __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2* lrec,
                                                 uint2* bmask, int32_t* bstart, uint8_t* wide) {
     extern __shared__ int32_t sm_i[];
-    const int P = p.P, W = (p.C + 31) >> 5;
-    int32_t* cnt = sm_i;                  // [P]
+    const int P = p.P, C = p.C, W = (C + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    int32_t* cnt = sm_i + (threadIdx.x >> 5) * bucket_ints_per_warp(P, C);   // [P]
     int32_t* base = cnt + P;              // [P+1]
     int32_t* ukey = base + P + 1;         // [C] keys in unordered bucket slots
-    uint32_t* msk = (uint32_t*)(ukey + p.C);   // [P * W] membership bits
+    uint32_t* msk = (uint32_t*)(ukey + C);   // [P * W] membership bits
+    // mark c -> (position c / P) << 16 | (block c mod P), so that no event divides by P
+    int32_t* qtab = sm_i + (blockDim.x >> 5) * bucket_ints_per_warp(P, C);
     if (failed(p.hdr)) return;
+    for (int c = threadIdx.x; c < p.M; c += blockDim.x) qtab[c] = ((c / P) << 16) | (c % P);
+    __syncthreads();
     const float beta = p.beta[0];
     const int64_t nb = num_chunks(p);
-    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += nw) {
         int64_t s0, s1;
         chunk_range(p, b, 0, s0, s1);
         const int n = (int)(s1 - s0);
-        const double tau = p.t[s0];
-        for (int q = threadIdx.x; q < P; q += blockDim.x) cnt[q] = 0;
-        for (int q = threadIdx.x; q < P * W; q += blockDim.x) msk[q] = 0u;
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int q = p.c[s0 + i] % P;
+        for (int q = lane; q < P; q += 32) cnt[q] = 0;
+        for (int q = lane; q < P * W; q += 32) msk[q] = 0u;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int q = qtab[__ldg(p.c + s0 + i)] & 0xffff;
             atomicAdd(&cnt[q], 1);
             atomicOr(&msk[q * W + (i >> 5)], 1u << (i & 31));
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        __syncwarp();
+        if (lane == 0) {
             int acc = 0;
             for (int q = 0; q < P; ++q) {
                 base[q] = acc;
@@ -157,24 +171,24 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             base[P] = acc;
             bstart[b * (P + 1) + P] = acc;
         }
-        for (int e = threadIdx.x; e < P * W; e += blockDim.x) {
+        __syncwarp();
+        for (int e = lane; e < P * W; e += 32) {
             int before = 0;
             for (int w = e - e % W; w < e; ++w) before += __popc(msk[w]);
             bmask[b * P * W + e] = make_uint2(msk[e], (uint32_t)before);
         }
-        __syncthreads();
         // unordered placement of the sort keys (position << 16 | index)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int ck = p.c[s0 + i];
-            const int q = ck % P;
-            ukey[base[q] + atomicAdd(&cnt[q], 1)] = ((ck / P) << 16) | i;
+        for (int i = lane; i < n; i += 32) {
+            const int qp = qtab[__ldg(p.c + s0 + i)];
+            const int q = qp & 0xffff;
+            ukey[base[q] + atomicAdd(&cnt[q], 1)] = (qp & 0xffff0000) | i;
         }
-        __syncthreads();
-        const bool isw = beta * (float)(p.t[s1 - 1] - tau) > kWideLimit;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int ck = p.c[s0 + i];
-            const int q = ck % P;
-            const int key = ((ck / P) << 16) | i;
+        __syncwarp();
+        const bool isw = n > 0 && beta * (float)(p.t[s1 - 1] - p.t[s0]) > kWideLimit;
+        for (int i = lane; i < n; i += 32) {
+            const int qp = qtab[__ldg(p.c + s0 + i)];
+            const int q = qp & 0xffff, pos = qp >> 16;
+            const int key = (qp & 0xffff0000) | i;
             int rank = 0;
             for (int j = base[q]; j < base[q + 1]; ++j) rank += ukey[j] < key;
             const uint32_t* mq = msk + q * W;
@@ -183,11 +197,11 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             const float d = p.delta[s0 + i];
             const float em = exp_unbiased(-beta * d);
             const float ep = isw ? 0.f : exp_unbiased(beta * d);
-            recs[s0 + base[q] + rank] = make_float4(d, em, ep, __int_as_float((i << 16) | (ck / P)));
-            lrec[s0 + base[q] + irank] = make_float2(ep, __int_as_float(ck / P));
+            recs[s0 + base[q] + rank] = make_float4(d, em, ep, __int_as_float((i << 16) | pos));
+            lrec[s0 + base[q] + irank] = make_float2(ep, __int_as_float(pos));
         }
-        if (threadIdx.x == 0) wide[b] = isw ? 1 : 0;
-        __syncthreads();
+        if (lane == 0) wide[b] = isw ? 1 : 0;
+        __syncwarp();
     }
 }
 
@@ -651,11 +665,17 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         k_alpha_tiles<<<(unsigned)blocks, 256, 0, s>>>(p, p.at);
         ++*nl;
-        const size_t W = ((size_t)p.C + 31) / 32;
-        size_t smem = sizeof(int32_t) * (2 * (size_t)P + 1 + (size_t)p.C + (size_t)P * W);
-        int64_t grid = nb < (int64_t)sms * 16 ? nb : (int64_t)sms * 16;
-        k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 256, smem, s>>>(p, p.recs, p.lrec, p.bmask,
-                                                                     p.bstart, p.wide);
+        int warps = 8;
+        while (warps > 1 && bucket_smem_bytes(P, p.C, (int)M, warps) > 227 * 1024) --warps;
+        const size_t smem = bucket_smem_bytes(P, p.C, (int)M, warps);
+        if (smem > 48 * 1024) {
+            err = cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+        }
+        int64_t grid = (nb + warps - 1) / warps;
+        if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+        k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 32 * warps, smem, s>>>(p, p.recs, p.lrec,
+                                                                          p.bmask, p.bstart, p.wide);
         ++*nl;
         prof_mark(s, "bucket");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

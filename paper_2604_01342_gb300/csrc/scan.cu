@@ -281,6 +281,72 @@ cudaError_t launch_slice_aggregate(const Problem& p, double t_next, float* agg_S
     return cudaGetLastError();
 }
 
+// Pass C on the chunk-GEMM path (one sequence, one shared decay, offsets from pass A):
+// the same re-walk as k_scan_group<1>, with chunk k at events [k C, min((k+1) C, N)) and
+// the next chunk's span and first event slot loaded one chunk ahead, so that the loads
+// overlap the state writes and the decay of the current chunk.
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_scan_states_fast(Problem p) {
+    extern __shared__ float sm[];
+    float* S = sm;
+    float* G = sm + p.M;
+    if (failed(p.hdr)) return;
+    const int64_t nb = num_chunks(p);
+    const int64_t g = blockIdx.x;
+    const int64_t b0 = g * p.Gc;
+    if (b0 >= nb) return;
+    const int64_t b1 = b0 + p.Gc < nb ? b0 + p.Gc : nb;
+    const int M = p.M, C = p.C, tid = threadIdx.x;
+    const int64_t N = p.N;
+    const float beta = p.beta[0];
+    for (int j = tid; j < M; j += blockDim.x) {
+        S[j] = p.carry_S[g * M + j];
+        if (GRAD) G[j] = p.carry_G[g * M + j];
+    }
+    auto slot = [&](int64_t b, float& Dn, int& cn, float& dn) {
+        const int64_t s1 = (b + 1) * C < N ? (b + 1) * C : N;
+        Dn = s1 < N ? __ldg(p.Dspan + b) : 0.f;
+        const int64_t l = b * C + tid;
+        cn = l < s1 ? __ldg(p.c + l) : 0;
+        dn = l < s1 ? __ldg(p.delta + l) : 0.f;
+    };
+    float Dn, dn;
+    int cn;
+    slot(b0, Dn, cn, dn);
+    __syncthreads();
+    for (int64_t b = b0; b < b1; ++b) {
+        const int64_t s0 = b * C, s1 = s0 + C < N ? s0 + C : N;
+        const float D = Dn, d0 = dn;
+        const int c0 = cn;
+        if (b + 1 < b1) slot(b + 1, Dn, cn, dn);
+        for (int j = tid; j < M; j += blockDim.x) {
+            p.Shat[b * M + j] = S[j];
+            if (GRAD) p.Ghat[b * M + j] = G[j];
+        }
+        if (s1 == N) break;                     // the last chunk maps to the zero state
+        const float d = exp_unbiased(-beta * D);
+        for (int j = tid; j < M; j += blockDim.x) {
+            const float sv = S[j];
+            if (GRAD) G[j] = d * (G[j] + D * sv);
+            S[j] = d * sv;
+        }
+        __syncthreads();
+        const bool narrow = beta * D <= 16.f;
+        for (int64_t l = s0 + tid; l < s1; l += blockDim.x) {
+            const int cl = l == s0 + tid ? c0 : __ldg(p.c + l);
+            const float dl = l == s0 + tid ? d0 : __ldg(p.delta + l);
+            const float x = narrow ? D - dl : (float)(p.t[s1] - p.t[l]);
+            const float e = exp_unbiased(-beta * x);
+            atomicAdd(&S[cl], e);
+            if (GRAD) atomicAdd(&G[cl], x * e);
+        }
+        __syncthreads();
+    }
+}
+
+// the chunk-GEMM path's pass C: one sequence, one shared decay, offsets written by pass A
+static bool fast_states(const Problem& p) { return p.delta != nullptr && p.shared && p.B == 1; }
+
 cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
     size_t smem = sizeof(float) * 2 * (size_t)p.M;
     unsigned grid = (unsigned)(p.ng_max > 0 ? p.ng_max : 1);
@@ -297,7 +363,8 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
         k_carry_compose<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
-        k_scan_group<1, true><<<grid, 256, smem, s>>>(p);
+        if (fast_states(p)) k_scan_states_fast<true><<<grid, 256, smem, s>>>(p);
+        else k_scan_group<1, true><<<grid, 256, smem, s>>>(p);
         prof_mark(s, "scan_states");
     } else {
         k_scan_group<0, false><<<grid, 256, smem, s>>>(p);
@@ -305,7 +372,8 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
         k_carry_compose<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
-        k_scan_group<1, false><<<grid, 256, smem, s>>>(p);
+        if (fast_states(p)) k_scan_states_fast<false><<<grid, 256, smem, s>>>(p);
+        else k_scan_group<1, false><<<grid, 256, smem, s>>>(p);
         prof_mark(s, "scan_states");
     }
     *nl += 4;
