@@ -458,18 +458,17 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                     int4 ko = kd[j];
                     for (int i = 0; i < L; ++i) {
                         const int gi = g0 + i;
-                        j += gi >= ko.w ? 1 : 0;
-                        ko = kd[min(j, 31)];
-                        if (gi < g1)
-                            atomicAdd(dtile + ko.x + __float_as_int(lst[gi + ko.z].y),
-                                      __int_as_float(ko.y) * lst[gi + ko.z].x);
+                        if (gi >= ko.w) ko = kd[min(++j, 31)];     // next owner (at most one step)
+                        if (gi < g1) {
+                            const float2 l = lst[gi + ko.z];
+                            atomicAdd(dtile + ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x);
+                        }
                     }
                 } else {
                     int4 ko = kd[j];
                     for (int i = 0; i < L; ++i) {
                         const int gi = g0 + i;
-                        j += gi >= ko.w ? 1 : 0;
-                        ko = kd[min(j, 31)];
+                        if (gi >= ko.w) ko = kd[min(++j, 31)];
                         if (gi < g1) {
                             const float2 l = __ldg(lrec + s0 + l0 + gi + ko.z);
                             atomicAdd(dtile + ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x);
