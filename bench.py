@@ -413,8 +413,8 @@ def run_ours(args):
 # one ncu capture on the first 2e6 events of the benchmark stream
 # (profiles/ncu_pair_kernels_m1024_n2m.md).  A launch processes every event of the step and
 # the kernels' traffic grows in proportion to the events, so a launch moves N times this.
-DRAM_BYTES_PER_EVENT = {"pairs_bwd": (52421376 + 16428544) / 2e6,
-                        "pairs_fwd": (36704000 + 115456) / 2e6}
+DRAM_BYTES_PER_EVENT = {"pairs_bwd": (52423168 + 17010944) / 2e6,
+                        "pairs_fwd": (36691200 + 104448) / 2e6}
 
 
 def kernel_work(name, N, M, C):
