@@ -82,7 +82,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->P = (int)P;
     }
     pl->nb_max = (N + C - 1) / C + B;
-    int64_t target_groups = 1216;  // ~8 blocks per SM on 152 SMs
+    int64_t target_groups = 2432;  // ~16 blocks of 128 threads per SM on 152 SMs
     int64_t gc = (pl->nb_max + target_groups - 1) / target_groups;
     if (gc < 1) gc = 1;
     if (gc > 64) gc = 64;

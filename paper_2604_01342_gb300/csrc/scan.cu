@@ -358,22 +358,22 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
     if (Q < 1) Q = 1;
     const dim3 cgrid((unsigned)((p.M + 127) / 128), (unsigned)Q);
     if (p.grad) {
-        k_scan_group<0, true><<<grid, 256, smem, s>>>(p);
+        k_scan_group<0, true><<<grid, 128, smem, s>>>(p);
         prof_mark(s, "scan_reduce");
         k_carry_compose<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
-        if (fast_states(p)) k_scan_states_fast<true><<<grid, 256, smem, s>>>(p);
-        else k_scan_group<1, true><<<grid, 256, smem, s>>>(p);
+        if (fast_states(p)) k_scan_states_fast<true><<<grid, 128, smem, s>>>(p);
+        else k_scan_group<1, true><<<grid, 128, smem, s>>>(p);
         prof_mark(s, "scan_states");
     } else {
-        k_scan_group<0, false><<<grid, 256, smem, s>>>(p);
+        k_scan_group<0, false><<<grid, 128, smem, s>>>(p);
         prof_mark(s, "scan_reduce");
         k_carry_compose<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
-        if (fast_states(p)) k_scan_states_fast<false><<<grid, 256, smem, s>>>(p);
-        else k_scan_group<1, false><<<grid, 256, smem, s>>>(p);
+        if (fast_states(p)) k_scan_states_fast<false><<<grid, 128, smem, s>>>(p);
+        else k_scan_group<1, false><<<grid, 128, smem, s>>>(p);
         prof_mark(s, "scan_states");
     }
     *nl += 4;
