@@ -546,14 +546,15 @@ __global__ void k_colmax(const float* __restrict__ src, int64_t cols, const int6
 // dst[c][r] = split(2^a_c (src[r][c] - centre[c])) for r < rows_pad (zero for
 // r >= *rows_valid), a_c from the column's largest magnitude: transposes a chunk-major
 // [rows][cols] FP32 matrix into cols x rows fp16 hi/lo with chunks contiguous, and
-// inv_scale[c] = 2^-a_c.
+// inv_scale[c] = 2^-a_c.  Tiles of 64 rows x 32 columns; each thread stores two adjacent
+// rows as one half2 (rows_pad and ldd are even).
 __global__ void k_transpose_split_f16(const float* __restrict__ src, int64_t cols,
                                       const int64_t* rows_valid, int64_t rows_pad, __half* hi,
                                       __half* lo, int64_t ldd, const float* centre,
                                       const uint32_t* __restrict__ amax_bits, float* inv_scale) {
-    __shared__ float tile[32][33];
+    __shared__ float tile[64][33];
     __shared__ float sc[32];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 32;
     const int64_t nvalid = *rows_valid;
     if (threadIdx.y == 0) {
         const int64_t c = c0 + threadIdx.x;
@@ -561,19 +562,21 @@ __global__ void k_transpose_split_f16(const float* __restrict__ src, int64_t col
         sc[threadIdx.x] = ldexpf(1.f, a);
         if (blockIdx.y == 0 && c < cols) inv_scale[c] = ldexpf(1.f, -a);
     }
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int64_t r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] =
-            (r < nvalid && c < cols) ? src[r * cols + c] - (centre ? centre[c] : 0.f) : 0.f;
+    const int64_t c_ld = c0 + threadIdx.x;
+    const float cen = (centre && c_ld < cols) ? centre[c_ld] : 0.f;
+    for (int i = threadIdx.y; i < 64; i += blockDim.y) {
+        const int64_t r = r0 + i;
+        tile[i][threadIdx.x] = (r < nvalid && c_ld < cols) ? src[r * cols + c_ld] - cen : 0.f;
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        const int64_t c = c0 + i, r = r0 + 2 * threadIdx.x;
         if (c < cols && r < rows_pad) {
-            __half h, l;
-            tc::split_f16(tile[threadIdx.x][i] * sc[i], h, l);
-            hi[c * ldd + r] = h;
-            lo[c * ldd + r] = l;
+            __half h0, l0, h1, l1;
+            tc::split_f16(tile[2 * threadIdx.x][i] * sc[i], h0, l0);
+            tc::split_f16(tile[2 * threadIdx.x + 1][i] * sc[i], h1, l1);
+            *(__half2*)(hi + c * ldd + r) = __halves2half2(h0, h1);
+            *(__half2*)(lo + c * ldd + r) = __halves2half2(l0, l1);
         }
     }
 }
@@ -590,7 +593,8 @@ cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* r
     if (rb < 1) rb = 1;
     k_colmax<<<dim3((unsigned)cb, (unsigned)rb), dim3(32, 8), 0, s>>>(src, cols, rows_valid,
                                                                      centre, amax_bits);
-    dim3 grid((unsigned)cb, (unsigned)((rows_pad + 31) / 32));
+    if ((rows_pad & 1) || (ldd & 1)) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)cb, (unsigned)((rows_pad + 63) / 64));
     k_transpose_split_f16<<<grid, dim3(32, 8), 0, s>>>(src, cols, rows_valid, rows_pad, hi, lo,
                                                        ldd, centre, amax_bits, inv_scale);
     return cudaGetLastError();
