@@ -449,11 +449,21 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
         for (int o = 16; o >= 1; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         const int a = tc::row_exponent(amax);
         const float sc = ldexpf(1.f, a);
-        for (int64_t c = lane; c < cols; c += 32) {
+        // pairs of columns as half2 (ldd is even, so every pair is 4-byte aligned), then
+        // the odd last column
+        const int64_t cp = cols & ~(int64_t)1;
+        for (int64_t c = 2 * lane; c < cp; c += 64) {
+            __half h0, l0, h1, l1;
+            tc::split_f16(val(c) * sc, h0, l0);
+            tc::split_f16(val(c + 1) * sc, h1, l1);
+            *(__half2*)(hr + c) = __halves2half2(h0, h1);
+            *(__half2*)(lr + c) = __halves2half2(l0, l1);
+        }
+        if (lane == 0 && cp < cols) {
             __half h, l;
-            tc::split_f16(val(c) * sc, h, l);
-            hr[c] = h;
-            lr[c] = l;
+            tc::split_f16(val(cp) * sc, h, l);
+            hr[cp] = h;
+            lr[cp] = l;
         }
         if (lane == 0) inv_scale[r] = ldexpf(1.f, -a);
     }
@@ -493,11 +503,19 @@ __global__ void __launch_bounds__(256) k_split_f16_long_rows(const float* __rest
         const float sc = ldexpf(1.f, a);
         __half* hr = hi + r * ldd;
         __half* lr = lo + r * ldd;
-        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+        const int64_t cp = cols & ~(int64_t)1;
+        for (int64_t c = 2 * threadIdx.x; c < cp; c += 2 * blockDim.x) {
+            __half h0, l0, h1, l1;
+            tc::split_f16(sr[c] * sc, h0, l0);
+            tc::split_f16(sr[c + 1] * sc, h1, l1);
+            *(__half2*)(hr + c) = __halves2half2(h0, h1);
+            *(__half2*)(lr + c) = __halves2half2(l0, l1);
+        }
+        if (threadIdx.x == 0 && cp < cols) {
             __half h, l;
-            tc::split_f16(sr[c] * sc, h, l);
-            hr[c] = h;
-            lr[c] = l;
+            tc::split_f16(sr[cp] * sc, h, l);
+            hr[cp] = h;
+            lr[cp] = l;
         }
         if (threadIdx.x == 0) inv_scale[r] = ldexpf(1.f, -a);
     }
@@ -507,6 +525,7 @@ cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* hi, __hal
                                 int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
                                 float* inv_scale, double* row_sum) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (ldd & 1) return cudaErrorInvalidValue;
     const int64_t blocks = rows < 152 * 8 ? rows : 152 * 8;
     k_split_f16_long_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols,
                                                            inv_scale, row_sum);
@@ -518,7 +537,7 @@ cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo
                            const int64_t* rows_valid, float* inv_scale, const float* sub,
                            const float* coef) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
-    if ((sub == nullptr) != (coef == nullptr)) return cudaErrorInvalidValue;
+    if ((sub == nullptr) != (coef == nullptr) || (ldd & 1)) return cudaErrorInvalidValue;
     if (cols >= 4096 && !centre && !rows_valid && !sub)
         return split_f16_long_rows(src, lds, hi, lo, ldd, rows, cols, s, inv_scale, nullptr);
     int64_t blocks = (rows + 7) / 8;
