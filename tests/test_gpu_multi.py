@@ -35,11 +35,11 @@ def _scales(p):
     return cond["ll"], cond["dbeta"].sum(axis=1)       # one decay per kernel
 
 
-def _run(p, chunk=0, grad=True):
+def _run(p, chunk=0, grad=True, validate=True):
     import torch
     from paper_2604_01342_gb300 import torch_api
     t, c, T, mu, al, be = _dev(p)
-    r = torch_api.loglik_grad_multi(t, c, T, mu, al, be, chunk=chunk, grad=grad)
+    r = torch_api.loglik_grad_multi(t, c, T, mu, al, be, chunk=chunk, grad=grad, validate=validate)
     torch.cuda.synchronize()
     if not grad:
         return {"ll": float(r.item())}
@@ -61,6 +61,11 @@ def _check(p, got, what):
 def test_multi_kernel_matches_oracle(m, n, k, chunk, seed):
     p = synth.random_problem_multi(m, n, seed=seed, kernels=k)
     _check(p, _run(p, chunk=chunk), f"M={m} K={k} N={n}")
+
+
+def test_multi_kernel_without_validation():
+    p = synth.random_problem_multi(24, 6000, seed=62, kernels=2)
+    _check(p, _run(p, validate=False), "unvalidated K=2")
 
 
 def test_multi_kernel_loglik_only():

@@ -102,6 +102,15 @@ def test_walk_batches_past_the_factorised_limit(m, shared, mu_range):
     assert_close(gpu_run(p, path=1, chunk=96), oracle_ref(p), what=f"walk past limit m={m}")
 
 
+@pytest.mark.parametrize("path,shared", [(1, False), (2, True)])
+def test_without_validation(path, shared):
+    """validate=False skips the device checks and the mark counts: the chunk-GEMM path then
+    centres nothing and counts the marks of its compensator in the epilogue."""
+    p = synth.random_problem(40, 5000, 61, shared)
+    assert_close(gpu_run(p, path=path, chunk=96, validate=False), oracle_ref(p),
+                 what=f"unvalidated path {path}")
+
+
 def test_chunk_invariance_gemm():
     p = synth.random_problem(64, 6000, 6, True)
     res = [gpu_run(p, path=2, chunk=C) for C in (8, 64, 256, 1024)]
