@@ -74,38 +74,50 @@ __global__ void k_finalize_vec(Problem p, const double* colsum) {
 // mode 1: X = beta * (dal_gemm + m_j wsum_i + sum_r part_r[i][j])  (chunk-GEMM path, one
 //         shared beta; the GEMM ran on S^ - m, so m_j sum_b W[b][i] restores the centre;
 //         part_r are the intra-chunk pair tiles of chunk range r (ceil(M / P) square,
-//         tile-major), summed in range order)
+//         tile-major), summed in range order).  Mode 1 walks the elements in the tiles'
+//         order, so that the reads of the R pair tiles are contiguous.
 __global__ void k_finalize_alpha(Problem p, int mode) {
     const int M = p.M;
     const bool bad = failed(p.hdr);
     const double nanv = __longlong_as_double(0x7ff8000000000000ll);
-    const int64_t total = (int64_t)p.B * M * M;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / ((int64_t)M * M), ij = e % ((int64_t)M * M);
-        const int j = (int)(ij % M);
-        double x;
-        if (mode == 0) {
-            x = p.dal_acc[e];
-        } else {
-            const float beta = p.beta[0];
-            const int i = (int)(ij / M), P = p.P, TR = (M + P - 1) / P;
-            const int64_t at = (((int64_t)(i % P) * P + (j % P)) * TR + (i / P)) * TR + (j / P);
-            const int64_t stride = (int64_t)P * P * TR * TR;
-            // compensated FP32 sum of the chunk ranges' tiles (FP64 arithmetic runs at 1/64
-            // of the FP32 rate here)
-            float pairs = 0.f, comp = 0.f;
-            for (int r = 0; r < p.dal_parts; ++r) {
-                const float y = p.dal_part[r * stride + at] - comp;
-                const float t = pairs + y;
-                comp = (t - pairs) - y;
-                pairs = t;
-            }
-            x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] +
-                                (double)pairs);
+    if (mode == 0) {
+        const int64_t total = (int64_t)p.B * M * M;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t s = e / ((int64_t)M * M), ij = e % ((int64_t)M * M);
+            const int j = (int)(ij % M);
+            const double v = p.dal_acc[e] - p.E_acc[s * M + j];
+            p.d_alpha[e] = bad ? (float)nanv : (float)v;
         }
-        const double v = x - p.E_acc[s * M + j];
-        p.d_alpha[e] = bad ? (float)nanv : (float)v;
+        return;
+    }
+    const float beta = p.beta[0];
+    const int P = p.P, TR = (M + P - 1) / P;
+    const int64_t stride = (int64_t)P * P * TR * TR;
+    for (int64_t at = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; at < stride;
+         at += (int64_t)gridDim.x * blockDim.x) {
+        // at = ((qi * P + qj) * TR + ti) * TR + tj  <->  i = ti * P + qi, j = tj * P + qj
+        const int tj = (int)(at % TR);
+        const int64_t r1 = at / TR;
+        const int ti = (int)(r1 % TR);
+        const int q = (int)(r1 / TR);
+        const int qi = q / P, qj = q % P;
+        const int i = ti * P + qi, j = tj * P + qj;
+        if (i >= M || j >= M) continue;
+        // compensated FP32 sum of the chunk ranges' tiles (FP64 arithmetic runs at 1/64 of
+        // the FP32 rate here)
+        float pairs = 0.f, comp = 0.f;
+        for (int r = 0; r < p.dal_parts; ++r) {
+            const float y = p.dal_part[r * stride + at] - comp;
+            const float t = pairs + y;
+            comp = (t - pairs) - y;
+            pairs = t;
+        }
+        const int64_t ij = (int64_t)i * M + j;
+        const double x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] +
+                                         (double)pairs);
+        const double v = x - p.E_acc[j];
+        p.d_alpha[ij] = bad ? (float)nanv : (float)v;
     }
 }
 
