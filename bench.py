@@ -448,7 +448,8 @@ def kernel_work(name, N, M, C):
 
 
 def roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src):
-    """Dominant kernel's achieved rate against its bound (units stated in the design doc)."""
+    """Dominant kernel's achieved rate against its bound (bytes, flops or FMAs per launch over
+    the launch's CUDA-event time, against the peak of that bound)."""
     if not kern_ms:
         return None
     C = args.chunk or 192

@@ -72,7 +72,7 @@ typedef enum {
     HAWKES_ERR_PARAM_DOMAIN = 5,      /* mu <= 0, alpha < 0, beta <= 0, or a non-finite value  */
     HAWKES_ERR_NONPOS_INTENSITY = 6,  /* some lambda_k <= 0 (impossible inside the domain)     */
     HAWKES_ERR_WORKSPACE = 7,         /* workspace null, too small or not 256-byte aligned     */
-    HAWKES_ERR_UNSUPPORTED = 8,       /* a configuration this build does not implement         */
+    HAWKES_ERR_UNSUPPORTED = 8,       /* a configuration the library does not implement          */
     HAWKES_ERR_CUDA = 9               /* a CUDA runtime call failed                            */
 } hawkes_status;
 
