@@ -25,11 +25,23 @@
 namespace hk {
 
 // PHASE 0 = A (compose from zero), 1 = C (re-walk from carry and write states).
+// With few marks (M <= kScanSplitM) the events of a chunk pile their contributions onto a
+// handful of state entries, so each warp adds into its own copy of the state and the
+// copies are folded into S, G once per chunk.
+constexpr int kScanSplitM = 64;
+__host__ __device__ inline size_t scan_smem_floats(int M, int threads) {
+    return 2 * (size_t)M + (M <= kScanSplitM ? 2 * (size_t)M * (threads / 32) : 0);
+}
+
 template <int PHASE, bool GRAD>
 __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
     extern __shared__ float sm[];
     float* S = sm;
     float* G = sm + p.M;
+    const bool split = p.M <= kScanSplitM;
+    const int nwarps = blockDim.x >> 5;
+    float* Sw = sm + 2 * p.M + (threadIdx.x >> 5) * p.M;     // this warp's copies (split only)
+    float* Gw = sm + 2 * p.M + (nwarps + (threadIdx.x >> 5)) * p.M;
     __shared__ double span_sh;
     __shared__ int reset_sh;
     if (failed(p.hdr)) return;
@@ -48,6 +60,8 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
             if (GRAD) G[j] = p.carry_G[g * M + j];
         }
     }
+    if (split)
+        for (int j = threadIdx.x; j < 2 * nwarps * M; j += blockDim.x) sm[2 * M + j] = 0.f;
     if (threadIdx.x == 0) { span_sh = 0.0; reset_sh = 0; }
     __syncthreads();
     // Chunk-GEMM path (p.delta set): the per-event offsets delta_l = t_l - t_0 from the chunk
@@ -130,10 +144,26 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
                 x = (float)(tn - p.t[l]);
             }
             float e = exp_unbiased(-beta_of(p, seq, cl) * x);
-            atomicAdd(&S[cl], e);
-            if (GRAD) atomicAdd(&G[cl], x * e);
+            atomicAdd(split ? &Sw[cl] : &S[cl], e);
+            if (GRAD) atomicAdd(split ? &Gw[cl] : &G[cl], x * e);
         }
         __syncthreads();
+        if (split)      // fold the warps' copies (same thread-to-entry map as every other pass)
+            for (int j = threadIdx.x; j < M; j += blockDim.x) {
+                float sv = S[j], gv = GRAD ? G[j] : 0.f;
+                for (int w = 0; w < nwarps; ++w) {
+                    float* sw = sm + 2 * M + w * M;
+                    sv += sw[j];
+                    sw[j] = 0.f;
+                    if (GRAD) {
+                        float* gw = sm + 2 * M + (nwarps + w) * M;
+                        gv += gw[j];
+                        gw[j] = 0.f;
+                    }
+                }
+                S[j] = sv;
+                if (GRAD) G[j] = gv;
+            }
     }
     if (PHASE == 0) {
         for (int j = threadIdx.x; j < M; j += blockDim.x) {
@@ -348,7 +378,17 @@ __global__ void __launch_bounds__(256) k_scan_states_fast(Problem p) {
 static bool fast_states(const Problem& p) { return p.delta != nullptr && p.shared && p.B == 1; }
 
 cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
-    size_t smem = sizeof(float) * 2 * (size_t)p.M;
+    const size_t smem_fast = sizeof(float) * 2 * (size_t)p.M;
+    size_t smem = sizeof(float) * scan_smem_floats(p.M, 128);
+    if (smem > 48 * 1024) {       // large M on the chunk-GEMM path: opt in to more shared memory
+        const void* kerns[] = {(const void*)k_scan_group<0, true>, (const void*)k_scan_group<1, true>,
+                               (const void*)k_scan_group<0, false>, (const void*)k_scan_group<1, false>,
+                               (const void*)k_scan_states_fast<true>, (const void*)k_scan_states_fast<false>};
+        for (const void* k : kerns) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+    }
     unsigned grid = (unsigned)(p.ng_max > 0 ? p.ng_max : 1);
     // segments of the carry pass: enough (mark, segment) threads for every SM, at least
     // four groups per segment
@@ -363,7 +403,7 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
         k_carry_compose<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
-        if (fast_states(p)) k_scan_states_fast<true><<<grid, 128, smem, s>>>(p);
+        if (fast_states(p)) k_scan_states_fast<true><<<grid, 128, smem_fast, s>>>(p);
         else k_scan_group<1, true><<<grid, 128, smem, s>>>(p);
         prof_mark(s, "scan_states");
     } else {
@@ -372,7 +412,7 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
         k_carry_compose<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
-        if (fast_states(p)) k_scan_states_fast<false><<<grid, 128, smem, s>>>(p);
+        if (fast_states(p)) k_scan_states_fast<false><<<grid, 128, smem_fast, s>>>(p);
         else k_scan_group<1, false><<<grid, 128, smem, s>>>(p);
         prof_mark(s, "scan_states");
     }

@@ -35,6 +35,13 @@ def test_gemm_path_matches_oracle(m, chunk):
     assert_close(gpu_run(p, path=2, chunk=chunk), oracle_ref(p), what=f"gemm m={m} C={chunk}")
 
 
+def test_gemm_path_large_m():
+    """M = 8192 (64 mark blocks): the scan and epilogue kernels opt in to more than 48 KB
+    of shared memory per block."""
+    p = synth.random_problem(8192, 4000, 63, True, rho=0.5)
+    assert_close(gpu_run(p, path=2, chunk=128), oracle_ref(p), what="gemm path M=8192")
+
+
 def test_gemm_path_forward_only():
     p = synth.random_problem(200, 3000, 9, True)
     assert_close(gpu_run(p, path=2, grad=False), oracle_ref(p, grad=False), grad=False)
