@@ -433,6 +433,7 @@ def kernel_work(name, N, M, C):
         "scan_states": ("hbm", 8.0 * N + 8.0 * M * nb),         # offsets, c in; S^, G^ out
         "split_S": ("hbm", 4.0 * M * nb + 4.0 * M * nb),
         "split_G": ("hbm", 8.0 * M * nb + 4.0 * M * nb),         # S^, G^ in; S^ - beta G^ out
+        "split_S_G": ("hbm", 8.0 * M * nb + 8.0 * M * nb),       # S^, G^ in; both splits out
         "bucket": ("hbm", 8.0 * N + 24.0 * N),                  # offsets, c in; records out
         "epilogue": ("hbm", 12.0 * N + 8.0 * N + 12.0 * N),
         "split_W": ("hbm", 4.0 * M * nb + 4.0 * M * nb),

@@ -34,6 +34,11 @@ cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo
 cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* hi, __half* lo,
                                 int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
                                 float* inv_scale, double* row_sum);
+cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
+                                const float* centre, const float* coef, __half* hi1,
+                                __half* lo1, float* isc1, __half* hi2, __half* lo2, float* isc2,
+                                int64_t ldd, int64_t rows, int64_t cols,
+                                const int64_t* rows_valid, cudaStream_t s);
 cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
                                 int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
                                 cudaStream_t s, const float* centre, uint32_t* amax_bits,
@@ -625,11 +630,21 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
         return err;
     ++*nl;
     prof_mark(s, "split_alpha");
-    if ((err = split_f16_rows(p.Shat, M, p.S_h, p.S_l, p.ldk, nb, M, s, p.cen_S, nb_dev,
-                              p.isc_S, nullptr, nullptr)) != cudaSuccess)
-        return err;
-    ++*nl;
-    prof_mark(s, "split_S");
+    // S^ - m for Y and, with the gradient, S^ - beta G^ for Z (see below) in one pass over S^
+    if (p.grad) {
+        if ((err = split_f16_rows_pair(p.Shat, p.Ghat, M, p.cen_S, p.beta, p.S_h, p.S_l, p.isc_S,
+                                       p.G_h, p.G_l, p.isc_G, p.ldk, nb, M, nb_dev, s)) !=
+            cudaSuccess)
+            return err;
+        ++*nl;
+        prof_mark(s, "split_S_G");
+    } else {
+        if ((err = split_f16_rows(p.Shat, M, p.S_h, p.S_l, p.ldk, nb, M, s, p.cen_S, nb_dev,
+                                  p.isc_S, nullptr, nullptr)) != cudaSuccess)
+            return err;
+        ++*nl;
+        prof_mark(s, "split_S");
+    }
     if ((err = tc_gemm_f16x3(p.S_h, p.S_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Y, M, (int)nb,
                              (int)M, M, 1, false, p.hdr, s, p.bias_Y, p.isc_S, p.isc_al)) !=
         cudaSuccess)
@@ -640,12 +655,7 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
         // Z = (S^ - beta G^) alpha^T: the decay-gradient term of an event is
         // e (Z - beta delta Y) + (A - beta B), so the near-cancelling difference of the
         // forward state and its beta-derivative is formed once per chunk and element from
-        // the scan's states, before any rounding of the tensor-core product
-        if ((err = split_f16_rows(p.Shat, M, p.G_h, p.G_l, p.ldk, nb, M, s, nullptr, nb_dev,
-                                  p.isc_G, p.Ghat, p.beta)) != cudaSuccess)
-            return err;
-        ++*nl;
-        prof_mark(s, "split_G");
+        // the scan's states (split above), before any rounding of the tensor-core product
         if ((err = tc_gemm_f16x3(p.G_h, p.G_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Z, M, (int)nb,
                                  (int)M, M, 1, false, p.hdr, s, nullptr, p.isc_G, p.isc_al)) !=
             cudaSuccess)

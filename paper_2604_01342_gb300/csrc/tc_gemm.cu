@@ -469,6 +469,86 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
     }
 }
 
+// Two row-scaled splits of one matrix in one pass over it (one warp per row): out1 = src -
+// centre (per column) and out2 = src - (*coef) sub, each with its own row exponent and
+// inverse scale; rows at or past *rows_valid are written as zeros.
+__global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float* __restrict__ sub,
+                                      int64_t lds, const float* __restrict__ centre,
+                                      const float* __restrict__ coef, __half* hi1, __half* lo1,
+                                      float* isc1, __half* hi2, __half* lo2, float* isc2,
+                                      int64_t ldd, int64_t rows, int64_t cols,
+                                      const int64_t* rows_valid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nvalid = rows_valid ? *rows_valid : rows;
+    const float cf = *coef;
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+        const float* sr = src + r * lds;
+        const float* ur = sub + r * lds;
+        __half *h1 = hi1 + r * ldd, *l1 = lo1 + r * ldd, *h2 = hi2 + r * ldd, *l2 = lo2 + r * ldd;
+        if (r >= nvalid) {
+            for (int64_t c = lane; c < cols; c += 32)
+                h1[c] = l1[c] = h2[c] = l2[c] = __float2half_rn(0.f);
+            if (lane == 0) { isc1[r] = 1.f; isc2[r] = 1.f; }
+            continue;
+        }
+        float m1 = 0.f, m2 = 0.f;
+        for (int64_t c = lane; c < cols; c += 32) {
+            const float v = sr[c];
+            m1 = fmaxf(m1, fabsf(v - centre[c]));
+            m2 = fmaxf(m2, fabsf(v - cf * ur[c]));
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+            m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        }
+        const int a1 = tc::row_exponent(m1), a2 = tc::row_exponent(m2);
+        const float sc1 = ldexpf(1.f, a1), sc2 = ldexpf(1.f, a2);
+        const int64_t cp = cols & ~(int64_t)1;
+        for (int64_t c = 2 * lane; c < cp; c += 64) {
+            const float v0 = sr[c], v1 = sr[c + 1];
+            __half x0, y0, x1, y1;
+            tc::split_f16((v0 - centre[c]) * sc1, x0, y0);
+            tc::split_f16((v1 - centre[c + 1]) * sc1, x1, y1);
+            *(__half2*)(h1 + c) = __halves2half2(x0, x1);
+            *(__half2*)(l1 + c) = __halves2half2(y0, y1);
+            tc::split_f16((v0 - cf * ur[c]) * sc2, x0, y0);
+            tc::split_f16((v1 - cf * ur[c + 1]) * sc2, x1, y1);
+            *(__half2*)(h2 + c) = __halves2half2(x0, x1);
+            *(__half2*)(l2 + c) = __halves2half2(y0, y1);
+        }
+        if (lane == 0 && cp < cols) {
+            __half x, y;
+            tc::split_f16((sr[cp] - centre[cp]) * sc1, x, y);
+            h1[cp] = x;
+            l1[cp] = y;
+            tc::split_f16((sr[cp] - cf * ur[cp]) * sc2, x, y);
+            h2[cp] = x;
+            l2[cp] = y;
+        }
+        if (lane == 0) {
+            isc1[r] = ldexpf(1.f, -a1);
+            isc2[r] = ldexpf(1.f, -a2);
+        }
+    }
+}
+
+cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
+                                const float* centre, const float* coef, __half* hi1,
+                                __half* lo1, float* isc1, __half* hi2, __half* lo2, float* isc2,
+                                int64_t ldd, int64_t rows, int64_t cols,
+                                const int64_t* rows_valid, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (!src || !sub || !centre || !coef || (ldd & 1)) return cudaErrorInvalidValue;
+    int64_t blocks = (rows + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_split_f16_rows_pair<<<(unsigned)blocks, 256, 0, s>>>(src, sub, lds, centre, coef, hi1, lo1,
+                                                           isc1, hi2, lo2, isc2, ldd, rows, cols,
+                                                           rows_valid);
+    return cudaGetLastError();
+}
+
 // Long rows (cols >> 32): one block per row, two passes over it (the row maximum and, if
 // asked, the FP64 row sum; then the split, mostly from L2), no centre or subtrahend.
 __global__ void __launch_bounds__(256) k_split_f16_long_rows(const float* __restrict__ src,
