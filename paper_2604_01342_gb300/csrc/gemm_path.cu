@@ -38,11 +38,11 @@ cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
                                 const float* centre, const float* coef, __half* hi1,
                                 __half* lo1, float* isc1, __half* hi2, __half* lo2, float* isc2,
                                 int64_t ldd, int64_t rows, int64_t cols,
-                                const int64_t* rows_valid, cudaStream_t s);
+                                const int64_t* rows_valid, uint32_t* colmax, cudaStream_t s);
 cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
                                 int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
                                 cudaStream_t s, const float* centre, uint32_t* amax_bits,
-                                float* inv_scale);
+                                float* inv_scale, bool have_max);
 
 // Centre of the Y GEMM operand: the stationary means m_j = n_j / (beta T) of S_j, and the
 // exact products alpha . m in FP64.  (The Z operand S - beta G has stationary mean 0.)
@@ -632,8 +632,10 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     prof_mark(s, "split_alpha");
     // S^ - m for Y and, with the gradient, S^ - beta G^ for Z (see below) in one pass over S^
     if (p.grad) {
+        // (and the column maxima of S^ - m for the transposed split of the dalpha GEMM)
         if ((err = split_f16_rows_pair(p.Shat, p.Ghat, M, p.cen_S, p.beta, p.S_h, p.S_l, p.isc_S,
-                                       p.G_h, p.G_l, p.isc_G, p.ldk, nb, M, nb_dev, s)) !=
+                                       p.G_h, p.G_l, p.isc_G, p.ldk, nb, M, nb_dev, p.colmax,
+                                       s)) !=
             cudaSuccess)
             return err;
         ++*nl;
@@ -782,9 +784,9 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
         ++*nl;
         prof_mark(s, "split_W");
         if ((err = transpose_split_f16(p.Shat, M, nb_dev, p.nbp, p.St_h, p.St_l, p.nbp, s,
-                                       p.cen_S, p.colmax, p.isc_St)) != cudaSuccess)
+                                       p.cen_S, p.colmax, p.isc_St, true)) != cudaSuccess)
             return err;
-        *nl += 2;
+        ++*nl;
         prof_mark(s, "transpose_S");
         cudaMemsetAsync(p.dal_gemm, 0, sizeof(float) * (size_t)M * M, s);
         // split K so that the blocks (one per SM) fill whole waves: minimise

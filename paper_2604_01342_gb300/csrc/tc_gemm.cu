@@ -477,11 +477,16 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
                                       const float* __restrict__ coef, __half* hi1, __half* lo1,
                                       float* isc1, __half* hi2, __half* lo2, float* isc2,
                                       int64_t ldd, int64_t rows, int64_t cols,
-                                      const int64_t* rows_valid) {
+                                      const int64_t* rows_valid, uint32_t* colmax) {
+    extern __shared__ uint32_t cmax_sh[];     // [cols] this block's column maxima of |out1|
     const int lane = threadIdx.x & 31;
     const int64_t nvalid = rows_valid ? *rows_valid : rows;
     const float cf = *coef;
     const int64_t wpb = blockDim.x >> 5;
+    if (colmax) {
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) cmax_sh[c] = 0u;
+        __syncthreads();
+    }
     for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
         const float* sr = src + r * lds;
         const float* ur = sub + r * lds;
@@ -495,8 +500,10 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
         float m1 = 0.f, m2 = 0.f;
         for (int64_t c = lane; c < cols; c += 32) {
             const float v = sr[c];
-            m1 = fmaxf(m1, fabsf(v - centre[c]));
+            const float d1 = fabsf(v - centre[c]);
+            m1 = fmaxf(m1, d1);
             m2 = fmaxf(m2, fabsf(v - cf * ur[c]));
+            if (colmax && d1 > 0.f) atomicMax(&cmax_sh[c], __float_as_uint(d1));
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
@@ -532,20 +539,38 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
             isc2[r] = ldexpf(1.f, -a2);
         }
     }
+    if (colmax) {
+        __syncthreads();
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x)
+            if (cmax_sh[c]) atomicMax(colmax + c, cmax_sh[c]);
+    }
 }
 
+// colmax (optional, [cols] uint bits, zeroed here): the largest |out1| of every column over
+// the valid rows, for a later transposed split of the same matrix.
 cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
                                 const float* centre, const float* coef, __half* hi1,
                                 __half* lo1, float* isc1, __half* hi2, __half* lo2, float* isc2,
                                 int64_t ldd, int64_t rows, int64_t cols,
-                                const int64_t* rows_valid, cudaStream_t s) {
+                                const int64_t* rows_valid, uint32_t* colmax, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if (!src || !sub || !centre || !coef || (ldd & 1)) return cudaErrorInvalidValue;
+    const size_t smem = colmax ? sizeof(uint32_t) * (size_t)cols : 0;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (colmax) {
+        cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint32_t) * (size_t)cols, s);
+        if (e != cudaSuccess) return e;
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_split_f16_rows_pair,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+    }
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_split_f16_rows_pair<<<(unsigned)blocks, 256, 0, s>>>(src, sub, lds, centre, coef, hi1, lo1,
-                                                           isc1, hi2, lo2, isc2, ldd, rows, cols,
-                                                           rows_valid);
+    k_split_f16_rows_pair<<<(unsigned)blocks, 256, smem, s>>>(src, sub, lds, centre, coef, hi1,
+                                                              lo1, isc1, hi2, lo2, isc2, ldd, rows,
+                                                              cols, rows_valid, colmax);
     return cudaGetLastError();
 }
 
@@ -680,18 +705,21 @@ __global__ void k_transpose_split_f16(const float* __restrict__ src, int64_t col
     }
 }
 
+// have_max: amax_bits already holds the column maxima (taken by an earlier pass over src).
 cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
                                 int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
                                 cudaStream_t s, const float* centre, uint32_t* amax_bits,
-                                float* inv_scale) {
+                                float* inv_scale, bool have_max) {
     if (cols <= 0 || rows_pad <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(amax_bits, 0, sizeof(uint32_t) * (size_t)cols, s);
-    if (e != cudaSuccess) return e;
     const int64_t cb = (cols + 31) / 32;
-    int64_t rb = (152 * 8 + cb - 1) / cb;
-    if (rb < 1) rb = 1;
-    k_colmax<<<dim3((unsigned)cb, (unsigned)rb), dim3(32, 8), 0, s>>>(src, cols, rows_valid,
-                                                                     centre, amax_bits);
+    if (!have_max) {
+        cudaError_t e = cudaMemsetAsync(amax_bits, 0, sizeof(uint32_t) * (size_t)cols, s);
+        if (e != cudaSuccess) return e;
+        int64_t rb = (152 * 8 + cb - 1) / cb;
+        if (rb < 1) rb = 1;
+        k_colmax<<<dim3((unsigned)cb, (unsigned)rb), dim3(32, 8), 0, s>>>(src, cols, rows_valid,
+                                                                         centre, amax_bits);
+    }
     if ((rows_pad & 1) || (ldd & 1)) return cudaErrorInvalidValue;
     dim3 grid((unsigned)cb, (unsigned)((rows_pad + 63) / 64));
     k_transpose_split_f16<<<grid, dim3(32, 8), 0, s>>>(src, cols, rows_valid, rows_pad, hi, lo,
