@@ -37,10 +37,9 @@ struct Plan {
     int64_t nb_max, ng_max;
     size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
         off_grp_dt, off_grp_reset, off_seg_comp, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
-        off_dal_gemm, off_al_h, off_al_l, off_S_h, off_S_l, off_G_h, off_G_l, off_Wt_h, off_Wt_l,
-        off_St_h, off_St_l, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf, off_delta, off_Dspan, off_Tmt,
+        off_dal_gemm, off_al_p, off_S_p, off_G_p, off_Wt_p, off_St_p, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf, off_delta, off_Dspan, off_Tmt,
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
-    int64_t ldk, nbp;
+    int64_t ldk, ldt, nbp;
     int dal_parts_max;
     int K;                 // decay kernels (one workspace slice each)
     size_t scratch_off;
@@ -106,11 +105,11 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     size_t n_acc = (size_t)B * (1 + 4 * (size_t)M) + (grad ? (size_t)B * M * M : 0);
     pl->off_acc = take(sizeof(double) * n_acc);
     pl->off_colsum = take(sizeof(double) * (size_t)B * M);
-    pl->ldk = ((int64_t)M + 7) / 8 * 8;
     pl->nbp = (pl->nb_max + 7) / 8 * 8;
+    pl->ldk = ((int64_t)M + 31) / 32 * 64;          // paired fp16 rows (tc_gemm.cu)
+    pl->ldt = (pl->nbp + 31) / 32 * 64;
     pl->off_Y = pl->off_Z = pl->off_W = pl->off_dal_gemm = 0;
-    pl->off_al_h = pl->off_al_l = pl->off_S_h = pl->off_S_l = pl->off_G_h = pl->off_G_l = 0;
-    pl->off_Wt_h = pl->off_Wt_l = pl->off_St_h = pl->off_St_l = 0;
+    pl->off_al_p = pl->off_S_p = pl->off_G_p = pl->off_Wt_p = pl->off_St_p = 0;
     pl->off_recs = pl->off_lrec = pl->off_bmask = pl->off_kprep = pl->off_dal_part = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
     pl->off_delta = pl->off_Dspan = pl->off_Tmt = 0;
     pl->off_cen = pl->off_wsum = pl->off_at = pl->off_isc = pl->off_colmax = 0;
@@ -145,20 +144,15 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_Y = take(sizeof(float) * nbM);
         pl->off_isc = take(sizeof(float) * (3 * (size_t)M + 2 * (size_t)pl->nb_max));
         pl->off_colmax = take(sizeof(uint32_t) * (size_t)M);
-        pl->off_al_h = take(h * (size_t)M * pl->ldk);
-        pl->off_al_l = take(h * (size_t)M * pl->ldk);
-        pl->off_S_h = take(h * (size_t)pl->nb_max * pl->ldk);
-        pl->off_S_l = take(h * (size_t)pl->nb_max * pl->ldk);
+        pl->off_al_p = take(h * (size_t)M * pl->ldk);
+        pl->off_S_p = take(h * (size_t)pl->nb_max * pl->ldk);
         if (grad) {
             pl->off_Z = take(sizeof(float) * nbM);
             pl->off_W = take(sizeof(float) * (size_t)M * pl->nbp);   // transposed: [M][nbp]
             pl->off_dal_gemm = take(sizeof(float) * (size_t)M * M);
-            pl->off_G_h = take(h * (size_t)pl->nb_max * pl->ldk);
-            pl->off_G_l = take(h * (size_t)pl->nb_max * pl->ldk);
-            pl->off_Wt_h = take(h * (size_t)M * pl->nbp);
-            pl->off_Wt_l = take(h * (size_t)M * pl->nbp);
-            pl->off_St_h = take(h * (size_t)M * pl->nbp);
-            pl->off_St_l = take(h * (size_t)M * pl->nbp);
+            pl->off_G_p = take(h * (size_t)pl->nb_max * pl->ldk);
+            pl->off_Wt_p = take(h * (size_t)M * pl->ldt);
+            pl->off_St_p = take(h * (size_t)M * pl->ldt);
         }
     }
     pl->scratch_off = path == PATH_GEMM ? take(sizeof(float) * ((size_t)M + 2)) : 0;
@@ -198,16 +192,11 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.Z = at<float>(ws, pl.off_Z);
     p.W = at<float>(ws, pl.off_W);
     p.dal_gemm = at<float>(ws, pl.off_dal_gemm);
-    p.al_h = at<__half>(ws, pl.off_al_h);
-    p.al_l = at<__half>(ws, pl.off_al_l);
-    p.S_h = at<__half>(ws, pl.off_S_h);
-    p.S_l = at<__half>(ws, pl.off_S_l);
-    p.G_h = at<__half>(ws, pl.off_G_h);
-    p.G_l = at<__half>(ws, pl.off_G_l);
-    p.Wt_h = at<__half>(ws, pl.off_Wt_h);
-    p.Wt_l = at<__half>(ws, pl.off_Wt_l);
-    p.St_h = at<__half>(ws, pl.off_St_h);
-    p.St_l = at<__half>(ws, pl.off_St_l);
+    p.al_p = at<__half>(ws, pl.off_al_p);
+    p.S_p = at<__half>(ws, pl.off_S_p);
+    p.G_p = at<__half>(ws, pl.off_G_p);
+    p.Wt_p = at<__half>(ws, pl.off_Wt_p);
+    p.St_p = at<__half>(ws, pl.off_St_p);
     p.recs = at<float4>(ws, pl.off_recs);
     p.lrec = at<float2>(ws, pl.off_lrec);
     p.bmask = at<uint2>(ws, pl.off_bmask);
@@ -235,6 +224,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.isc_St = p.isc_Wt ? p.isc_Wt + M : nullptr;
     p.colmax = at<uint32_t>(ws, pl.off_colmax);
     p.ldk = pl.ldk;
+    p.ldt = pl.ldt;
     p.nbp = pl.nbp;
     p.C = pl.C;
     p.P = pl.P;

@@ -81,12 +81,13 @@ struct Problem {
     float* W;                // [M][nbp]  per-chunk weights of the dalpha GEMM, transposed:
                              // W[i * nbp + b] = sum of w_k e_k over the events k of mark i in chunk b
     float* dal_gemm;         // [M*M]
-    // fp16 hi/lo operands of the tensor-core GEMMs (rows scaled by powers of two)
-    __half *al_h, *al_l;     // [M][ldk]       alpha
-    __half *S_h, *S_l;       // [nb_max][ldk]  chunk-start states
-    __half *G_h, *G_l;       // [nb_max][ldk]  Shat - beta Ghat
-    __half *Wt_h, *Wt_l;     // [M][nbp]       W transposed (chunks contiguous)
-    __half *St_h, *St_l;     // [M][nbp]       S^ transposed
+    // fp16 hi/lo operands of the tensor-core GEMMs (rows scaled by powers of two), as
+    // paired rows: per group of 32 elements their 32 high parts, then their 32 low parts
+    __half* al_p;            // [M][ldk]       alpha
+    __half* S_p;             // [nb_max][ldk]  chunk-start states
+    __half* G_p;             // [nb_max][ldk]  Shat - beta Ghat
+    __half* Wt_p;            // [M][ldt]       W transposed (chunks contiguous)
+    __half* St_p;            // [M][ldt]       S^ transposed
     float *isc_al, *isc_S, *isc_G, *isc_Wt, *isc_St;   // inverse row scales of the operands
     uint32_t* colmax;        // [M] column maxima scratch of the transposed operands
     // intra-chunk pair kernels
@@ -110,7 +111,8 @@ struct Problem {
     float* cen_S;            // [M] m_j = n_j / (beta T): stationary mean of S_j
     float* bias_Y;           // [M] alpha . cen_S  (FP64-accumulated)
     double* wsum_acc;        // [M] sum_b W[b][i]
-    int64_t ldk;             // M rounded up to 8
+    int64_t ldk;             // 64 ceil(M / 32): halves per paired row of K = M elements
+    int64_t ldt;             // 64 ceil(nbp / 32): halves per paired row of K = nbp elements
     int64_t nbp;             // nb_max rounded up to 8
     // outputs
     double* out_ll;          // [B]

@@ -21,28 +21,28 @@ namespace hk {
 
 cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int* nl);
 
-// Tensor-core GEMM and fp16 hi/lo splitting of row-scaled operands (tc_gemm.cu).
-cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const __half* Bh,
-                          const __half* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
-                          int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
-                          cudaStream_t s, const float* bias, const float* inv_sa,
-                          const float* inv_sb);
-cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo, int64_t ldd,
+// Tensor-core GEMM and fp16 hi/lo splitting of row-scaled operands into paired rows
+// (tc_gemm.cu).
+cudaError_t tc_gemm_f16x3(const __half* A, int64_t lda, const __half* B, int64_t ldb, float* D,
+                          int64_t ldd, int Mdim, int Ndim, int64_t Kdim, int splits,
+                          bool accumulate, WsHeader* hdr, cudaStream_t s, const float* bias,
+                          const float* inv_sa, const float* inv_sb);
+cudaError_t split_f16_rows(const float* src, int64_t lds, __half* dst, int64_t ldd,
                            int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
                            const int64_t* rows_valid, float* inv_scale, const float* sub,
                            const float* coef);
-cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* hi, __half* lo,
-                                int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
-                                float* inv_scale, double* row_sum);
+cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* dst, int64_t ldd,
+                                int64_t rows, int64_t cols, cudaStream_t s, float* inv_scale,
+                                double* row_sum);
 cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
-                                const float* centre, const float* coef, __half* hi1,
-                                __half* lo1, float* isc1, __half* hi2, __half* lo2, float* isc2,
-                                int64_t ldd, int64_t rows, int64_t cols,
-                                const int64_t* rows_valid, uint32_t* colmax, cudaStream_t s);
+                                const float* centre, const float* coef, __half* out1,
+                                float* isc1, __half* out2, float* isc2, int64_t ldd,
+                                int64_t rows, int64_t cols, const int64_t* rows_valid,
+                                uint32_t* colmax, cudaStream_t s);
 cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
-                                int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
-                                cudaStream_t s, const float* centre, uint32_t* amax_bits,
-                                float* inv_scale, bool have_max);
+                                int64_t rows_pad, __half* dst, int64_t ldd, cudaStream_t s,
+                                const float* centre, uint32_t* amax_bits, float* inv_scale,
+                                bool have_max);
 
 // Centre of the Y GEMM operand: the stationary means m_j = n_j / (beta T) of S_j, and the
 // exact products alpha . m in FP64.  (The Z operand S - beta G has stationary mean 0.)
@@ -625,7 +625,7 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     prof_mark(s, "centres");
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int64_t* nb_dev = p.chunk_base + p.B;   // number of chunks, on the device
-    if ((err = split_f16_rows(p.alpha, M, p.al_h, p.al_l, p.ldk, M, M, s, nullptr, nullptr,
+    if ((err = split_f16_rows(p.alpha, M, p.al_p, p.ldk, M, M, s, nullptr, nullptr,
                               p.isc_al, nullptr, nullptr)) != cudaSuccess)
         return err;
     ++*nl;
@@ -633,21 +633,20 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     // S^ - m for Y and, with the gradient, S^ - beta G^ for Z (see below) in one pass over S^
     if (p.grad) {
         // (and the column maxima of S^ - m for the transposed split of the dalpha GEMM)
-        if ((err = split_f16_rows_pair(p.Shat, p.Ghat, M, p.cen_S, p.beta, p.S_h, p.S_l, p.isc_S,
-                                       p.G_h, p.G_l, p.isc_G, p.ldk, nb, M, nb_dev, p.colmax,
-                                       s)) !=
+        if ((err = split_f16_rows_pair(p.Shat, p.Ghat, M, p.cen_S, p.beta, p.S_p, p.isc_S,
+                                       p.G_p, p.isc_G, p.ldk, nb, M, nb_dev, p.colmax, s)) !=
             cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "split_S_G");
     } else {
-        if ((err = split_f16_rows(p.Shat, M, p.S_h, p.S_l, p.ldk, nb, M, s, p.cen_S, nb_dev,
+        if ((err = split_f16_rows(p.Shat, M, p.S_p, p.ldk, nb, M, s, p.cen_S, nb_dev,
                                   p.isc_S, nullptr, nullptr)) != cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "split_S");
     }
-    if ((err = tc_gemm_f16x3(p.S_h, p.S_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Y, M, (int)nb,
+    if ((err = tc_gemm_f16x3(p.S_p, p.ldk, p.al_p, p.ldk, p.Y, M, (int)nb,
                              (int)M, M, 1, false, p.hdr, s, p.bias_Y, p.isc_S, p.isc_al)) !=
         cudaSuccess)
         return err;
@@ -658,7 +657,7 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
         // e (Z - beta delta Y) + (A - beta B), so the near-cancelling difference of the
         // forward state and its beta-derivative is formed once per chunk and element from
         // the scan's states (split above), before any rounding of the tensor-core product
-        if ((err = tc_gemm_f16x3(p.G_h, p.G_l, p.ldk, p.al_h, p.al_l, p.ldk, p.Z, M, (int)nb,
+        if ((err = tc_gemm_f16x3(p.G_p, p.ldk, p.al_p, p.ldk, p.Z, M, (int)nb,
                                  (int)M, M, 1, false, p.hdr, s, nullptr, p.isc_G, p.isc_al)) !=
             cudaSuccess)
             return err;
@@ -778,12 +777,12 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
         // dalpha_gemm[i][j] = sum_b W[b][i] S^[b][j] with the chunk index as the contiguous
         // K dimension: W is already transposed (columns past the chunk count are 0), S^ is
         // transposed here
-        if ((err = split_f16_long_rows(p.W, p.nbp, p.Wt_h, p.Wt_l, p.nbp, M, p.nbp, s, p.isc_Wt,
+        if ((err = split_f16_long_rows(p.W, p.nbp, p.Wt_p, p.ldt, M, p.nbp, s, p.isc_Wt,
                                        p.wsum_acc)) != cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "split_W");
-        if ((err = transpose_split_f16(p.Shat, M, nb_dev, p.nbp, p.St_h, p.St_l, p.nbp, s,
+        if ((err = transpose_split_f16(p.Shat, M, nb_dev, p.nbp, p.St_p, p.ldt, s,
                                        p.cen_S, p.colmax, p.isc_St, true)) != cudaSuccess)
             return err;
         ++*nl;
@@ -800,7 +799,7 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
             const int64_t cost = waves * ((ktiles + sp - 1) / sp + 4);
             if (best < 0 || cost < best) { best = cost; splits = (int)sp; }
         }
-        if ((err = tc_gemm_f16x3(p.Wt_h, p.Wt_l, p.nbp, p.St_h, p.St_l, p.nbp, p.dal_gemm, M,
+        if ((err = tc_gemm_f16x3(p.Wt_p, p.ldt, p.St_p, p.ldt, p.dal_gemm, M,
                                  (int)M, (int)M, p.nbp, splits, true, p.hdr, s, nullptr,
                                  p.isc_Wt, p.isc_St)) != cudaSuccess)
             return err;

@@ -9,12 +9,18 @@
 // maximum in the normal FP16 range, and the scaling and its inverse are exact.  All three
 // products accumulate into FP32 accumulators in tensor memory.
 //
+// Operand layout ("paired" rows): for every group of 32 consecutive k the 32 high parts are
+// followed by the 32 low parts, so element k of a row has its high part at
+// 64 (k / 32) + k % 32 and its low part 32 halves later; a row of K elements takes
+// 64 ceil(K / 32) halves, the positions past K holding zeros.  One 128-byte TMA row
+// (128-byte swizzle) then carries both parts of a k-tile of 32.
+//
 // Used for the two dense contractions of the chunk-GEMM path: alpha . S^_b over
 // all chunk-start states, and the dalpha contraction W^T S^ over all chunks.
 //
 // One CTA computes one 128 x 256 output tile over a slice of K (split-K with
 // atomic accumulation when there is more than one slice).  One thread issues the TMA
-// loads (cp.async.bulk.tensor, 64-byte swizzle, 32 fp16 of K per row) into a
+// loads (cp.async.bulk.tensor, 128-byte swizzle, one paired k-tile per row) into a
 // four-stage ring and the tcgen05.mma instructions (kind::f16, f32 accumulate,
 // M=128, N=256, K=16); tcgen05.commit arrives on the stage's "empty"
 // mbarrier when the MMAs that read it are done.  The tensor-core accumulator
@@ -37,15 +43,16 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BN = 256;
-constexpr int BK = 32;                  // fp16 elements = 64 bytes = one swizzle row
+constexpr int BK = 32;                  // k per tile: 32 high + 32 low fp16 = 128 bytes per row
+constexpr int ROW_BYTES = 4 * BK;
 constexpr int STAGES = 4;
-constexpr int A_TILE = BM * BK * 2;     // 8 KB
-constexpr int B_TILE = BN * BK * 2;     // 16 KB
+constexpr int A_TILE = BM * ROW_BYTES;  // 16 KB
+constexpr int B_TILE = BN * ROW_BYTES;  // 32 KB
 constexpr int kTilesPerGroup = 2;       // k-tiles accumulated in TMEM before promotion (64 of K)
 // unused bytes between the stages and the barriers, so that no operand descriptor of the
 // last stage can reach the barriers or the end of the allocation
 constexpr int kSlack = 24 * 1024;
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // Ah, Al, Bh, Bl
+constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + kSlack + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t TMEM_COLS = 512;      // two accumulator banks of BN columns
 constexpr uint32_t kSpinLimit = 1u << 26;   // bounded waits (~ seconds)
@@ -91,15 +98,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
-__device__ __forceinline__ uint64_t sw64_desc(const void* tile) {
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+// (tiles 1024-byte aligned, so the base offset is 0).
+__device__ __forceinline__ uint64_t sw128_desc(const void* tile) {
     uint64_t a = smem_u32(tile);
     uint64_t d = 0;
     d |= (a >> 4) & 0x3FFFull;          // start address
     d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
     d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
-    d |= (uint64_t)4 << 61;             // SWIZZLE_64B
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
     return d;
 }
 
@@ -142,7 +150,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 struct Maps {
-    CUtensorMap ah, al, bh, bl;
+    CUtensorMap a, b;
 };
 
 // Threads: warps 0-7 read and promote the accumulator (warp w owns TMEM lanes
@@ -203,11 +211,9 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
             auto load_stage = [&](int s, int kt) {
                 uint8_t* st = smem + s * STAGE_BYTES;
                 mbar_expect_tx(&full[s], STAGE_BYTES);
-                const int kx = kt * BK;
-                tma_load_2d(st, &maps.ah, &full[s], kx, m0);
-                tma_load_2d(st + A_TILE, &maps.al, &full[s], kx, m0);
-                tma_load_2d(st + 2 * A_TILE, &maps.bh, &full[s], kx, n0);
-                tma_load_2d(st + 2 * A_TILE + B_TILE, &maps.bl, &full[s], kx, n0);
+                const int kx = kt * 2 * BK;          // halves: 128-byte aligned
+                tma_load_2d(st, &maps.a, &full[s], kx, m0);
+                tma_load_2d(st + A_TILE, &maps.b, &full[s], kx, n0);
             };
             int inflight[STAGES];
             for (int s2 = 0; s2 < STAGES; ++s2) inflight[s2] = -1;
@@ -219,9 +225,7 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                 inflight[s] = -1;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 uint8_t* st = smem + s * STAGE_BYTES;
-                const uint64_t dah = sw64_desc(st), dal = sw64_desc(st + A_TILE);
-                const uint64_t dbh = sw64_desc(st + 2 * A_TILE);
-                const uint64_t dbl = sw64_desc(st + 2 * A_TILE + B_TILE);
+                const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
                 const int g = i / kTilesPerGroup, bank = g & 1;
                 const bool first_in_group = (i % kTilesPerGroup) == 0;
                 if (first_in_group && g >= 2) {
@@ -232,12 +236,14 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                 const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
-                    // 16 fp16 = 32 bytes along the 64-byte swizzled row
-                    const uint64_t off = (uint64_t)(kk * 32) >> 4;
+                    // 16 fp16 = 32 bytes along the 128-byte swizzled row: the high parts
+                    // at bytes 0-63, the low parts at 64-127
+                    const uint64_t oh = (uint64_t)(kk * 32) >> 4;
+                    const uint64_t ol = (uint64_t)(64 + kk * 32) >> 4;
                     const uint32_t acc0 = (!first_in_group || kk > 0) ? 1u : 0u;
-                    mma_f16(acc_t, dah + off, dbh + off, idesc, acc0);
-                    mma_f16(acc_t, dah + off, dbl + off, idesc, 1u);
-                    mma_f16(acc_t, dal + off, dbh + off, idesc, 1u);
+                    mma_f16(acc_t, da + oh, db + oh, idesc, acc0);
+                    mma_f16(acc_t, da + oh, db + ol, idesc, 1u);
+                    mma_f16(acc_t, da + ol, db + oh, idesc, 1u);
                 }
                 if ((i % kTilesPerGroup) == kTilesPerGroup - 1 || i == KT - 1) mma_commit(&bank_full[bank]);
                 if (!ok) break;
@@ -348,18 +354,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D fp16 tensor [rows][k] with row stride ld (elements), box {32, box_rows}.
-static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t k, int64_t ld,
-                     int box_rows) {
+// 2-D fp16 tensor of paired rows [rows][2 * BK * k_tiles] with row stride ld (halves),
+// box {2 * BK, box_rows} (128 bytes per box row).
+static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t k_tiles,
+                     int64_t ld, int box_rows) {
     auto enc = get_encode();
     if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * BK * k_tiles), (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * BK), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -377,22 +384,77 @@ __device__ __forceinline__ void split_f16(float x, __half& hi, __half& lo) {
     lo = __float2half_rn(x - __half2float(hi));
 }
 
+// Position of the high part of element c in a paired row (the low part is 32 further on).
+__host__ __device__ __forceinline__ int64_t pidx(int64_t c) { return c + (c & ~(int64_t)31); }
+__host__ __device__ __forceinline__ int64_t round32(int64_t c) { return (c + 31) & ~(int64_t)31; }
+
+// Split of four consecutive values: their high parts (h01, h23) and low parts (l01, l23)
+// as pairs of halves.
+struct Split4 {
+    uint32_t h01, h23, l01, l23;
+};
+__device__ __forceinline__ uint32_t pack2(__half a, __half b) {
+    const __half2 v = __halves2half2(a, b);
+    return *(const uint32_t*)&v;
+}
+__device__ __forceinline__ Split4 split4(float4 x) {
+    __half h0, l0, h1, l1, h2, l2, h3, l3;
+    split_f16(x.x, h0, l0);
+    split_f16(x.y, h1, l1);
+    split_f16(x.z, h2, l2);
+    split_f16(x.w, h3, l3);
+    return Split4{pack2(h0, h1), pack2(h2, h3), pack2(l0, l1), pack2(l2, l3)};
+}
+
+// A warp whose lane L holds the split of elements c0 + 4 L + {0, 1, 2, 3} of a paired row
+// (c0 a multiple of 64) stores elements [c0, c0 + 128) as two contiguous 256-byte stores:
+// in store s, lane L writes 8 bytes at byte 8 L of the run, the high (L % 16 < 8) or low
+// parts of elements c0 + 64 s + 32 (L / 16) + 4 (L % 8) + {0..3}, received by shuffles from
+// the lane that split them.  Elements at or past cpad (a multiple of 32) are not stored.
+// Every lane of the warp must call it.
+__device__ __forceinline__ void p128_store(__half* row, int64_t c0, int64_t cpad, int lane,
+                                           const Split4& v) {
+    const bool low = ((lane >> 3) & 1) != 0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int src = 16 * s + 8 * (lane >> 4) + (lane & 7);
+        const uint32_t a = __shfl_sync(0xffffffffu, v.h01, src);
+        const uint32_t b = __shfl_sync(0xffffffffu, v.h23, src);
+        const uint32_t c = __shfl_sync(0xffffffffu, v.l01, src);
+        const uint32_t d = __shfl_sync(0xffffffffu, v.l23, src);
+        const int64_t e = c0 + 64 * s + 32 * (lane >> 4) + 4 * (lane & 7);
+        if (e < cpad) *(uint2*)(row + pidx(e) + (low ? 32 : 0)) = low ? make_uint2(c, d) : make_uint2(a, b);
+    }
+}
+
+// four consecutive values p[c .. c + 3] (0 at or past n); vec: p is 16-byte aligned and
+// c a multiple of 4
+__device__ __forceinline__ float4 load4(const float* __restrict__ p, int64_t c, int64_t n, bool vec) {
+    if (vec && c + 4 <= n) return __ldg((const float4*)(p + c));
+    return make_float4(c < n ? p[c] : 0.f, c + 1 < n ? p[c + 1] : 0.f, c + 2 < n ? p[c + 2] : 0.f,
+                       c + 3 < n ? p[c + 3] : 0.f);
+}
+
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 }  // namespace tc
 
 // D[m][n] (+)= inv_sa[m] inv_sb[n] sum_k A[m][k] B[n][k] over m < Mdim, n < Ndim, k < Kdim;
-// A and B given as fp16 hi/lo pairs of the scaled rows, with row strides lda, ldb
-// (elements, multiples of 8; bases 16-byte aligned), inv_sa / inv_sb the inverse scales.
-cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const __half* Bh,
-                          const __half* Bl, int64_t ldb, float* D, int64_t ldd, int Mdim,
-                          int Ndim, int64_t Kdim, int splits, bool accumulate, WsHeader* hdr,
-                          cudaStream_t s, const float* bias, const float* inv_sa,
-                          const float* inv_sb) {
+// A and B given as paired fp16 hi/lo rows of the scaled matrices (row strides lda, ldb in
+// halves, multiples of 8 and at least 64 ceil(Kdim / 32); bases 16-byte aligned; zeros
+// past Kdim), inv_sa / inv_sb the inverse scales.
+cudaError_t tc_gemm_f16x3(const __half* A, int64_t lda, const __half* B, int64_t ldb, float* D,
+                          int64_t ldd, int Mdim, int Ndim, int64_t Kdim, int splits,
+                          bool accumulate, WsHeader* hdr, cudaStream_t s, const float* bias,
+                          const float* inv_sa, const float* inv_sb) {
     using namespace tc;
     if (Mdim <= 0 || Ndim <= 0 || Kdim <= 0) return cudaSuccess;
-    if ((lda % 8) || (ldb % 8)) return cudaErrorInvalidValue;
+    const int64_t kt_total64 = (Kdim + BK - 1) / BK;
+    if ((lda % 8) || (ldb % 8) || lda < 2 * BK * kt_total64 || ldb < 2 * BK * kt_total64)
+        return cudaErrorInvalidValue;
     Maps maps;
-    if (!make_map(&maps.ah, Ah, Mdim, Kdim, lda, BM) || !make_map(&maps.al, Al, Mdim, Kdim, lda, BM) ||
-        !make_map(&maps.bh, Bh, Ndim, Kdim, ldb, BN) || !make_map(&maps.bl, Bl, Ndim, Kdim, ldb, BN))
+    if (!make_map(&maps.a, A, Mdim, kt_total64, lda, BM) ||
+        !make_map(&maps.b, B, Ndim, kt_total64, ldb, BN))
         return cudaErrorInvalidValue;
     static bool attr_set = false;
     if (!attr_set) {
@@ -402,7 +464,7 @@ cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int kt_total = (int)((Kdim + BK - 1) / BK);
+    const int kt_total = (int)kt_total64;
     if (splits < 1) splits = 1;
     if (splits > kt_total) splits = kt_total;
     const int per = (kt_total + splits - 1) / splits;
@@ -417,10 +479,10 @@ cudaError_t tc_gemm_f16x3(const __half* Ah, const __half* Al, int64_t lda, const
 // One warp per row r < rows of an FP32 matrix [rows][cols] (row stride lds), minus an
 // optional per-column centre and minus an optional (*coef) * sub[r][c] (same layout as
 // src; coef on the device): the row's scale exponent from its largest magnitude, the
-// fp16 hi/lo split of the scaled row into [rows][ldd], and inv_scale[r] = 2^-a.  Rows at
-// or past *rows_valid (when given) are written as zeros.
-__global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __half* hi,
-                                 __half* lo, int64_t ldd, int64_t rows, int64_t cols,
+// paired fp16 hi/lo rows of the scaled row in dst [rows][ldd], and inv_scale[r] = 2^-a.
+// Rows at or past *rows_valid (when given) are written as zeros.
+__global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __half* dst,
+                                 int64_t ldd, int64_t rows, int64_t cols,
                                  const float* __restrict__ centre, const int64_t* rows_valid,
                                  float* inv_scale, const float* __restrict__ sub,
                                  const float* __restrict__ coef) {
@@ -428,6 +490,7 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
     const int64_t nvalid = rows_valid ? *rows_valid : rows;
     const float cf = sub ? *coef : 0.f;
     const int64_t wpb = blockDim.x >> 5;
+    const int64_t cpad = tc::round32(cols);
     for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
         const float* sr = src + r * lds;
         const float* ur = sub ? sub + r * lds : nullptr;
@@ -435,54 +498,47 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
             float v = sr[c] - (centre ? centre[c] : 0.f);
             return ur ? v - cf * ur[c] : v;
         };
-        __half* hr = hi + r * ldd;
-        __half* lr = lo + r * ldd;
-        if (r >= nvalid) {
-            for (int64_t c = lane; c < cols; c += 32) hr[c] = lr[c] = __float2half_rn(0.f);
-            if (lane == 0) inv_scale[r] = 1.f;
-            continue;
-        }
+        __half* dr = dst + r * ldd;
+        const bool valid = r < nvalid;
         float amax = 0.f;
-        for (int64_t c = lane; c < cols; c += 32)
-            amax = fmaxf(amax, fabsf(val(c)));
+        if (valid)
+            for (int64_t c = lane; c < cols; c += 32) amax = fmaxf(amax, fabsf(val(c)));
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         const int a = tc::row_exponent(amax);
         const float sc = ldexpf(1.f, a);
-        // pairs of columns as half2 (ldd is even, so every pair is 4-byte aligned), then
-        // the odd last column
-        const int64_t cp = cols & ~(int64_t)1;
-        for (int64_t c = 2 * lane; c < cp; c += 64) {
-            __half h0, l0, h1, l1;
-            tc::split_f16(val(c) * sc, h0, l0);
-            tc::split_f16(val(c + 1) * sc, h1, l1);
-            *(__half2*)(hr + c) = __halves2half2(h0, h1);
-            *(__half2*)(lr + c) = __halves2half2(l0, l1);
+        // 128 elements per two warp stores (zeros past cols, and for the rows past the valid ones)
+        for (int64_t c0 = 0; c0 < cpad; c0 += 128) {
+            const int64_t c = c0 + 4 * lane;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) {
+                x.x = c < cols ? val(c) * sc : 0.f;
+                x.y = c + 1 < cols ? val(c + 1) * sc : 0.f;
+                x.z = c + 2 < cols ? val(c + 2) * sc : 0.f;
+                x.w = c + 3 < cols ? val(c + 3) * sc : 0.f;
+            }
+            tc::p128_store(dr, c0, cpad, lane, tc::split4(x));
         }
-        if (lane == 0 && cp < cols) {
-            __half h, l;
-            tc::split_f16(val(cp) * sc, h, l);
-            hr[cp] = h;
-            lr[cp] = l;
-        }
-        if (lane == 0) inv_scale[r] = ldexpf(1.f, -a);
+        if (lane == 0) inv_scale[r] = valid ? ldexpf(1.f, -a) : 1.f;
     }
 }
 
 // Two row-scaled splits of one matrix in one pass over it (one warp per row): out1 = src -
 // centre (per column) and out2 = src - (*coef) sub, each with its own row exponent and
-// inverse scale; rows at or past *rows_valid are written as zeros.
+// inverse scale, as paired rows; rows at or past *rows_valid are written as zeros.
 __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float* __restrict__ sub,
                                       int64_t lds, const float* __restrict__ centre,
-                                      const float* __restrict__ coef, __half* hi1, __half* lo1,
-                                      float* isc1, __half* hi2, __half* lo2, float* isc2,
-                                      int64_t ldd, int64_t rows, int64_t cols,
-                                      const int64_t* rows_valid, uint32_t* colmax) {
+                                      const float* __restrict__ coef, __half* out1, float* isc1,
+                                      __half* out2, float* isc2, int64_t ldd, int64_t rows,
+                                      int64_t cols, const int64_t* rows_valid, uint32_t* colmax) {
     extern __shared__ uint32_t cmax_sh[];     // [cols] this block's column maxima of |out1|
     const int lane = threadIdx.x & 31;
     const int64_t nvalid = rows_valid ? *rows_valid : rows;
     const float cf = *coef;
     const int64_t wpb = blockDim.x >> 5;
+    const int64_t cpad = tc::round32(cols);
+    const bool vec = (lds & 3) == 0 && tc::aligned16(src) && tc::aligned16(sub) &&
+                     tc::aligned16(centre);
     if (colmax) {
         for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) cmax_sh[c] = 0u;
         __syncthreads();
@@ -490,20 +546,23 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
     for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
         const float* sr = src + r * lds;
         const float* ur = sub + r * lds;
-        __half *h1 = hi1 + r * ldd, *l1 = lo1 + r * ldd, *h2 = hi2 + r * ldd, *l2 = lo2 + r * ldd;
+        __half *d1 = out1 + r * ldd, *d2 = out2 + r * ldd;
         if (r >= nvalid) {
-            for (int64_t c = lane; c < cols; c += 32)
-                h1[c] = l1[c] = h2[c] = l2[c] = __float2half_rn(0.f);
+            const tc::Split4 z = tc::split4(make_float4(0.f, 0.f, 0.f, 0.f));
+            for (int64_t c0 = 0; c0 < cpad; c0 += 128) {
+                tc::p128_store(d1, c0, cpad, lane, z);
+                tc::p128_store(d2, c0, cpad, lane, z);
+            }
             if (lane == 0) { isc1[r] = 1.f; isc2[r] = 1.f; }
             continue;
         }
         float m1 = 0.f, m2 = 0.f;
         for (int64_t c = lane; c < cols; c += 32) {
             const float v = sr[c];
-            const float d1 = fabsf(v - centre[c]);
-            m1 = fmaxf(m1, d1);
+            const float a1 = fabsf(v - centre[c]);
+            m1 = fmaxf(m1, a1);
             m2 = fmaxf(m2, fabsf(v - cf * ur[c]));
-            if (colmax && d1 > 0.f) atomicMax(&cmax_sh[c], __float_as_uint(d1));
+            if (colmax && a1 > 0.f) atomicMax(&cmax_sh[c], __float_as_uint(a1));
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
@@ -512,27 +571,18 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
         }
         const int a1 = tc::row_exponent(m1), a2 = tc::row_exponent(m2);
         const float sc1 = ldexpf(1.f, a1), sc2 = ldexpf(1.f, a2);
-        const int64_t cp = cols & ~(int64_t)1;
-        for (int64_t c = 2 * lane; c < cp; c += 64) {
-            const float v0 = sr[c], v1 = sr[c + 1];
-            __half x0, y0, x1, y1;
-            tc::split_f16((v0 - centre[c]) * sc1, x0, y0);
-            tc::split_f16((v1 - centre[c + 1]) * sc1, x1, y1);
-            *(__half2*)(h1 + c) = __halves2half2(x0, x1);
-            *(__half2*)(l1 + c) = __halves2half2(y0, y1);
-            tc::split_f16((v0 - cf * ur[c]) * sc2, x0, y0);
-            tc::split_f16((v1 - cf * ur[c + 1]) * sc2, x1, y1);
-            *(__half2*)(h2 + c) = __halves2half2(x0, x1);
-            *(__half2*)(l2 + c) = __halves2half2(y0, y1);
-        }
-        if (lane == 0 && cp < cols) {
-            __half x, y;
-            tc::split_f16((sr[cp] - centre[cp]) * sc1, x, y);
-            h1[cp] = x;
-            l1[cp] = y;
-            tc::split_f16((sr[cp] - cf * ur[cp]) * sc2, x, y);
-            h2[cp] = x;
-            l2[cp] = y;
+        // 128 elements per two warp stores per output (zeros past cols)
+        for (int64_t c0 = 0; c0 < cpad; c0 += 128) {
+            const int64_t c = c0 + 4 * lane;
+            const float4 v = tc::load4(sr, c, cols, vec);
+            const float4 m = tc::load4(centre, c, cols, vec);
+            const float4 u = tc::load4(ur, c, cols, vec);
+            tc::p128_store(d1, c0, cpad, lane,
+                           tc::split4(make_float4((v.x - m.x) * sc1, (v.y - m.y) * sc1,
+                                                  (v.z - m.z) * sc1, (v.w - m.w) * sc1)));
+            tc::p128_store(d2, c0, cpad, lane,
+                           tc::split4(make_float4((v.x - cf * u.x) * sc2, (v.y - cf * u.y) * sc2,
+                                                  (v.z - cf * u.z) * sc2, (v.w - cf * u.w) * sc2)));
         }
         if (lane == 0) {
             isc1[r] = ldexpf(1.f, -a1);
@@ -549,12 +599,13 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
 // colmax (optional, [cols] uint bits, zeroed here): the largest |out1| of every column over
 // the valid rows, for a later transposed split of the same matrix.
 cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
-                                const float* centre, const float* coef, __half* hi1,
-                                __half* lo1, float* isc1, __half* hi2, __half* lo2, float* isc2,
-                                int64_t ldd, int64_t rows, int64_t cols,
-                                const int64_t* rows_valid, uint32_t* colmax, cudaStream_t s) {
+                                const float* centre, const float* coef, __half* out1,
+                                float* isc1, __half* out2, float* isc2, int64_t ldd,
+                                int64_t rows, int64_t cols, const int64_t* rows_valid,
+                                uint32_t* colmax, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
-    if (!src || !sub || !centre || !coef || (ldd & 1)) return cudaErrorInvalidValue;
+    if (!src || !sub || !centre || !coef || (ldd & 1) || ldd < 2 * tc::round32(cols))
+        return cudaErrorInvalidValue;
     const size_t smem = colmax ? sizeof(uint32_t) * (size_t)cols : 0;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     if (colmax) {
@@ -568,25 +619,36 @@ cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
     }
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_split_f16_rows_pair<<<(unsigned)blocks, 256, smem, s>>>(src, sub, lds, centre, coef, hi1,
-                                                              lo1, isc1, hi2, lo2, isc2, ldd, rows,
-                                                              cols, rows_valid, colmax);
+    k_split_f16_rows_pair<<<(unsigned)blocks, 256, smem, s>>>(src, sub, lds, centre, coef, out1,
+                                                              isc1, out2, isc2, ldd, rows, cols,
+                                                              rows_valid, colmax);
     return cudaGetLastError();
 }
 
-// Long rows (cols >> 32): one block per row, two passes over it (the row maximum and, if
-// asked, the FP64 row sum; then the split, mostly from L2), no centre or subtrahend.
-__global__ void __launch_bounds__(256) k_split_f16_long_rows(const float* __restrict__ src,
-                                                             int64_t lds, __half* hi, __half* lo,
-                                                             int64_t ldd, int64_t rows,
-                                                             int64_t cols, float* inv_scale,
-                                                             double* row_sum) {
-    __shared__ float red[8];
-    __shared__ double reds[8];
+// Long rows (cols >> 32): one block per row at a time, two passes over it (the row maximum
+// and, if asked, the FP64 row sum; then the split into a paired row), no centre or
+// subtrahend.  Two blocks per SM, so that the rows being split (2 x 152 at a time) stay in
+// L2 between the passes while they are at most a few hundred KB long.
+constexpr int kLongRowThreads = 512;
+__global__ void __launch_bounds__(kLongRowThreads) k_split_f16_long_rows(
+    const float* __restrict__ src, int64_t lds, __half* dst, int64_t ldd, int64_t rows,
+    int64_t cols, float* inv_scale, double* row_sum) {
+    __shared__ float red[kLongRowThreads / 32];
+    __shared__ double reds[kLongRowThreads / 32];
+    const int64_t cpad = tc::round32(cols);
+    const bool vec = (lds & 3) == 0 && tc::aligned16(src);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
         const float* sr = src + r * lds;
         float amax = 0.f, part = 0.f;         // FP32 partial sums per thread, FP64 across
-        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) {
+        const int64_t c4end = vec ? (cols & ~(int64_t)3) : 0;
+#pragma unroll 4
+        for (int64_t c = 4 * (int64_t)threadIdx.x; c < c4end; c += 4 * (int64_t)blockDim.x) {
+            const float4 v = __ldg((const float4*)(sr + c));
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            part += (v.x + v.y) + (v.z + v.w);
+        }
+        for (int64_t c = c4end + threadIdx.x; c < cols; c += blockDim.x) {
             const float v = sr[c];
             amax = fmaxf(amax, fabsf(v));
             part += v;
@@ -606,48 +668,41 @@ __global__ void __launch_bounds__(256) k_split_f16_long_rows(const float* __rest
         if (row_sum && threadIdx.x == 0) row_sum[r] = sum;
         const int a = tc::row_exponent(amax);
         const float sc = ldexpf(1.f, a);
-        __half* hr = hi + r * ldd;
-        __half* lr = lo + r * ldd;
-        const int64_t cp = cols & ~(int64_t)1;
-        for (int64_t c = 2 * threadIdx.x; c < cp; c += 2 * blockDim.x) {
-            __half h0, l0, h1, l1;
-            tc::split_f16(sr[c] * sc, h0, l0);
-            tc::split_f16(sr[c + 1] * sc, h1, l1);
-            *(__half2*)(hr + c) = __halves2half2(h0, h1);
-            *(__half2*)(lr + c) = __halves2half2(l0, l1);
-        }
-        if (threadIdx.x == 0 && cp < cols) {
-            __half h, l;
-            tc::split_f16(sr[cp] * sc, h, l);
-            hr[cp] = h;
-            lr[cp] = l;
+        __half* dr = dst + r * ldd;
+        // 128 elements per two warp stores (zeros past cols)
+#pragma unroll 4
+        for (int64_t c0 = 128 * (int64_t)warp; c0 < cpad; c0 += 128 * (int64_t)nwarps) {
+            const float4 v = tc::load4(sr, c0 + 4 * lane, cols, vec);
+            tc::p128_store(dr, c0, cpad, lane,
+                           tc::split4(make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc)));
         }
         if (threadIdx.x == 0) inv_scale[r] = ldexpf(1.f, -a);
     }
 }
 
-cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* hi, __half* lo,
-                                int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
-                                float* inv_scale, double* row_sum) {
+cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* dst, int64_t ldd,
+                                int64_t rows, int64_t cols, cudaStream_t s, float* inv_scale,
+                                double* row_sum) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
-    if (ldd & 1) return cudaErrorInvalidValue;
-    const int64_t blocks = rows < 152 * 8 ? rows : 152 * 8;
-    k_split_f16_long_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols,
-                                                           inv_scale, row_sum);
+    if ((ldd & 1) || ldd < 2 * tc::round32(cols)) return cudaErrorInvalidValue;
+    const int64_t blocks = rows < 152 * 2 ? rows : 152 * 2;
+    k_split_f16_long_rows<<<(unsigned)blocks, kLongRowThreads, 0, s>>>(src, lds, dst, ldd, rows,
+                                                                       cols, inv_scale, row_sum);
     return cudaGetLastError();
 }
 
-cudaError_t split_f16_rows(const float* src, int64_t lds, __half* hi, __half* lo, int64_t ldd,
+cudaError_t split_f16_rows(const float* src, int64_t lds, __half* dst, int64_t ldd,
                            int64_t rows, int64_t cols, cudaStream_t s, const float* centre,
                            const int64_t* rows_valid, float* inv_scale, const float* sub,
                            const float* coef) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
-    if ((sub == nullptr) != (coef == nullptr) || (ldd & 1)) return cudaErrorInvalidValue;
+    if ((sub == nullptr) != (coef == nullptr) || (ldd & 1) || ldd < 2 * tc::round32(cols))
+        return cudaErrorInvalidValue;
     if (cols >= 4096 && !centre && !rows_valid && !sub)
-        return split_f16_long_rows(src, lds, hi, lo, ldd, rows, cols, s, inv_scale, nullptr);
+        return split_f16_long_rows(src, lds, dst, ldd, rows, cols, s, inv_scale, nullptr);
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_split_f16_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, centre,
+    k_split_f16_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, centre,
                                                       rows_valid, inv_scale, sub, coef);
     return cudaGetLastError();
 }
@@ -667,14 +722,14 @@ __global__ void k_colmax(const float* __restrict__ src, int64_t cols, const int6
     if (m > 0.f) atomicMax(amax_bits + c, __float_as_uint(m));
 }
 
-// dst[c][r] = split(2^a_c (src[r][c] - centre[c])) for r < rows_pad (zero for
+// dst row c, element r = split(2^a_c (src[r][c] - centre[c])) for r < kpad (zero for
 // r >= *rows_valid), a_c from the column's largest magnitude: transposes a chunk-major
-// [rows][cols] FP32 matrix into cols x rows fp16 hi/lo with chunks contiguous, and
+// [rows][cols] FP32 matrix into cols paired rows with chunks contiguous, and
 // inv_scale[c] = 2^-a_c.  Tiles of 64 rows x 32 columns; each thread stores two adjacent
-// rows as one half2 (rows_pad and ldd are even).
+// rows as one half2 per part (kpad is a multiple of 32, ldd even).
 __global__ void k_transpose_split_f16(const float* __restrict__ src, int64_t cols,
-                                      const int64_t* rows_valid, int64_t rows_pad, __half* hi,
-                                      __half* lo, int64_t ldd, const float* centre,
+                                      const int64_t* rows_valid, int64_t kpad, __half* dst,
+                                      int64_t ldd, const float* centre,
                                       const uint32_t* __restrict__ amax_bits, float* inv_scale) {
     __shared__ float tile[64][33];
     __shared__ float sc[32];
@@ -695,22 +750,26 @@ __global__ void k_transpose_split_f16(const float* __restrict__ src, int64_t col
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int64_t c = c0 + i, r = r0 + 2 * threadIdx.x;
-        if (c < cols && r < rows_pad) {
+        if (c < cols && r < kpad) {
             __half h0, l0, h1, l1;
             tc::split_f16(tile[2 * threadIdx.x][i] * sc[i], h0, l0);
             tc::split_f16(tile[2 * threadIdx.x + 1][i] * sc[i], h1, l1);
-            *(__half2*)(hi + c * ldd + r) = __halves2half2(h0, h1);
-            *(__half2*)(lo + c * ldd + r) = __halves2half2(l0, l1);
+            __half* d = dst + c * ldd + tc::pidx(r);      // r even: one group, 4-byte aligned
+            *(__half2*)d = __halves2half2(h0, h1);
+            *(__half2*)(d + 32) = __halves2half2(l0, l1);
         }
     }
 }
 
 // have_max: amax_bits already holds the column maxima (taken by an earlier pass over src).
+// The paired rows cover rows_pad chunks rounded up to 32 (ldd halves each, at least twice that).
 cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* rows_valid,
-                                int64_t rows_pad, __half* hi, __half* lo, int64_t ldd,
-                                cudaStream_t s, const float* centre, uint32_t* amax_bits,
-                                float* inv_scale, bool have_max) {
+                                int64_t rows_pad, __half* dst, int64_t ldd, cudaStream_t s,
+                                const float* centre, uint32_t* amax_bits, float* inv_scale,
+                                bool have_max) {
     if (cols <= 0 || rows_pad <= 0) return cudaSuccess;
+    const int64_t kpad = tc::round32(rows_pad);
+    if ((ldd & 1) || ldd < 2 * kpad) return cudaErrorInvalidValue;
     const int64_t cb = (cols + 31) / 32;
     if (!have_max) {
         cudaError_t e = cudaMemsetAsync(amax_bits, 0, sizeof(uint32_t) * (size_t)cols, s);
@@ -720,10 +779,9 @@ cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* r
         k_colmax<<<dim3((unsigned)cb, (unsigned)rb), dim3(32, 8), 0, s>>>(src, cols, rows_valid,
                                                                          centre, amax_bits);
     }
-    if ((rows_pad & 1) || (ldd & 1)) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)cb, (unsigned)((rows_pad + 63) / 64));
-    k_transpose_split_f16<<<grid, dim3(32, 8), 0, s>>>(src, cols, rows_valid, rows_pad, hi, lo,
-                                                       ldd, centre, amax_bits, inv_scale);
+    dim3 grid((unsigned)cb, (unsigned)((kpad + 63) / 64));
+    k_transpose_split_f16<<<grid, dim3(32, 8), 0, s>>>(src, cols, rows_valid, kpad, dst, ldd,
+                                                       centre, amax_bits, inv_scale);
     return cudaGetLastError();
 }
 
@@ -731,23 +789,22 @@ cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* r
 
 // Test hook (declared in no public header): the same GEMM on caller buffers, so a GPU
 // test can compare it with a reference product.  D[m][n] = sum_k A[m][k] B[n][k] from
-// FP32 A [M][K] and B [N][K]; scratch must hold 2*(M+N)*ld halves (ld = K rounded up to
-// 8) followed by M+N floats.  Returns 0 on success.
+// FP32 A [M][K] and B [N][K]; scratch must hold (M+N)*ld halves (ld = 64 ceil(K / 32))
+// followed by M+N floats.  Returns 0 on success.
 extern "C" int hawkes_test_tc_gemm(const float* A, const float* B, float* D, int M, int N,
                                    int K, int splits, void* scratch, void* stream) {
     using namespace hk;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t ld = (K + 7) / 8 * 8;
-    __half* p = (__half*)scratch;
-    __half *Ah = p, *Al = Ah + (int64_t)M * ld, *Bh = Al + (int64_t)M * ld,
-           *Bl = Bh + (int64_t)N * ld;
-    float* inv_a = (float*)(Bl + (int64_t)N * ld);
+    const int64_t ld = 2 * tc::round32(K);
+    __half* Ap = (__half*)scratch;
+    __half* Bp = Ap + (int64_t)M * ld;
+    float* inv_a = (float*)(Bp + (int64_t)N * ld);
     float* inv_b = inv_a + M;
-    if (split_f16_rows(A, K, Ah, Al, ld, M, K, s, nullptr, nullptr, inv_a, nullptr, nullptr) != cudaSuccess) return 1;
-    if (split_f16_rows(B, K, Bh, Bl, ld, N, K, s, nullptr, nullptr, inv_b, nullptr, nullptr) != cudaSuccess) return 1;
+    if (split_f16_rows(A, K, Ap, ld, M, K, s, nullptr, nullptr, inv_a, nullptr, nullptr) != cudaSuccess) return 1;
+    if (split_f16_rows(B, K, Bp, ld, N, K, s, nullptr, nullptr, inv_b, nullptr, nullptr) != cudaSuccess) return 1;
     if (splits > 1) cudaMemsetAsync(D, 0, sizeof(float) * (size_t)M * N, s);
-    return tc_gemm_f16x3(Ah, Al, ld, Bh, Bl, ld, D, N, M, N, K, splits, false, nullptr, s,
-                         nullptr, inv_a, inv_b) == cudaSuccess
+    return tc_gemm_f16x3(Ap, ld, Bp, ld, D, N, M, N, K, splits, false, nullptr, s, nullptr, inv_a,
+                         inv_b) == cudaSuccess
                ? 0
                : 2;
 }

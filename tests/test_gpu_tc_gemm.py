@@ -24,7 +24,8 @@ def lib():
 
 @pytest.mark.parametrize("M,N,K,splits,signed", [
     (128, 256, 64, 1, False), (128, 256, 1024, 1, False), (300, 520, 1000, 1, True),
-    (1024, 1024, 4096, 4, False), (96, 40, 200, 3, True), (1024, 2048, 1024, 1, False)])
+    (1024, 1024, 4096, 4, False), (96, 40, 200, 3, True), (1024, 2048, 1024, 1, False),
+    (130, 70, 77, 2, True)])
 def test_tc_gemm_matches_fp64(lib, M, N, K, splits, signed):
     import torch
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
@@ -33,8 +34,8 @@ def test_tc_gemm_matches_fp64(lib, M, N, K, splits, signed):
     B = (torch.rand(N, K, device="cuda", generator=g) * (1 - lo) + lo).float()
     A[0, :3] = torch.tensor([1e-6, 3.0e4, -2.5 if signed else 2.5], device="cuda")
     D = torch.full((M, N), float("nan"), device="cuda")
-    ld = (K + 7) // 8 * 8
-    scratch = torch.empty(2 * (M + N) * ld * 2 + 4 * (M + N), dtype=torch.uint8, device="cuda")
+    ld = (K + 31) // 32 * 64                # halves per paired hi/lo row
+    scratch = torch.empty((M + N) * ld * 2 + 4 * (M + N), dtype=torch.uint8, device="cuda")
     rc = lib.hawkes_test_tc_gemm(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, splits,
                                  scratch.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert rc == 0
