@@ -53,7 +53,8 @@ constexpr int kTilesPerGroup = 2;       // k-tiles accumulated in TMEM before pr
 // last stage can reach the barriers or the end of the allocation
 constexpr int kSlack = 24 * 1024;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + kSlack + 1024 /*align*/ + 256 /*barriers*/;
+// then the barriers (256 B) and the tile's column factors (inverse scale, bias: 2 x BN floats)
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + kSlack + 1024 /*align*/ + 256 + 2 * BN * 4;
 constexpr uint32_t TMEM_COLS = 512;      // two accumulator banks of BN columns
 constexpr uint32_t kSpinLimit = 1u << 26;   // bounded waits (~ seconds)
 
@@ -86,6 +87,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t i = 0; i < kSpinLimit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bounded wait that also gives up as soon as *abort is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   volatile int* abort) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
     return false;
 }
 
@@ -155,9 +166,12 @@ struct Maps {
 
 // Threads: warps 0-7 read and promote the accumulator (warp w owns TMEM lanes
 // 32 (w % 4) .. +31 = rows, and columns (w / 4) * 128 .. +127); warp 8 allocates the
-// tensor memory and one of its threads issues the TMA loads and the MMAs.
+// tensor memory and one of its threads issues the MMAs; one thread of warp 9 issues the
+// TMA loads, refilling each stage as soon as the MMAs that read it are done, so that the
+// MMA thread never waits for a refill and can queue MMAs up to the ring's depth ahead.
 constexpr int kEpiWarps = 8;
-constexpr int kThreads = (kEpiWarps + 1) * 32;
+constexpr int kMmaWarp = kEpiWarps, kTmaWarp = kEpiWarps + 1;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim, int Ndim,
@@ -172,6 +186,8 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
     uint64_t* done = bank_empty + 2;          // every MMA of this block has completed
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    float* col_scale = (float*)(smem + STAGES * STAGE_BYTES + kSlack + 256);   // [BN]
+    float* col_bias = col_scale + BN;                                         // [BN]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -194,7 +210,12 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kEpiWarps) {
+    if (threadIdx.x < BN) {
+        const int col = n0 + threadIdx.x;
+        col_scale[threadIdx.x] = col < Ndim ? __ldg(inv_sb + col) : 0.f;
+        col_bias[threadIdx.x] = (bias && blockIdx.z == 0 && col < Ndim) ? __ldg(bias + col) : 0.f;
+    }
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(TMEM_COLS));
@@ -205,24 +226,16 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == kEpiWarps) {
+    if (warp == kMmaWarp) {
         if (lane == 0 && KT > 0) {
             const uint32_t idesc = idesc_f16(BM, BN);
-            auto load_stage = [&](int s, int kt) {
-                uint8_t* st = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                const int kx = kt * 2 * BK;          // halves: 128-byte aligned
-                tma_load_2d(st, &maps.a, &full[s], kx, m0);
-                tma_load_2d(st + A_TILE, &maps.b, &full[s], kx, n0);
-            };
-            int inflight[STAGES];
-            for (int s2 = 0; s2 < STAGES; ++s2) inflight[s2] = -1;
-            for (int i = 0; i < STAGES && i < KT; ++i) { load_stage(i, kt0 + i); inflight[i] = i; }
             bool ok = true;
-            for (int i = 0; i < KT && ok; ++i) {
+            for (int i = 0; i < KT; ++i) {
                 const int s = i % STAGES;
-                if (!mbar_wait(&full[s], (uint32_t)((i / STAGES) & 1))) { ok = false; break; }
-                inflight[s] = -1;
+                if (!mbar_wait_or_abort(&full[s], (uint32_t)((i / STAGES) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 uint8_t* st = smem + s * STAGE_BYTES;
                 const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
@@ -230,7 +243,10 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                 const bool first_in_group = (i % kTilesPerGroup) == 0;
                 if (first_in_group && g >= 2) {
                     // the epilogue must have read this bank's previous group
-                    if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) { ok = false; break; }
+                    if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
                 const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
@@ -246,22 +262,9 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                     mma_f16(acc_t, da + ol, db + oh, idesc, 1u);
                 }
                 if ((i % kTilesPerGroup) == kTilesPerGroup - 1 || i == KT - 1) mma_commit(&bank_full[bank]);
-                if (!ok) break;
-                mma_commit(&empty[s]);
-                // refill the stage the previous k-tile used once its MMAs are done
-                if (i >= 1) {
-                    const int ps = (i - 1) % STAGES;
-                    const int nxt = i - 1 + STAGES;
-                    if (nxt < KT) {
-                        if (!mbar_wait(&empty[ps], (uint32_t)(((i - 1) / STAGES) & 1))) { ok = false; break; }
-                        load_stage(ps, kt0 + nxt);
-                        inflight[ps] = nxt;
-                    }
-                }
+                mma_commit(&empty[s]);           // the stage may be refilled once these are done
             }
             if (!ok) {
-                for (int s2 = 0; s2 < STAGES; ++s2)
-                    if (inflight[s2] >= 0) mbar_wait(&full[s2], (uint32_t)((inflight[s2] / STAGES) & 1));
                 *abort_flag = 1;
                 if (hdr) set_status(hdr, HAWKES_ERR_CUDA);
                 // release the epilogue warps waiting on the banks
@@ -271,6 +274,32 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
             // no MMA may still be writing tensor memory when it is freed
             mma_commit(done);
             mbar_wait(done, 0);
+        }
+    } else if (warp == kTmaWarp) {
+        if (lane == 0 && KT > 0) {
+            int last[STAGES];                    // the last k-tile loaded into each stage
+            for (int s2 = 0; s2 < STAGES; ++s2) last[s2] = -1;
+            for (int i = 0; i < KT; ++i) {
+                const int s = i % STAGES;
+                if (i >= STAGES &&
+                    !mbar_wait_or_abort(&empty[s], (uint32_t)(((i / STAGES) - 1) & 1), abort_flag)) {
+                    if (!*abort_flag) {
+                        *abort_flag = 1;
+                        if (hdr) set_status(hdr, HAWKES_ERR_CUDA);
+                    }
+                    break;
+                }
+                if (*abort_flag) break;
+                uint8_t* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                const int kx = (kt0 + i) * 2 * BK;   // halves: 128-byte aligned
+                tma_load_2d(st, &maps.a, &full[s], kx, m0);
+                tma_load_2d(st + A_TILE, &maps.b, &full[s], kx, n0);
+                last[s] = i;
+            }
+            // no copy may still be writing shared memory when the block exits
+            for (int s2 = 0; s2 < STAGES; ++s2)
+                if (last[s2] >= 0) mbar_wait(&full[s2], (uint32_t)((last[s2] / STAGES) & 1));
         }
     } else if (KT > 0) {
         // epilogue warps: promote each group's partial sum into FP32 registers
@@ -301,31 +330,28 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
         }
         if (!good && lane == 0 && hdr) set_status(hdr, HAWKES_ERR_CUDA);
         const int row = m0 + lane_base + lane;
-        // undo the row scalings (exact powers of two), then add the bias
+        // undo the row scalings (exact powers of two), add the bias, store; four columns at
+        // a time
         const float fa = row < Mdim ? __ldg(inv_sa + row) : 0.f;
+        const bool store = good && row < Mdim;
+        float* drow = D + (int64_t)row * ldd + n0 + col_base;
+        const bool vec = !atomic_out && (ldd & 3) == 0 && n0 + col_base + 128 <= Ndim &&
+                         ((uintptr_t)drow & 15) == 0;
 #pragma unroll
-        for (int j = 0; j < 128; ++j) {
-            const int col = n0 + col_base + j;
-            run[j] *= fa * (col < Ndim ? __ldg(inv_sb + col) : 0.f);
-        }
-        if (bias && blockIdx.z == 0) {
+        for (int j = 0; j < 128; j += 4) {
+            float o[4];
 #pragma unroll
-            for (int j = 0; j < 128; ++j)
-                run[j] += (n0 + col_base + j < Ndim) ? __ldg(bias + n0 + col_base + j) : 0.f;
-        }
-        if (good && row < Mdim) {
-            float* drow = D + (int64_t)row * ldd + n0 + col_base;
-            if (!atomic_out && (ldd & 3) == 0 && n0 + col_base + 128 <= Ndim &&
-                ((uintptr_t)drow & 15) == 0) {
-#pragma unroll
-                for (int j = 0; j < 128; j += 4)
-                    *(float4*)(drow + j) = make_float4(run[j], run[j + 1], run[j + 2], run[j + 3]);
+            for (int q = 0; q < 4; ++q)
+                o[q] = run[j + q] * (fa * col_scale[col_base + j + q]) + col_bias[col_base + j + q];
+            if (!store) continue;
+            if (vec) {
+                *(float4*)(drow + j) = make_float4(o[0], o[1], o[2], o[3]);
             } else {
 #pragma unroll
-                for (int j = 0; j < 128; ++j) {
-                    if (n0 + col_base + j < Ndim) {
-                        if (atomic_out) atomicAdd(drow + j, run[j]);
-                        else drow[j] = run[j];
+                for (int q = 0; q < 4; ++q) {
+                    if (n0 + col_base + j + q < Ndim) {
+                        if (atomic_out) atomicAdd(drow + j + q, o[q]);
+                        else drow[j + q] = o[q];
                     }
                 }
             }
@@ -333,7 +359,7 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == kEpiWarps)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
 }
