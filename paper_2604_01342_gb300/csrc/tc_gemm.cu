@@ -55,6 +55,10 @@ constexpr int kSlack = 24 * 1024;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
 // then the barriers (256 B) and the tile's column factors (inverse scale, bias: 2 x BN floats)
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + kSlack + 1024 /*align*/ + 256 + 2 * BN * 4;
+// row stride (floats) of the output tile staged in the stage buffers: 16 bytes of padding
+// per row, so that the rows' float4 writes (one row per lane) fall in distinct banks
+constexpr int kOutLd = BN + 4;
+static_assert(BM * kOutLd * 4 <= STAGES * STAGE_BYTES, "the output tile fits the stages");
 constexpr uint32_t TMEM_COLS = 512;      // two accumulator banks of BN columns
 constexpr uint32_t kSpinLimit = 1u << 26;   // bounded waits (~ seconds)
 
@@ -329,29 +333,50 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
                                         : "memory");
         }
         if (!good && lane == 0 && hdr) set_status(hdr, HAWKES_ERR_CUDA);
-        const int row = m0 + lane_base + lane;
-        // undo the row scalings (exact powers of two), add the bias, store; four columns at
-        // a time
+        // Output: undo the row scalings (exact powers of two) and add the bias into a row-major
+        // copy of the tile in the stage buffers (free now: the last group's commit means every
+        // load was consumed and every MMA has completed), then store whole row pieces: with
+        // one row per thread, direct stores would be 32 separate 16-byte pieces per warp
+        // instruction.
+        const int rloc = lane_base + lane;
+        const int row = m0 + rloc;
         const float fa = row < Mdim ? __ldg(inv_sa + row) : 0.f;
-        const bool store = good && row < Mdim;
-        float* drow = D + (int64_t)row * ldd + n0 + col_base;
-        const bool vec = !atomic_out && (ldd & 3) == 0 && n0 + col_base + 128 <= Ndim &&
-                         ((uintptr_t)drow & 15) == 0;
+        float* otile = (float*)smem;                       // [BM][kOutLd]
+        if (good) {
+            float* orow = otile + rloc * kOutLd + col_base;
 #pragma unroll
-        for (int j = 0; j < 128; j += 4) {
-            float o[4];
+            for (int j = 0; j < 128; j += 4) {
+                float4 o;
+                o.x = run[j] * (fa * col_scale[col_base + j]) + col_bias[col_base + j];
+                o.y = run[j + 1] * (fa * col_scale[col_base + j + 1]) + col_bias[col_base + j + 1];
+                o.z = run[j + 2] * (fa * col_scale[col_base + j + 2]) + col_bias[col_base + j + 2];
+                o.w = run[j + 3] * (fa * col_scale[col_base + j + 3]) + col_bias[col_base + j + 3];
+                *(float4*)(orow + j) = o;
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");   // epilogue warps only
+        if (good) {
+            const bool vec = (ldd & 3) == 0 && ((uintptr_t)D & 15) == 0;
+            // warp w stores rows w, w + 8, ...: 256 columns as two 512-byte pieces per row
+            for (int rr = warp; rr < BM && m0 + rr < Mdim; rr += kEpiWarps) {
+                float* drow = D + (int64_t)(m0 + rr) * ldd + n0;
+                const float* srow = otile + rr * kOutLd;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                o[q] = run[j + q] * (fa * col_scale[col_base + j + q]) + col_bias[col_base + j + q];
-            if (!store) continue;
-            if (vec) {
-                *(float4*)(drow + j) = make_float4(o[0], o[1], o[2], o[3]);
-            } else {
+                for (int h = 0; h < 2; ++h) {
+                    const int c = 128 * h + 4 * lane;
+                    const float4 v = *(const float4*)(srow + c);
+                    if (vec && n0 + c + 4 <= Ndim) {
+                        if (atomic_out) atomicAdd((float4*)(drow + c), v);
+                        else *(float4*)(drow + c) = v;
+                    } else {
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (n0 + col_base + j + q < Ndim) {
-                        if (atomic_out) atomicAdd(drow + j + q, o[q]);
-                        else drow[j + q] = o[q];
+                        for (int q = 0; q < 4; ++q) {
+                            if (n0 + c + q < Ndim) {
+                                if (atomic_out) atomicAdd(drow + c + q, vv[q]);
+                                else drow[c + q] = vv[q];
+                            }
+                        }
                     }
                 }
             }
