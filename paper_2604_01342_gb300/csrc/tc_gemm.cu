@@ -21,15 +21,17 @@
 // One CTA computes one 128 x 256 output tile over a slice of K (split-K with
 // atomic accumulation when there is more than one slice).  One thread issues the TMA
 // loads (cp.async.bulk.tensor, 128-byte swizzle, one paired k-tile per row) into a
-// four-stage ring and the tcgen05.mma instructions (kind::f16, f32 accumulate,
-// M=128, N=256, K=16); tcgen05.commit arrives on the stage's "empty"
-// mbarrier when the MMAs that read it are done.  The tensor-core accumulator
-// loses precision with the number of accumulation steps (measured with TF32 operands:
-// ~1.6e-6 after 64 of K, ~2.6e-5 after 1024), so every 64 of K (two k-tiles) is
-// accumulated into one of two TMEM banks and then promoted: eight warps read the finished
-// bank with tcgen05.ld and add it to FP32 registers while the MMAs fill the other bank.  Every mbarrier wait is
-// bounded; on timeout the kernel records an error in the status word, waits (bounded) for
-// its MMAs, frees its tensor memory and returns.
+// four-stage ring; a thread of another warp issues the tcgen05.mma instructions
+// (kind::f16, f32 accumulate, M=128, N=256, K=16); tcgen05.commit arrives on the stage's
+// "empty" mbarrier when the MMAs that read it are done, and the loading thread refills it.
+// The tensor-core accumulator loses precision with the number of accumulation steps
+// (measured with TF32 operands: ~1.6e-6 after 64 of K, ~2.6e-5 after 1024), so every 64 of
+// K (two k-tiles) is accumulated into one of two TMEM banks and then promoted: eight warps
+// read the finished bank with tcgen05.ld and add it to FP32 registers while the MMAs fill
+// the other bank.  The output tile is staged in the (then free) stage buffers and stored as
+// whole row pieces.  Every mbarrier wait is bounded; on timeout the kernel records an error
+// in the status word, waits (bounded) for its MMAs and copies, frees its tensor memory and
+// returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
