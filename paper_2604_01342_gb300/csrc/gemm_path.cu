@@ -126,26 +126,35 @@ __global__ void k_alpha_tiles(Problem p, float* at) {
 // of the mark in its block, index in the chunk) in recs; the same buckets in index order in
 // lrec (source side of the backward pairs), and the membership bits of every bucket over
 // the chunk's event indices in bmask, each 32-bit word with the number of members in the
-// words before it.
-__host__ __device__ inline int bucket_ints_per_warp(int P, int C) {
-    return 2 * P + 1 + C + P * ((C + 31) >> 5);
+// words before it.  The sorted order comes from counts: per (block, position) - one mark -
+// the number of the chunk's events, an exclusive scan of those counts in (block, position)
+// order (the first slot of every mark), and the events taking their slots in index order
+// (the lanes of one mark in one 32-event step ordered by lane).
+// the per-mark counts are stored with one padding word after every 32, so that the
+// lanes' contiguous runs of the scan fall in distinct banks
+__host__ __device__ inline int bucket_pad(int e) { return e + (e >> 5); }
+__host__ __device__ inline int bucket_ints_per_warp(int P, int C, int M) {
+    const int TR = (M + P - 1) / P;
+    return 2 * P + 1 + bucket_pad(P * TR) + 1 + P * ((C + 31) >> 5);
 }
 // shared memory of k_bucket: each warp's scratch, then the mark -> (block, position) table
 __host__ __device__ inline size_t bucket_smem_bytes(int P, int C, int M, int warps) {
-    return sizeof(int32_t) * ((size_t)warps * bucket_ints_per_warp(P, C) + (size_t)M);
+    return sizeof(int32_t) * ((size_t)warps * bucket_ints_per_warp(P, C, M) + (size_t)M);
 }
 
 __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2* lrec,
                                                 uint2* bmask, int32_t* bstart, uint8_t* wide) {
     extern __shared__ int32_t sm_i[];
     const int P = p.P, C = p.C, W = (C + 31) >> 5;
+    const int TR = (p.M + P - 1) / P, PT = P * TR;
     const int lane = threadIdx.x & 31;
-    int32_t* cnt = sm_i + (threadIdx.x >> 5) * bucket_ints_per_warp(P, C);   // [P]
+    int32_t* cnt = sm_i + (threadIdx.x >> 5) * bucket_ints_per_warp(P, C, p.M);   // [P]
     int32_t* base = cnt + P;              // [P+1]
-    int32_t* ukey = base + P + 1;         // [C] keys in unordered bucket slots
-    uint32_t* msk = (uint32_t*)(ukey + C);   // [P * W] membership bits
+    int32_t* slot = base + P + 1;         // [P * TR] per (block, position), padded: count, then next slot
+    const int PTP = bucket_pad(PT) + 1;
+    uint32_t* msk = (uint32_t*)(slot + PTP);  // [P * W] membership bits
     // mark c -> (position c / P) << 16 | (block c mod P), so that no event divides by P
-    int32_t* qtab = sm_i + (blockDim.x >> 5) * bucket_ints_per_warp(P, C);
+    int32_t* qtab = sm_i + (blockDim.x >> 5) * bucket_ints_per_warp(P, C, p.M);
     if (failed(p.hdr)) return;
     for (int c = threadIdx.x; c < p.M; c += blockDim.x) qtab[c] = ((c / P) << 16) | (c % P);
     __syncthreads();
@@ -158,10 +167,13 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
         const int n = (int)(s1 - s0);
         for (int q = lane; q < P; q += 32) cnt[q] = 0;
         for (int q = lane; q < P * W; q += 32) msk[q] = 0u;
+        for (int e = lane; e < PTP; e += 32) slot[e] = 0;
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
-            const int q = qtab[__ldg(p.c + s0 + i)] & 0xffff;
+            const int qp = qtab[__ldg(p.c + s0 + i)];
+            const int q = qp & 0xffff;
             atomicAdd(&cnt[q], 1);
+            atomicAdd(&slot[bucket_pad(q * TR + (qp >> 16))], 1);
             atomicOr(&msk[q * W + (i >> 5)], 1u << (i & 31));
         }
         __syncwarp();
@@ -171,10 +183,29 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
                 base[q] = acc;
                 bstart[b * (P + 1) + q] = acc;
                 acc += cnt[q];
-                cnt[q] = 0;
             }
             base[P] = acc;
             bstart[b * (P + 1) + P] = acc;
+        }
+        {
+            // exclusive scan of the per-mark counts in (block, position) order: each lane sums
+            // a contiguous run, the warp scans the run sums, each lane writes its run's prefixes
+            const int per = (PT + 31) >> 5;
+            const int e0 = min(lane * per, PT), e1 = min(e0 + per, PT);
+            int sum = 0;
+            for (int e = e0; e < e1; ++e) sum += slot[bucket_pad(e)];
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(HK_FULL, incl, o);
+                if (lane >= o) incl += x;
+            }
+            int run = incl - sum;
+            for (int e = e0; e < e1; ++e) {
+                const int v = slot[bucket_pad(e)];
+                slot[bucket_pad(e)] = run;
+                run += v;
+            }
         }
         __syncwarp();
         for (int e = lane; e < P * W; e += 32) {
@@ -182,28 +213,30 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             for (int w = e - e % W; w < e; ++w) before += __popc(msk[w]);
             bmask[b * P * W + e] = make_uint2(msk[e], (uint32_t)before);
         }
-        // unordered placement of the sort keys (position << 16 | index)
-        for (int i = lane; i < n; i += 32) {
-            const int qp = qtab[__ldg(p.c + s0 + i)];
-            const int q = qp & 0xffff;
-            ukey[base[q] + atomicAdd(&cnt[q], 1)] = (qp & 0xffff0000) | i;
-        }
-        __syncwarp();
         const bool isw = n > 0 && beta * (float)(p.t[s1 - 1] - p.t[s0]) > kWideLimit;
-        for (int i = lane; i < n; i += 32) {
-            const int qp = qtab[__ldg(p.c + s0 + i)];
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const bool have = i < n;
+            const int qp = have ? qtab[__ldg(p.c + s0 + i)] : 0;
             const int q = qp & 0xffff, pos = qp >> 16;
-            const int key = (qp & 0xffff0000) | i;
-            int rank = 0;
-            for (int j = base[q]; j < base[q + 1]; ++j) rank += ukey[j] < key;
-            const uint32_t* mq = msk + q * W;
-            int irank = __popc(mq[i >> 5] & ((1u << (i & 31)) - 1u));
-            for (int w = 0; w < (i >> 5); ++w) irank += __popc(mq[w]);
-            const float d = p.delta[s0 + i];
-            const float em = exp_unbiased(-beta * d);
-            const float ep = isw ? 0.f : exp_unbiased(beta * d);
-            recs[s0 + base[q] + rank] = make_float4(d, em, ep, __int_as_float((i << 16) | pos));
-            lrec[s0 + base[q] + irank] = make_float2(ep, __int_as_float(pos));
+            // the lanes of one mark take consecutive slots in lane (= index) order
+            const int key = have ? q * TR + pos : -1 - lane;
+            const uint32_t peers = __match_any_sync(HK_FULL, key);
+            const int leader = __ffs(peers) - 1;
+            int first = 0;
+            if (have && lane == leader) first = atomicAdd(&slot[bucket_pad(key)], __popc(peers));
+            first = __shfl_sync(HK_FULL, first, leader);
+            if (have) {
+                const int at = first + __popc(peers & ((1u << lane) - 1u));   // from the chunk's start
+                const uint32_t* mq = msk + q * W;
+                int irank = __popc(mq[i >> 5] & ((1u << (i & 31)) - 1u));
+                for (int w = 0; w < (i >> 5); ++w) irank += __popc(mq[w]);
+                const float d = p.delta[s0 + i];
+                const float em = exp_unbiased(-beta * d);
+                const float ep = isw ? 0.f : exp_unbiased(beta * d);
+                recs[s0 + at] = make_float4(d, em, ep, __int_as_float((i << 16) | pos));
+                lrec[s0 + base[q] + irank] = make_float2(ep, __int_as_float(pos));
+            }
         }
         if (lane == 0) wide[b] = isw ? 1 : 0;
         __syncwarp();
