@@ -208,6 +208,36 @@ hawkes_status hawkes_last_device_status(void* workspace, void* stream);
  * or NULL if that call did not validate.  The pointer is into the workspace. */
 const int64_t* hawkes_mark_counts(void* workspace);
 
+/* Integer tables of the last call on `workspace`, as device pointers into the workspace,
+ * for checking the library's integer work bit by bit (no counterpart in the paper; the
+ * chunks are the contiguous batches of Section 3.3).  N, M, B, grad and opts must be those
+ * of that call; the pointers of tables that its path does not build are NULL.  Nothing is
+ * launched or read back; read the tables after that call has completed.
+ *   mark_counts   [B*M] int64: events of each (sequence, mark); meaningful only when the
+ *                 call validated its inputs (opts->validate = 1)
+ *   chunk_base    [B+1] int64: chunks of the sequences before each sequence; [B] = all chunks
+ *   chunk_seq     [chunks] int32: the sequence that owns each chunk (chunk q of a sequence
+ *                 covers its events [q C, min((q + 1) C, len)))
+ *   bucket_start  [chunks][P+1] int32 (chunk-GEMM path): per chunk, the number of its events
+ *                 whose mark block (mark mod P) is below q, q = 0..P
+ *   bucket_slots  [N][4] uint32 (chunk-GEMM path): the chunk's events ordered by (mark mod P,
+ *                 mark / P, index in the chunk); word 3 of slot r of a chunk starting at event
+ *                 s0 (slot s0 + r) is (index in the chunk << 16) | (mark / P)
+ *   chunk         C, events per chunk;  mark_blocks  P (chunk-GEMM path), else 0.
+ * Returns HAWKES_ERR_INVALID_ARG for a null workspace or output, or the status that
+ * hawkes_workspace_size's configuration check gives. */
+typedef struct {
+    const int64_t* mark_counts;
+    const int64_t* chunk_base;
+    const int32_t* chunk_seq;
+    const int32_t* bucket_start;
+    const uint32_t* bucket_slots;
+    int32_t chunk;
+    int32_t mark_blocks;
+} hawkes_tables;
+hawkes_status hawkes_integer_tables(void* workspace, int64_t N, int32_t M, int32_t B,
+                                    int32_t grad, const hawkes_opts* opts, hawkes_tables* out);
+
 /* Static description of a status code. */
 const char* hawkes_status_str(hawkes_status s);
 

@@ -77,6 +77,10 @@ def _load():
             lib.oracle_loglik_grad_varlen.argtypes = [p, p, p, i32, p, i32, p, p, p, p, p, p, p]
             lib.oracle_mark_counts.argtypes = [i64, p, i32, p]
             lib.oracle_condition.argtypes = [i64, p, p, d, i32, p, p, p, p, p]
+            lib.oracle_chunk_table.argtypes = [i32, p, i32, p, p]
+            lib.oracle_chunk_table.restype = ctypes.c_int
+            lib.oracle_bucket_order.argtypes = [i64, p, i32, i32, i32, p, p]
+            lib.oracle_bucket_order.restype = ctypes.c_int
             lib.oracle_loglik_grad_carry.argtypes = [i64, p, p, d, i32, p, p, p, p, p,
                                                      ctypes.c_int, p, p, p, p, p]
             lib.oracle_loglik_grad_carry.restype = ctypes.c_int
@@ -190,6 +194,34 @@ def mark_counts(c, M):
     if rc:
         raise OracleError(rc)
     return out
+
+
+def chunk_table(offsets, C):
+    """(chunk_base [B+1] int64, chunk_seq [chunks] int32) of sequences cut into chunks of C."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    B = offsets.shape[0] - 1
+    lens = np.diff(offsets)
+    nb = int(sum((int(x) + C - 1) // C for x in lens))
+    base = np.zeros(B + 1, dtype=np.int64)
+    seq = np.zeros(max(nb, 1), dtype=np.int32)
+    rc = _load().oracle_chunk_table(B, _ptr(offsets), int(C), _ptr(base), _ptr(seq))
+    if rc:
+        raise OracleError(rc)
+    return base, seq[:nb]
+
+
+def bucket_order(c, M, C, P):
+    """(bucket_start [chunks, P+1] int32, order [N] int32): per chunk of C events, the
+    events ordered by (mark mod P, mark // P, index), and each block's first slot."""
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    N = c.shape[0]
+    nb = (N + C - 1) // C
+    bs = np.zeros((max(nb, 1), P + 1), dtype=np.int32)
+    order = np.zeros(max(N, 1), dtype=np.int32)
+    rc = _load().oracle_bucket_order(N, _ptr(c), int(M), int(C), int(P), _ptr(bs), _ptr(order))
+    if rc:
+        raise OracleError(rc)
+    return bs[:nb], order[:N]
 
 
 def condition(t, c, T, mu, alpha, beta):

@@ -369,6 +369,60 @@ int oracle_mark_counts(int64_t N, const int32_t* c, int32_t M, int64_t* counts)
     return OR_OK;
 }
 
+/* Integer pass: the chunk table of B sequences cut into chunks of C consecutive
+ * events (paper, Section 3.3: the stream is processed in contiguous batches, each
+ * depending on the earlier ones only through one carried state).  Sequence s owns
+ * events [offsets[s], offsets[s+1]) and ceil(len_s / C) chunks; chunk_base[s] is the
+ * number of chunks of the sequences before s (chunk_base[B] = all chunks) and
+ * chunk_seq[b] the sequence that owns chunk b (chunk_seq holds chunk_base[B] entries;
+ * the caller sizes it from the same formula).  A sequence's chunk q covers its events
+ * [q C, min((q + 1) C, len)). */
+int oracle_chunk_table(int32_t B, const int64_t* offsets, int32_t C, int64_t* chunk_base,
+                       int32_t* chunk_seq)
+{
+    if (B <= 0 || C <= 0 || offsets[0] != 0) return OR_INVALID;
+    int64_t nb = 0;
+    for (int32_t s = 0; s < B; ++s) {
+        int64_t len = offsets[s + 1] - offsets[s];
+        if (len < 0) return OR_INVALID;
+        chunk_base[s] = nb;
+        int64_t n = len / C + (len % C != 0 ? 1 : 0);
+        for (int64_t q = 0; q < n; ++q) chunk_seq[nb + q] = s;
+        nb += n;
+    }
+    chunk_base[B] = nb;
+    return OR_OK;
+}
+
+/* Integer pass of the pair kernels of one sequence: the marks are dealt into P blocks
+ * (block of mark c = c mod P, position c / P), and the events of every chunk of C events
+ * are ordered by (block, position, index in the chunk).  Outputs, per chunk b:
+ *   bucket_start[b (P + 1) + q] = number of the chunk's events whose block is below q
+ *                                 (q = 0..P; the last entry is the chunk's length),
+ *   order[b C + r]              = the index in the chunk of its r-th event in that order.
+ * This is a stable counting sort, written as plain nested loops over the blocks, the
+ * positions in a block and the chunk's events. */
+int oracle_bucket_order(int64_t N, const int32_t* c, int32_t M, int32_t C, int32_t P,
+                        int32_t* bucket_start, int32_t* order)
+{
+    if (N < 0 || M <= 0 || C <= 0 || P <= 0) return OR_INVALID;
+    int64_t nb = N / C + (N % C != 0 ? 1 : 0);
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t s0 = b * C, s1 = s0 + C < N ? s0 + C : N;
+        int32_t* bs = bucket_start + b * (P + 1);
+        int32_t r = 0;
+        for (int32_t q = 0; q < P; ++q) {
+            bs[q] = r;
+            for (int32_t pos = 0; pos * P + q < M; ++pos)          /* marks of block q, by position */
+                for (int64_t k = s0; k < s1; ++k)                  /* their events, by index */
+                    if (c[k] == pos * P + q) order[s0 + r++] = (int32_t)(k - s0);
+        }
+        bs[P] = r;
+        if (r != (int32_t)(s1 - s0)) return OR_MARK;
+    }
+    return OR_OK;
+}
+
 /* Conditioning scales of the results (for stating errors of near-zero results):
  *   scale_ll       = sum_k |log lambda_k| + Lambda(T)
  *   scale_dbeta[j] = sum_k |w_k alpha[c_k][j] (S_{k,j} - beta_j G_{k,j})| + colsum_j F_j

@@ -31,7 +31,7 @@ EXPORTED = (
     "hawkes_loglik_grad_host", "hawkes_last_device_status", "hawkes_mark_counts",
     "hawkes_status_str", "hawkes_last_launch_count", "hawkes_profile_enable",
     "hawkes_profile_read", "hawkes_static_scratch_bytes", "hawkes_loglik_grad_static",
-    "hawkes_slice_aggregate", "hawkes_loglik_grad_slice",
+    "hawkes_slice_aggregate", "hawkes_loglik_grad_slice", "hawkes_integer_tables",
 )
 
 
@@ -39,6 +39,13 @@ class HawkesOpts(ctypes.Structure):
     _fields_ = [("beta_shared", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("kernels", ctypes.c_int32)]
+
+
+class HawkesTables(ctypes.Structure):
+    _fields_ = [("mark_counts", ctypes.c_void_p), ("chunk_base", ctypes.c_void_p),
+                ("chunk_seq", ctypes.c_void_p), ("bucket_start", ctypes.c_void_p),
+                ("bucket_slots", ctypes.c_void_p), ("chunk", ctypes.c_int32),
+                ("mark_blocks", ctypes.c_int32)]
 
 
 class HawkesError(RuntimeError):
@@ -97,7 +104,9 @@ def lib():
         L.hawkes_static_scratch_bytes.argtypes = []
         L.hawkes_static_scratch_bytes.restype = sz
         L.hawkes_loglik_grad_static.argtypes = [p, p, i64, d, i32, p, p, p, op, p, p, p, p, p]
-        for name in ("hawkes_slice_aggregate", "hawkes_loglik_grad_slice",
+        L.hawkes_integer_tables.argtypes = [p, i64, i32, i32, i32, op,
+                                            ctypes.POINTER(HawkesTables)]
+        for name in ("hawkes_integer_tables", "hawkes_slice_aggregate", "hawkes_loglik_grad_slice",
                      "hawkes_loglik_grad_static", "hawkes_loglik", "hawkes_loglik_grad",
                      "hawkes_loglik_varlen",
                      "hawkes_loglik_grad_varlen", "hawkes_loglik_grad_host",
@@ -197,6 +206,15 @@ def hawkes_profile_read(cap: int = 64):
     if n < 0:
         raise HawkesError(-n, "hawkes_profile_read")
     return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def hawkes_integer_tables(ws, N, M, B, grad, opts) -> HawkesTables:
+    """Device pointers of the integer tables of the last call on ``ws``."""
+    out = HawkesTables()
+    _check(lib().hawkes_integer_tables(ws, int(N), int(M), int(B), int(bool(grad)),
+                                       ctypes.byref(opts), ctypes.byref(out)),
+           "hawkes_integer_tables")
+    return out
 
 
 def hawkes_static_scratch_bytes() -> int:

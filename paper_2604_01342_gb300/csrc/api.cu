@@ -139,7 +139,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_delta = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
         pl->off_Dspan = take(sizeof(float) * (size_t)pl->nb_max);
         pl->off_Tmt = take(sizeof(float) * (size_t)pl->nb_max);
-        pl->off_cen = take(sizeof(float) * 2 * (size_t)M);
+        pl->off_cen = take(sizeof(float) * (6 * (size_t)M + 1));
         pl->off_wsum = take(sizeof(double) * (size_t)M);
         pl->off_Y = take(sizeof(float) * nbM);
         pl->off_isc = take(sizeof(float) * (3 * (size_t)M + 2 * (size_t)pl->nb_max));
@@ -216,6 +216,9 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.Tmt = at<float>(ws, pl.off_Tmt);
     p.cen_S = at<float>(ws, pl.off_cen);
     p.bias_Y = p.cen_S ? p.cen_S + M : nullptr;
+    p.cen_Z = p.cen_S ? p.cen_S + 2 * (size_t)M : nullptr;
+    p.bias_Z = p.cen_S ? p.cen_S + 3 * (size_t)M : nullptr;
+    p.cen_acc = p.cen_S ? p.cen_S + 4 * (size_t)M : nullptr;
     p.wsum_acc = at<double>(ws, pl.off_wsum);
     p.isc_al = at<float>(ws, pl.off_isc);
     p.isc_S = p.isc_al ? p.isc_al + M : nullptr;
@@ -375,19 +378,38 @@ size_t hawkes_workspace_size(int64_t N, int32_t M, int32_t B, int32_t grad,
     return pl.total;
 }
 
+}  // extern "C"
+
+namespace hk {
+// The host-side checks of one single-sequence call, in the order hawkes_loglik_grad makes
+// them: sizes and T, null pointers, then the configuration (make_plan).  Returns 0 or the
+// status that call would return before touching the workspace.
+int check_single_args(const double* t, const int32_t* c, int64_t N, double T, int32_t M,
+                      const float* mu, const float* alpha, const float* beta,
+                      const hawkes_opts* opts, const double* out_ll, const float* d_mu,
+                      const float* d_alpha, const float* d_beta, int grad) {
+    if (N < 0 || M <= 0 || !(T >= 0.0)) return HAWKES_ERR_INVALID_ARG;
+    if (bad_ptrs({mu, alpha, beta, out_ll})) return HAWKES_ERR_INVALID_ARG;
+    if (N > 0 && bad_ptrs({t, c})) return HAWKES_ERR_INVALID_ARG;
+    if (grad && bad_ptrs({d_mu, d_alpha, d_beta})) return HAWKES_ERR_INVALID_ARG;
+    Plan pl;
+    return make_plan(N, M, 1, grad, opts, &pl);
+}
+}  // namespace hk
+
+extern "C" {
+
 static hawkes_status single(const double* t, const int32_t* c, int64_t N, double T, int32_t M,
                             const float* mu, const float* alpha, const float* beta,
                             const hawkes_opts* opts, void* ws, size_t ws_bytes, double* out_ll,
                             float* d_mu, float* d_alpha, float* d_beta, int grad, void* stream,
                             const float* carry_S = nullptr, const float* carry_G = nullptr,
                             int base_term = 1) {
-    if (N < 0 || M <= 0 || !(T >= 0.0)) return HAWKES_ERR_INVALID_ARG;
-    if (bad_ptrs({mu, alpha, beta, out_ll})) return HAWKES_ERR_INVALID_ARG;
-    if (N > 0 && bad_ptrs({t, c})) return HAWKES_ERR_INVALID_ARG;
-    if (grad && bad_ptrs({d_mu, d_alpha, d_beta})) return HAWKES_ERR_INVALID_ARG;
-    Plan pl;
-    int rc = make_plan(N, M, 1, grad, opts, &pl);
+    int rc = hk::check_single_args(t, c, N, T, M, mu, alpha, beta, opts, out_ll, d_mu, d_alpha,
+                                   d_beta, grad);
     if (rc) return (hawkes_status)rc;
+    Plan pl;
+    make_plan(N, M, 1, grad, opts, &pl);
     if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < pl.total) return HAWKES_ERR_WORKSPACE;
     // single sequence: offsets {0, N} and T are written into the header's spare
     // words by the first kernel, so the call issues no host-to-device copy
@@ -585,6 +607,22 @@ hawkes_status hawkes_last_device_status(void* workspace, void* stream) {
 const int64_t* hawkes_mark_counts(void* workspace) {
     if (!workspace) return nullptr;
     return (const int64_t*)((char*)workspace + align_up(sizeof(hk::WsHeader)));
+}
+
+hawkes_status hawkes_integer_tables(void* workspace, int64_t N, int32_t M, int32_t B,
+                                    int32_t grad, const hawkes_opts* opts, hawkes_tables* out) {
+    if (!workspace || !out) return HAWKES_ERR_INVALID_ARG;
+    Plan pl;
+    int rc = make_plan(N, M, B, grad ? 1 : 0, opts, &pl);
+    if (rc) return (hawkes_status)rc;
+    out->mark_counts = at<int64_t>(workspace, pl.off_counts);
+    out->chunk_base = at<int64_t>(workspace, pl.off_chunk_base);
+    out->chunk_seq = at<int32_t>(workspace, pl.off_chunk_seq);
+    out->bucket_start = pl.path == PATH_GEMM ? at<int32_t>(workspace, pl.off_bstart) : nullptr;
+    out->bucket_slots = pl.path == PATH_GEMM ? at<uint32_t>(workspace, pl.off_recs) : nullptr;
+    out->chunk = pl.C;
+    out->mark_blocks = pl.path == PATH_GEMM ? pl.P : 0;
+    return HAWKES_OK;
 }
 
 const char* hawkes_status_str(hawkes_status s) {

@@ -107,9 +107,13 @@ struct Problem {
     float* Dspan;            // [nb_max] t of the next chunk's first event - t of its first (same)
     float* Tmt;              // [nb_max] T - t of the chunk's first event (same)
     // centering of the GEMM operands (the tensor-core accumulation error is one-signed
-    // for same-signed operands; centred operands make it unbiased)
-    float* cen_S;            // [M] m_j = n_j / (beta T): stationary mean of S_j
+    // for same-signed operands; centred operands make it unbiased): column means of the
+    // operands over a sample of chunks, added back exactly through the biases
+    float* cen_S;            // [M] mean of S^_b[j] over the sampled chunks
     float* bias_Y;           // [M] alpha . cen_S  (FP64-accumulated)
+    float* cen_Z;            // [M] mean of (S^_b - beta G^_b)[j] over the sampled chunks
+    float* bias_Z;           // [M] alpha . cen_Z  (FP64-accumulated)
+    float* cen_acc;          // [2M + 1] column sums of the sampled rows, then their number
     double* wsum_acc;        // [M] sum_b W[b][i]
     int64_t ldk;             // 64 ceil(M / 32): halves per paired row of K = M elements
     int64_t ldt;             // 64 ceil(nbp / 32): halves per paired row of K = nbp elements
@@ -176,10 +180,7 @@ __device__ __forceinline__ void chunk_range(const Problem& p, int64_t b, int32_t
 
 __device__ __forceinline__ int64_t num_chunks(const Problem& p) { return p.chunk_base[p.B]; }
 
-// Sum of log lambda without per-event log rounding: each thread keeps the product of its
-// lambdas as an FP64 mantissa in [0.5, 1) and an integer binary exponent, and takes one
-// FP64 log when the product is folded into a sum.
-// Running product of positive FP32 factors as an FP32 mantissa in [1, 2) and an integer
+// Sum of log lambda without per-event log rounding.  Running product of positive FP32 factors as an FP32 mantissa in [1, 2) and an integer
 // binary exponent (no FP64 arithmetic per factor: this part's FP64 rate is 1/64 of its
 // FP32 rate); one FP64 log per thread at the end.  Each factor adds one FP32 rounding
 // (relative 2^-24, either sign) to the product.
@@ -251,6 +252,12 @@ cudaError_t launch_finalize(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_slice_aggregate(const Problem& p, double t_next, float* agg_S, float* agg_G,
                                    cudaStream_t s, int* nlaunch);
 int walk_max_m(int grad);
+// Host-side argument checks of a single-sequence call (api.cu): 0 or the status that
+// hawkes_loglik(_grad) returns before anything is launched.
+int check_single_args(const double* t, const int32_t* c, int64_t N, double T, int32_t M,
+                      const float* mu, const float* alpha, const float* beta,
+                      const hawkes_opts* opts, const double* out_ll, const float* d_mu,
+                      const float* d_alpha, const float* d_beta, int grad);
 // Optional per-kernel timing: when enabled, records a CUDA event on the launch
 // stream after each kernel (names are static strings).
 void prof_mark(cudaStream_t s, const char* name);

@@ -35,7 +35,8 @@ cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* dst, int6
                                 int64_t rows, int64_t cols, cudaStream_t s, float* inv_scale,
                                 double* row_sum);
 cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
-                                const float* centre, const float* coef, __half* out1,
+                                const float* centre, const float* centre2, const float* coef,
+                                __half* out1,
                                 float* isc1, __half* out2, float* isc2, int64_t ldd,
                                 int64_t rows, int64_t cols, const int64_t* rows_valid,
                                 uint32_t* colmax, cudaStream_t s);
@@ -44,25 +45,66 @@ cudaError_t transpose_split_f16(const float* src, int64_t cols, const int64_t* r
                                 const float* centre, uint32_t* amax_bits, float* inv_scale,
                                 bool have_max);
 
-// Centre of the Y GEMM operand: the stationary means m_j = n_j / (beta T) of S_j, and the
-// exact products alpha . m in FP64.  (The Z operand S - beta G has stationary mean 0.)
-// One warp per row of alpha.
-__global__ void k_centres(Problem p, int have_counts) {
+// Centres of the GEMM operands.  The tensor cores accumulate the products of one k-group
+// with a rounding toward zero, so when a row's products share one sign the error of every
+// product adds up with that sign (Section 3's products of the states with alpha >= 0 are
+// such rows: most marks fire rarely, and S^ - beta G^ of a rarely fired mark is mostly
+// negative).  Each operand column is therefore centred on its mean over a sample of the
+// chunks (every step-th chunk, at most kCentreRows of them) before the split, and the
+// exact products alpha . centre (FP64-accumulated) are added back as the GEMM's bias.
+// Any centre gives the same product up to rounding; a centre near the column mean makes
+// the products of each row mixed in sign, so that the accumulation error has mean zero.
+constexpr int kCentreRows = 1024;
+constexpr int kCentreSlices = 32;     // row slices of the column sums, one block row each
+
+// Column sums of S^ and S^ - beta G^ over the sampled chunks: block (x, y) takes 256
+// columns and every kCentreSlices-th sampled row from slice y; sums into acc [2 M] (zeroed
+// before), the number of sampled rows into acc_n.
+__global__ void k_col_sums(Problem p, int want_z, float* acc, int* acc_n) {
     const int M = p.M;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nb = num_chunks(p);
+    const int64_t step = nb > kCentreRows ? (nb + kCentreRows - 1) / kCentreRows : 1;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *acc_n = (int)((nb + step - 1) / step);
+    if (j >= M) return;
     const float beta = p.beta[0];
-    const double T = p.Tarr[0];
+    float s = 0.f, z = 0.f;
+    for (int64_t b = (int64_t)blockIdx.y * step; b < nb; b += (int64_t)kCentreSlices * step) {
+        const float v = p.Shat[b * M + j];
+        s += v;
+        if (want_z) z += v - beta * p.Ghat[b * M + j];
+    }
+    if (s != 0.f) atomicAdd(&acc[j], s);
+    if (want_z && z != 0.f) atomicAdd(&acc[M + j], z);
+}
+
+// The centres cen_S, cen_Z (column means: the sums of k_col_sums over the sampled rows)
+// and bias_Y = alpha . cen_S, bias_Z = alpha . cen_Z in FP64, one warp per row of alpha.
+__global__ void k_centres(Problem p, int want_z, const float* acc, const int* acc_n) {
+    const int M = p.M;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    auto centre = [&](int j) -> float {
-        return (have_counts && T > 0.0) ? (float)((double)p.counts[j] / ((double)beta * T)) : 0.f;
-    };
+    const float inv = *acc_n > 0 ? 1.f / (float)*acc_n : 0.f;
     if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < M; j += blockDim.x) p.cen_S[j] = centre(j);
+        for (int j = threadIdx.x; j < M; j += blockDim.x) {
+            p.cen_S[j] = acc[j] * inv;
+            if (want_z) p.cen_Z[j] = acc[M + j] * inv;
+        }
     for (int i = warp; i < M; i += nwarps) {
-        double y = 0.0;
-        for (int j = lane; j < M; j += 32) y += (double)p.alpha[(int64_t)i * M + j] * (double)centre(j);
-        for (int o = 16; o >= 1; o >>= 1) y += __shfl_xor_sync(HK_FULL, y, o);
-        if (lane == 0) p.bias_Y[i] = (float)y;
+        double y = 0.0, z = 0.0;
+        for (int j = lane; j < M; j += 32) {
+            const double a = (double)p.alpha[(int64_t)i * M + j];
+            y += a * (double)(acc[j] * inv);
+            if (want_z) z += a * (double)(acc[M + j] * inv);
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            y += __shfl_xor_sync(HK_FULL, y, o);
+            z += __shfl_xor_sync(HK_FULL, z, o);
+        }
+        if (lane == 0) {
+            p.bias_Y[i] = (float)y;
+            if (want_z) p.bias_Z[i] = (float)z;
+        }
     }
 }
 
@@ -651,10 +693,13 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     cudaError_t err;
     const int64_t M = p.M, nb = p.nb_max;
     // Y = S^ alpha^T and Z = (S^ - beta G^) alpha^T on the tensor cores (rows = chunks)
-    // mark counts exist only when the inputs were validated; without them the centre is 0
     cudaMemsetAsync(p.wsum_acc, 0, sizeof(double) * (size_t)M, s);
-    k_centres<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(p, p.validated);
-    ++*nl;
+    cudaMemsetAsync(p.cen_acc, 0, sizeof(float) * (2 * (size_t)M + 1), s);
+    int* acc_n = (int*)(p.cen_acc + 2 * (size_t)M);
+    k_col_sums<<<dim3((unsigned)((M + 255) / 256), kCentreSlices), 256, 0, s>>>(p, p.grad,
+                                                                              p.cen_acc, acc_n);
+    k_centres<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(p, p.grad, p.cen_acc, acc_n);
+    *nl += 2;
     prof_mark(s, "centres");
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int64_t* nb_dev = p.chunk_base + p.B;   // number of chunks, on the device
@@ -666,8 +711,9 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     // S^ - m for Y and, with the gradient, S^ - beta G^ for Z (see below) in one pass over S^
     if (p.grad) {
         // (and the column maxima of S^ - m for the transposed split of the dalpha GEMM)
-        if ((err = split_f16_rows_pair(p.Shat, p.Ghat, M, p.cen_S, p.beta, p.S_p, p.isc_S,
-                                       p.G_p, p.isc_G, p.ldk, nb, M, nb_dev, p.colmax, s)) !=
+        if ((err = split_f16_rows_pair(p.Shat, p.Ghat, M, p.cen_S, p.cen_Z, p.beta, p.S_p,
+                                       p.isc_S, p.G_p, p.isc_G, p.ldk, nb, M, nb_dev, p.colmax,
+                                       s)) !=
             cudaSuccess)
             return err;
         ++*nl;
@@ -691,7 +737,7 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
         // forward state and its beta-derivative is formed once per chunk and element from
         // the scan's states (split above), before any rounding of the tensor-core product
         if ((err = tc_gemm_f16x3(p.G_p, p.ldk, p.al_p, p.ldk, p.Z, M, (int)nb,
-                                 (int)M, M, 1, false, p.hdr, s, nullptr, p.isc_G, p.isc_al)) !=
+                                 (int)M, M, 1, false, p.hdr, s, p.bias_Z, p.isc_G, p.isc_al)) !=
             cudaSuccess)
             return err;
         ++*nl;

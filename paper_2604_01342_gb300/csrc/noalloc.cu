@@ -54,8 +54,13 @@ hawkes_status hawkes_loglik_grad_static(const double* t, const int32_t* c, int64
                                         const float* beta, const hawkes_opts* opts,
                                         double* out_ll, float* d_mu, float* d_alpha,
                                         float* d_beta, void* stream) {
+    // the same checks, in the same order, as hawkes_loglik_grad: a call that one rejects,
+    // the other rejects with the same status; only then the size of the scratch array
+    const int rc = hk::check_single_args(t, c, N, T, M, mu, alpha, beta, opts, out_ll, d_mu,
+                                         d_alpha, d_beta, 1);
+    if (rc) return (hawkes_status)rc;
     const size_t need = hawkes_workspace_size(N, M, 1, 1, opts);
-    if (need == 0) return (N < 0 || M <= 0) ? HAWKES_ERR_INVALID_ARG : HAWKES_ERR_UNSUPPORTED;
+    if (need == 0) return HAWKES_ERR_UNSUPPORTED;
     if (need > kStaticScratchBytes) return HAWKES_ERR_WORKSPACE;   // problem too large
     void* ws = scratch_for_current_device();
     if (!ws) return HAWKES_ERR_CUDA;

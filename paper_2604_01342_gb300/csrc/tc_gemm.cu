@@ -28,7 +28,9 @@
 // (measured with TF32 operands: ~1.6e-6 after 64 of K, ~2.6e-5 after 1024), so every 64 of
 // K (two k-tiles) is accumulated into one of two TMEM banks and then promoted: eight warps
 // read the finished bank with tcgen05.ld and add it to FP32 registers while the MMAs fill
-// the other bank.  The output tile is staged in the (then free) stage buffers and stored as
+// the other bank.  Within a group the eight small cross-product MMAs are issued before the
+// four hi x hi ones, so that the truncation of each MMA's sum happens at the small
+// products' own scale and only the last four are truncated at the scale of the result.  The output tile is staged in the (then free) stage buffers and stored as
 // whole row pieces.  Every mbarrier wait is bounded; on timeout the kernel records an error
 // in the status word, waits (bounded) for its MMAs and copies, frees its tensor memory and
 // returns.
@@ -236,39 +238,55 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
         if (lane == 0 && KT > 0) {
             const uint32_t idesc = idesc_f16(BM, BN);
             bool ok = true;
-            for (int i = 0; i < KT; ++i) {
-                const int s = i % STAGES;
-                if (!mbar_wait_or_abort(&full[s], (uint32_t)((i / STAGES) & 1), abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                uint8_t* st = smem + s * STAGE_BYTES;
-                const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
-                const int g = i / kTilesPerGroup, bank = g & 1;
-                const bool first_in_group = (i % kTilesPerGroup) == 0;
-                if (first_in_group && g >= 2) {
+            for (int g = 0; g < ngroups && ok; ++g) {
+                const int i0 = g * kTilesPerGroup;
+                const int i1 = i0 + kTilesPerGroup < KT ? i0 + kTilesPerGroup : KT;
+                const int bank = g & 1;
+                if (g >= 2) {
                     // the epilogue must have read this bank's previous group
                     if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) {
                         ok = false;
                         break;
                     }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
+                for (int i = i0; i < i1 && ok; ++i)
+                    if (!mbar_wait_or_abort(&full[i % STAGES], (uint32_t)((i / STAGES) & 1),
+                                            abort_flag))
+                        ok = false;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
+                // The accumulator truncates each MMA's sum toward zero at its own magnitude,
+                // so the group's small cross products (hi x lo, lo x hi) go first, into the
+                // fresh bank while it is small, and the large hi x hi products last: only
+                // those (and the first of them) are truncated at the scale of the result.
+                uint32_t acc = 0u;
+                for (int i = i0; i < i1; ++i) {
+                    uint8_t* st = smem + (i % STAGES) * STAGE_BYTES;
+                    const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    // 16 fp16 = 32 bytes along the 128-byte swizzled row: the high parts
-                    // at bytes 0-63, the low parts at 64-127
-                    const uint64_t oh = (uint64_t)(kk * 32) >> 4;
-                    const uint64_t ol = (uint64_t)(64 + kk * 32) >> 4;
-                    const uint32_t acc0 = (!first_in_group || kk > 0) ? 1u : 0u;
-                    mma_f16(acc_t, da + oh, db + oh, idesc, acc0);
-                    mma_f16(acc_t, da + oh, db + ol, idesc, 1u);
-                    mma_f16(acc_t, da + ol, db + oh, idesc, 1u);
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        // 16 fp16 = 32 bytes along the 128-byte swizzled row: the high parts
+                        // at bytes 0-63, the low parts at 64-127
+                        const uint64_t oh = (uint64_t)(kk * 32) >> 4;
+                        const uint64_t ol = (uint64_t)(64 + kk * 32) >> 4;
+                        mma_f16(acc_t, da + oh, db + ol, idesc, acc);
+                        acc = 1u;
+                        mma_f16(acc_t, da + ol, db + oh, idesc, 1u);
+                    }
                 }
-                if ((i % kTilesPerGroup) == kTilesPerGroup - 1 || i == KT - 1) mma_commit(&bank_full[bank]);
-                mma_commit(&empty[s]);           // the stage may be refilled once these are done
+                for (int i = i0; i < i1; ++i) {
+                    uint8_t* st = smem + (i % STAGES) * STAGE_BYTES;
+                    const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t oh = (uint64_t)(kk * 32) >> 4;
+                        mma_f16(acc_t, da + oh, db + oh, idesc, 1u);
+                    }
+                }
+                mma_commit(&bank_full[bank]);
+                // the group's stages may be refilled once these MMAs are done
+                for (int i = i0; i < i1; ++i) mma_commit(&empty[i % STAGES]);
             }
             if (!ok) {
                 *abort_flag = 1;
@@ -577,10 +595,12 @@ __global__ void k_split_f16_rows(const float* __restrict__ src, int64_t lds, __h
 }
 
 // Two row-scaled splits of one matrix in one pass over it (one warp per row): out1 = src -
-// centre (per column) and out2 = src - (*coef) sub, each with its own row exponent and
-// inverse scale, as paired rows; rows at or past *rows_valid are written as zeros.
+// centre (per column) and out2 = src - (*coef) sub - centre2 (per column), each with its own
+// row exponent and inverse scale, as paired rows; rows at or past *rows_valid are written as
+// zeros.
 __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float* __restrict__ sub,
                                       int64_t lds, const float* __restrict__ centre,
+                                      const float* __restrict__ centre2,
                                       const float* __restrict__ coef, __half* out1, float* isc1,
                                       __half* out2, float* isc2, int64_t ldd, int64_t rows,
                                       int64_t cols, const int64_t* rows_valid, uint32_t* colmax) {
@@ -591,7 +611,7 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
     const int64_t wpb = blockDim.x >> 5;
     const int64_t cpad = tc::round32(cols);
     const bool vec = (lds & 3) == 0 && tc::aligned16(src) && tc::aligned16(sub) &&
-                     tc::aligned16(centre);
+                     tc::aligned16(centre) && tc::aligned16(centre2);
     if (colmax) {
         for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) cmax_sh[c] = 0u;
         __syncthreads();
@@ -614,7 +634,7 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
             const float v = sr[c];
             const float a1 = fabsf(v - centre[c]);
             m1 = fmaxf(m1, a1);
-            m2 = fmaxf(m2, fabsf(v - cf * ur[c]));
+            m2 = fmaxf(m2, fabsf((v - cf * ur[c]) - centre2[c]));
             if (colmax && a1 > 0.f) atomicMax(&cmax_sh[c], __float_as_uint(a1));
         }
 #pragma unroll
@@ -630,12 +650,15 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
             const float4 v = tc::load4(sr, c, cols, vec);
             const float4 m = tc::load4(centre, c, cols, vec);
             const float4 u = tc::load4(ur, c, cols, vec);
+            const float4 m2c = tc::load4(centre2, c, cols, vec);
             tc::p128_store(d1, c0, cpad, lane,
                            tc::split4(make_float4((v.x - m.x) * sc1, (v.y - m.y) * sc1,
                                                   (v.z - m.z) * sc1, (v.w - m.w) * sc1)));
             tc::p128_store(d2, c0, cpad, lane,
-                           tc::split4(make_float4((v.x - cf * u.x) * sc2, (v.y - cf * u.y) * sc2,
-                                                  (v.z - cf * u.z) * sc2, (v.w - cf * u.w) * sc2)));
+                           tc::split4(make_float4(((v.x - cf * u.x) - m2c.x) * sc2,
+                                                  ((v.y - cf * u.y) - m2c.y) * sc2,
+                                                  ((v.z - cf * u.z) - m2c.z) * sc2,
+                                                  ((v.w - cf * u.w) - m2c.w) * sc2)));
         }
         if (lane == 0) {
             isc1[r] = ldexpf(1.f, -a1);
@@ -652,12 +675,13 @@ __global__ void k_split_f16_rows_pair(const float* __restrict__ src, const float
 // colmax (optional, [cols] uint bits, zeroed here): the largest |out1| of every column over
 // the valid rows, for a later transposed split of the same matrix.
 cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
-                                const float* centre, const float* coef, __half* out1,
-                                float* isc1, __half* out2, float* isc2, int64_t ldd,
-                                int64_t rows, int64_t cols, const int64_t* rows_valid,
-                                uint32_t* colmax, cudaStream_t s) {
+                                const float* centre, const float* centre2, const float* coef,
+                                __half* out1, float* isc1, __half* out2, float* isc2,
+                                int64_t ldd, int64_t rows, int64_t cols,
+                                const int64_t* rows_valid, uint32_t* colmax, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
-    if (!src || !sub || !centre || !coef || (ldd & 1) || ldd < 2 * tc::round32(cols))
+    if (!src || !sub || !centre || !centre2 || !coef || (ldd & 1) ||
+        ldd < 2 * tc::round32(cols))
         return cudaErrorInvalidValue;
     const size_t smem = colmax ? sizeof(uint32_t) * (size_t)cols : 0;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
@@ -672,7 +696,8 @@ cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
     }
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_split_f16_rows_pair<<<(unsigned)blocks, 256, smem, s>>>(src, sub, lds, centre, coef, out1,
+    k_split_f16_rows_pair<<<(unsigned)blocks, 256, smem, s>>>(src, sub, lds, centre, centre2,
+                                                              coef, out1,
                                                               isc1, out2, isc2, ldd, rows, cols,
                                                               rows_valid, colmax);
     return cudaGetLastError();

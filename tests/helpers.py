@@ -5,15 +5,14 @@ compare with the stated tolerances:
   max-norm relative gradient error max|g - g*| / max|g*|    <= 1e-4 per block
 The oracle is evaluated at the FP32-rounded parameters the GPU receives.
 
-A result close to zero can be a small difference of large sums: the
-log-likelihood (intensity logs minus the compensator) or the decay gradient
-(excitation terms minus compensator terms, which nearly cancel at the simulating
-parameters).  Its relative error is then ill-conditioned.  With the oracle's
-conditioning scale S (the sum of magnitudes of those terms, oracle.condition),
-a result passes at the stated relative tolerance, or else when its error is at
-most 1e-7 of S (FP32-level accuracy of the terms): for L that is
-|L - L*| <= 1e-6 max(|L*|, S / 10), for dbeta max|d - d*| <= 1e-4 max(max|d*|, S / 1000).
-Every such case is reported with its kappa = S / |result|."""
+One reading is allowed for the log-likelihood only, and only where a test asks
+for it (the batch of short per-source sequences): L is the difference of the
+intensity logs and the compensator, and for some short sequences the two nearly
+cancel, so that |L*| is far below the size of its terms and a relative error
+of 1e-6 would need the FP32 intensities to be better than FP32.  With the
+oracle's conditioning scale S of L (the sum of the magnitudes of its terms,
+oracle.condition), such an L passes when |L - L*| <= 1e-7 S.  Every such case
+is reported with its kappa = S / |L*|.  Gradients have no such reading."""
 import numpy as np
 
 LL_RTOL = 1e-6
@@ -69,22 +68,20 @@ SCALE_REL = 1e-7
 
 
 def assert_close(got, ref, grad=True, ll_rtol=LL_RTOL, grad_rtol=GRAD_RTOL, what="",
-                 ll_scale=None, dbeta_scale=None):
+                 ll_scale=None):
+    """Stated tolerances per result; ``ll_scale`` (the oracle's conditioning scale of L)
+    admits an ill-conditioned L at 1e-7 of its scale, and returns True when it did."""
+    used_scale = False
     e = rel_err(got["ll"], ref["ll"])
     if e > ll_rtol and ll_scale is not None:
         kappa = ll_scale / abs(ref["ll"])
         e_s = abs(got["ll"] - ref["ll"]) / ll_scale
         print(f"{what}: loglik kappa {kappa:.1f}: rel err {e:.3e}, err / scale {e_s:.3e}")
         e = e_s * ll_rtol / SCALE_REL
+        used_scale = True
     assert e <= ll_rtol, f"{what} loglik rel err {e:.3e} (gpu {got['ll']!r} vs {ref['ll']!r})"
     if grad:
         for k in ("dmu", "dalpha", "dbeta"):
             e = maxnorm_rel(got[k], ref[k])
-            if k == "dbeta" and e > grad_rtol and dbeta_scale is not None:
-                S = float(np.max(dbeta_scale))
-                kappa = S / float(np.max(np.abs(ref[k])))
-                e_s = float(np.max(np.abs(np.asarray(got[k]) - np.asarray(ref[k])))) / S
-                print(f"{what}: dbeta kappa {kappa:.1f}: max-norm rel err {e:.3e}, "
-                      f"err / scale {e_s:.3e}")
-                e = e_s * grad_rtol / SCALE_REL
             assert e <= grad_rtol, f"{what} {k} max-norm rel err {e:.3e}"
+    return used_scale

@@ -58,15 +58,39 @@ def test_workspace_sizes(lib):
         1000, 8, 1, True, per)
 
 
+def _cuda_visible():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
 def test_host_side_errors_need_no_gpu(lib):
+    """Argument checks that return before anything is launched.  Pointers are NULL or
+    real (host) buffers of the right sizes, never made-up addresses."""
+    import numpy as np
     opts = binding.make_opts(False)
     rc = lib.hawkes_loglik(None, None, 5, 1.0, 3, None, None, None, ctypes.byref(opts), None, 0,
                            None, None)
-    assert rc == 1
-    fake = ctypes.c_void_p(256)
-    rc = lib.hawkes_loglik(fake, fake, 5, 1.0, 3, fake, fake, fake, ctypes.byref(opts), None, 0,
-                           fake, None)
+    assert rc == 1   # null inputs
+    rc = lib.hawkes_loglik_grad(None, None, 5, -1.0, 3, None, None, None, ctypes.byref(opts),
+                                None, 0, None, None, None, None, None)
+    assert rc == 1   # T < 0 (checked before the pointers)
+    rc = lib.hawkes_loglik_grad(None, None, 0, 1.0, 0, None, None, None, ctypes.byref(opts),
+                                None, 0, None, None, None, None, None)
+    assert rc == 1   # M = 0
+
+
+@pytest.mark.skipif(_cuda_visible(), reason="host-buffer pointers are for the no-GPU check only")
+def test_missing_workspace_is_reported_without_a_gpu(lib):
+    import numpy as np
+    opts = binding.make_opts(False)
+    t = np.linspace(0.0, 1.0, 5)
+    c = np.zeros(5, np.int32)
+    mu, al, be = np.ones(3, np.float32), np.ones(9, np.float32), np.ones(3, np.float32)
+    ll = np.zeros(1)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    rc = lib.hawkes_loglik(ptr(t), ptr(c), 5, 1.0, 3, ptr(mu), ptr(al), ptr(be),
+                           ctypes.byref(opts), None, 0, ptr(ll), None)
     assert rc == 7   # workspace missing
-    rc = lib.hawkes_loglik_grad(fake, fake, 5, -1.0, 3, fake, fake, fake, ctypes.byref(opts),
-                                fake, 1 << 30, fake, fake, fake, fake, None)
-    assert rc == 1   # T < 0

@@ -1,11 +1,16 @@
 """Parity at the benchmark's sizes, in the launch configuration bench.py times
-(default chunk, automatic path), on what the FP64 oracle can finish in seconds:
-  * the M=1024 shared-decay stream: the full 1e7-event run must be finite and
-    satisfy the Euler identity of the 1-homogeneous (mu, alpha); a 2e5-event
-    prefix of the same stream is compared with the oracle element by element;
-  * the M=64 per-source stream of 1e6 events: compared with the oracle in full;
-  * the 4,096-sequence batch of M=8 sequences: compared with the oracle in full.
+(default chunk, automatic path), against the FP64 oracle element by element at the
+stated tolerances (relative L error <= 1e-6, max-norm relative gradient error <= 1e-4
+per block):
+  * the M=1024 shared-decay stream: the whole 1e7-event run (the oracle takes about a
+    minute on one host core; it starts in a background thread when this module's first
+    test runs) and a 2e5-event prefix;
+  * the M=64 per-source stream of 1e6 events;
+  * the 4,096-sequence batch of M=8 sequences, where the log-likelihood of some short
+    sequences is ill-conditioned (see helpers.py) and is then stated against its scale.
 """
+import threading
+
 import numpy as np
 import pytest
 
@@ -20,47 +25,62 @@ def c4():
     return synth.workload(4)
 
 
+class _Background:
+    """The oracle on the whole M=1024 stream, computed while the other tests run (the
+    ctypes call releases the GIL)."""
+
+    def __init__(self, p):
+        self.result = None
+        self.error = None
+        self.thread = threading.Thread(target=self._run, args=(p,), daemon=True)
+        self.thread.start()
+
+    def _run(self, p):
+        try:
+            self.result = oracle_ref(p)
+        except Exception as e:        # reported by the test that waits for it
+            self.error = e
+
+    def get(self):
+        self.thread.join()
+        if self.error is not None:
+            raise self.error
+        return self.result
+
+
+@pytest.fixture(scope="module")
+def c4_oracle(c4):
+    return _Background(c4)
+
+
 def _prefix(p, n):
     q = synth.Problem(t=p.t[:n].copy(), c=p.c[:n].copy(), T=float(p.t[n - 1]), mu=p.mu,
                       alpha=p.alpha, beta=p.beta, shared_beta=p.shared_beta, name=p.name)
     return q
 
 
-def test_m1024_prefix_matches_oracle(c4):
+def _report(what, got, ref):
+    print(f"{what}: loglik rel err {rel_err(got['ll'], ref['ll']):.3e}; " + ", ".join(
+        f"{k} {maxnorm_rel(got[k], ref[k]):.3e}" for k in ("dmu", "dalpha", "dbeta")))
+
+
+def test_m1024_prefix_matches_oracle(c4, c4_oracle):
     import oracle
     p = _prefix(c4, 200_000)
     got = gpu_run(p)
     ref = oracle_ref(p)
-    for k in ("dmu", "dalpha", "dbeta"):
-        print(f"M=1024 prefix 2e5: {k} max-norm rel err {maxnorm_rel(got[k], ref[k]):.3e}")
-    print(f"M=1024 prefix 2e5: loglik rel err {rel_err(got['ll'], ref['ll']):.3e}")
+    _report("M=1024 prefix 2e5", got, ref)
     sc = oracle.condition(p.t, p.c, p.T, f32(p.mu), f32(p.alpha), np.full(p.M, f32(p.beta)[0]))
-    assert_close(got, ref, what="M=1024 prefix", ll_scale=sc["ll"],
-                 dbeta_scale=np.array([sc["dbeta"].sum()]))
-
-
-def test_m1024_full_size_identities(c4):
-    p = c4
-    got = gpu_run(p)
-    assert np.isfinite(got["ll"]) and all(np.all(np.isfinite(got[k]))
-                                          for k in ("dmu", "dalpha", "dbeta"))
-    # Euler identity: sum mu dmu + sum alpha dalpha = N - Lambda(T), with the compensator
-    # Lambda(T) computed here in FP64 from its closed form
-    mu, al, be = f32(p.mu), f32(p.alpha), f32(p.beta)[0]
-    colsum = al.sum(axis=0)
-    comp = p.T * mu.sum() + float(np.sum(colsum[p.c] * -np.expm1(-be * (p.T - p.t))))
-    lhs = float(np.dot(mu, got["dmu"]) + np.sum(al * got["dalpha"]))
-    scale = float(np.dot(mu, np.abs(got["dmu"] + p.T)) + p.T * mu.sum() + p.N)
-    print(f"M=1024 full: Euler residual {abs(lhs - (p.N - comp)) / scale:.3e} of its scale")
-    assert abs(lhs - (p.N - comp)) <= 1e-4 * scale
+    print(f"M=1024 prefix 2e5: dbeta kappa {sc['dbeta'].sum() / abs(ref['dbeta'][0]):.0f} "
+          f"(information only)")
+    assert_close(got, ref, what="M=1024 prefix")
 
 
 def test_m64_per_source_full_size():
     p = synth.workload(2)
     got = gpu_run(p)
     ref = oracle_ref(p)
-    for k in ("dmu", "dalpha", "dbeta"):
-        print(f"M=64 1e6: {k} max-norm rel err {maxnorm_rel(got[k], ref[k]):.3e}")
+    _report("M=64 1e6", got, ref)
     assert_close(got, ref, what="M=64 per-source 1e6")
 
 
@@ -79,16 +99,43 @@ def test_varlen_4096_full_size():
     ll, dmu, dal, dbe = [x.cpu().numpy().astype(np.float64) for x in r]
     ref = oracle.loglik_grad_varlen(vp.t, vp.c, vp.offsets, vp.T, f32(vp.mu), f32(vp.alpha),
                                     f32(vp.beta))
-    worst = 0.0
+    worst, n_scaled, worst_scaled = 0.0, 0, (0.0, 0.0, -1)
     for s in range(vp.B):
         got = {"ll": ll[s], "dmu": dmu[s], "dalpha": dal[s], "dbeta": dbe[s]}
         want = {k: ref[k][s] for k in ("ll", "dmu", "dalpha", "dbeta")}
-        scale = dscale = None
-        if rel_err(got["ll"], want["ll"]) > 1e-6 or maxnorm_rel(got["dbeta"], want["dbeta"]) > 1e-4:
+        scale = None
+        if rel_err(got["ll"], want["ll"]) > 1e-6:
             a, b = vp.offsets[s], vp.offsets[s + 1]
-            sc = oracle.condition(vp.t[a:b], vp.c[a:b], vp.T[s], f32(vp.mu[s]),
-                                  f32(vp.alpha[s]), f32(vp.beta[s]))
-            scale, dscale = sc["ll"], sc["dbeta"]
-        assert_close(got, want, what=f"seq {s}", ll_scale=scale, dbeta_scale=dscale)
-        worst = max(worst, rel_err(got["ll"], want["ll"]))
-    print(f"varlen 4096 x M=8: worst per-sequence loglik rel err {worst:.3e}")
+            scale = oracle.condition(vp.t[a:b], vp.c[a:b], vp.T[s], f32(vp.mu[s]),
+                                     f32(vp.alpha[s]), f32(vp.beta[s]))["ll"]
+        if assert_close(got, want, what=f"seq {s}", ll_scale=scale):
+            n_scaled += 1
+            e = rel_err(got["ll"], want["ll"])
+            if e > worst_scaled[0]:
+                worst_scaled = (e, scale / abs(want["ll"]), s)
+        else:
+            worst = max(worst, rel_err(got["ll"], want["ll"]))
+    print(f"varlen 4096 x M=8: worst loglik rel err of the well-conditioned sequences "
+          f"{worst:.3e}; {n_scaled} ill-conditioned L stated against their scale, worst rel err "
+          f"{worst_scaled[0]:.3e} at kappa {worst_scaled[1]:.0f} (sequence {worst_scaled[2]}); "
+          f"every gradient at the stated tolerance")
+
+
+def test_m1024_full_size_matches_oracle(c4, c4_oracle):
+    """The whole bench workload (1e7 events, M=1024), element by element."""
+    p = c4
+    got = gpu_run(p)
+    assert np.isfinite(got["ll"]) and all(np.all(np.isfinite(got[k]))
+                                          for k in ("dmu", "dalpha", "dbeta"))
+    # Euler identity: sum mu dmu + sum alpha dalpha = N - Lambda(T) (a check that needs no
+    # oracle), with the compensator Lambda(T) in FP64 from its closed form
+    mu, al, be = f32(p.mu), f32(p.alpha), f32(p.beta)[0]
+    colsum = al.sum(axis=0)
+    comp = p.T * mu.sum() + float(np.sum(colsum[p.c] * -np.expm1(-be * (p.T - p.t))))
+    lhs = float(np.dot(mu, got["dmu"]) + np.sum(al * got["dalpha"]))
+    scale = float(np.dot(mu, np.abs(got["dmu"] + p.T)) + p.T * mu.sum() + p.N)
+    print(f"M=1024 full: Euler residual {abs(lhs - (p.N - comp)) / scale:.3e} of its scale")
+    assert abs(lhs - (p.N - comp)) <= 1e-4 * scale
+    ref = c4_oracle.get()
+    _report("M=1024 full 1e7", got, ref)
+    assert_close(got, ref, what="M=1024 full 1e7")

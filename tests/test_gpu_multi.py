@@ -3,9 +3,9 @@ against the FP64 oracle of several kernels, at the stated tolerances (relative L
 <= 1e-6, max-norm relative gradient error <= 1e-4 per block).
 
 The log-likelihood and the decay gradient of each kernel are differences of large sums
-that nearly cancel at the simulating parameters; as for one kernel, they also pass when
-their error is at most 1e-7 of their conditioning scale (the oracle's sum of magnitudes
-of their terms, oracle.condition_multi), and the test prints kappa."""
+that nearly cancel at the simulating parameters; the tests print their conditioning
+(kappa = the oracle's sum of magnitudes of their terms over the result,
+oracle.condition_multi) for information; the tolerances are the stated ones."""
 import numpy as np
 import pytest
 
@@ -53,7 +53,9 @@ def _check(p, got, what):
     ref = _oracle(p)
     ref = dict(ref, dbeta=ref["dbeta"].sum(axis=1))      # one decay per kernel
     ll_scale, dbeta_scale = _scales(p)
-    assert_close(got, ref, what=what, ll_scale=ll_scale, dbeta_scale=dbeta_scale)
+    print(f"{what}: kappa of L {ll_scale / abs(ref['ll']):.0f}, of each dbeta "
+          f"{np.round(dbeta_scale / np.abs(ref['dbeta']))} (information only)")
+    assert_close(got, ref, what=what)
 
 
 @pytest.mark.parametrize("m,n,k,chunk,seed", [(8, 3000, 2, 64, 51), (5, 2500, 3, 0, 52),
