@@ -80,13 +80,24 @@ typedef struct {
     int32_t beta_shared;  /* 1: beta[0] is one decay shared by all sources; 0: beta[M]        */
     int32_t chunk;        /* events per scan chunk; 0 = library default                        */
     int32_t validate;     /* 1: run the device input checks (default); 0: trust the inputs      */
-    int32_t path;         /* 0: automatic; 1: state-walk kernels; 2: chunk-GEMM kernels
-                             (shared decay only).  Both give the same result within rounding.  */
+    int32_t path;         /* 0: automatic; 1: state-walk kernels (M <= 64 with the gradient,
+                             256 without); 2: chunk-GEMM kernels (shared decay, one sequence);
+                             3: mark-major walk (one sequence, one kernel; reads alpha through
+                             its support, see `support`).  Automatic: M <= 64 (256) -> 1, else
+                             shared decay -> 2, per-source decays -> 3.  Every path gives the
+                             same result within rounding.                                      */
     int32_t kernels;      /* decay kernels K: 0 or 1 = one kernel; 2..4 = several (see above)   */
+    int32_t support;      /* 1: the gradient with respect to alpha is taken on alpha's support,
+                             the entries alpha[i][j] != 0 (the interactions the model has): the
+                             other entries of d_alpha are 0, every other output is unchanged.
+                             0 (default): d_alpha in every entry.  Path 3 needs it for M > 128
+                             (its rows of up to 128 support entries are checked on the device:
+                             a longer row sets HAWKES_ERR_UNSUPPORTED in the status word).      */
 } hawkes_opts;
 
 /* Default options: per-source decay, default chunk, validation on, automatic path, one
- * decay kernel. */
+ * decay kernel, dense alpha gradient.  On path 3 `chunk` is the segment length in events
+ * (rounded up to whole tiles of 16,384 events; 0 = chosen by the library). */
 hawkes_opts hawkes_default_opts(void);
 
 /* Bytes of device workspace needed by a call on N events (all sequences together),
@@ -224,6 +235,15 @@ const int64_t* hawkes_mark_counts(void* workspace);
  *                 mark / P, index in the chunk); word 3 of slot r of a chunk starting at event
  *                 s0 (slot s0 + r) is (index in the chunk << 16) | (mark / P)
  *   chunk         C, events per chunk;  mark_blocks  P (chunk-GEMM path), else 0.
+ *   support_row_ptr [M+1] int32, support_col [entries] int32 (mark-major path): the support
+ *                 of alpha (every entry unless opts->support), row by row in column order
+ *   mark_start    [segments*M+1] int32 (mark-major path): first sorted slot of each
+ *                 (segment, mark); segment s covers events [s L, min((s+1) L, N)),
+ *                 L = segment_events
+ *   mark_slots    [N][4] uint32 (mark-major path): the events in (segment, mark, index)
+ *                 order; words 0 and 1 are the FP32 bit patterns of hi = fp32(d) and
+ *                 lo = fp32(d - hi), d = t - (time of the segment's first event) in FP64;
+ *                 word 2 the event index, word 3 its mark.
  * Returns HAWKES_ERR_INVALID_ARG for a null workspace or output, or the status that
  * hawkes_workspace_size's configuration check gives. */
 typedef struct {
@@ -234,6 +254,13 @@ typedef struct {
     const uint32_t* bucket_slots;
     int32_t chunk;
     int32_t mark_blocks;
+    const int32_t* support_row_ptr;
+    const int32_t* support_col;
+    const int32_t* mark_start;
+    const uint32_t* mark_slots;
+    int64_t segment_events;
+    int32_t segments;
+    int32_t reserved;
 } hawkes_tables;
 hawkes_status hawkes_integer_tables(void* workspace, int64_t N, int32_t M, int32_t B,
                                     int32_t grad, const hawkes_opts* opts, hawkes_tables* out);

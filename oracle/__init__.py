@@ -24,6 +24,13 @@ What pins each function (see ``tests/test_oracle_pins.py``):
     intensity against the brute-force double sum over kernels and pairs; two kernels
     with one decay equal one kernel with the summed matrix; central finite differences;
     quadrature of the compensator.
+  * ``loglik_grad_support`` (lazy per-component form, gradient on alpha's support): equals
+    ``loglik_grad`` on L, dmu, dbeta and the support entries of dalpha for sparse alpha,
+    and in every entry for a fully supported alpha; L against the brute-force intensity
+    and the closed-form compensator; ties and times near 1e7.
+  * ``chunk_table``, ``bucket_order`` (integer passes): numpy counting and stable sorting.
+  * ``condition``: a brute-force double sum with distinct per-source decays, and planted
+    source/target slips that it rejects.
   * ``condition_multi``: equals ``condition`` at K = 1; a brute-force double sum over
     kernels and event pairs; bounds every term it sums (|dbeta| <= its scale).
 """
@@ -77,7 +84,13 @@ def _load():
             lib.oracle_loglik_grad_varlen.argtypes = [p, p, p, i32, p, i32, p, p, p, p, p, p, p]
             lib.oracle_mark_counts.argtypes = [i64, p, i32, p]
             lib.oracle_condition.argtypes = [i64, p, p, d, i32, p, p, p, p, p]
+            lib.oracle_loglik_grad_support.argtypes = [i64, p, p, d, i32, p, p, p, p, p, p, p]
+            lib.oracle_loglik_grad_support.restype = ctypes.c_int
             lib.oracle_chunk_table.argtypes = [i32, p, i32, p, p]
+            lib.oracle_support_rows.argtypes = [i32, p, i32, p, p]
+            lib.oracle_support_rows.restype = ctypes.c_int
+            lib.oracle_mark_sort.argtypes = [i64, p, i32, i64, p, p]
+            lib.oracle_mark_sort.restype = ctypes.c_int
             lib.oracle_chunk_table.restype = ctypes.c_int
             lib.oracle_bucket_order.argtypes = [i64, p, i32, i32, i32, p, p]
             lib.oracle_bucket_order.restype = ctypes.c_int
@@ -196,6 +209,20 @@ def mark_counts(c, M):
     return out
 
 
+def loglik_grad_support(t, c, T, mu, alpha, beta):
+    """L and gradients by the lazy per-component form (cost per event: the nonzeros of its
+    row of alpha).  dalpha is the gradient on alpha's support (alpha != 0), 0 elsewhere;
+    L, dmu and dbeta are exact for any alpha."""
+    t, c, mu, alpha, beta, M = _prep(t, c, mu, alpha, beta)
+    ll, dmu, dal, dbe = np.zeros(1), np.zeros(M), np.zeros((M, M)), np.zeros(M)
+    rc = _load().oracle_loglik_grad_support(t.shape[0], _ptr(t), _ptr(c), float(T), M, _ptr(mu),
+                                            _ptr(alpha), _ptr(beta), _ptr(ll), _ptr(dmu),
+                                            _ptr(dal), _ptr(dbe))
+    if rc:
+        raise OracleError(rc)
+    return {"ll": float(ll[0]), "dmu": dmu, "dalpha": dal, "dbeta": dbe}
+
+
 def chunk_table(offsets, C):
     """(chunk_base [B+1] int64, chunk_seq [chunks] int32) of sequences cut into chunks of C."""
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -222,6 +249,33 @@ def bucket_order(c, M, C, P):
     if rc:
         raise OracleError(rc)
     return bs[:nb], order[:N]
+
+
+def support_rows(alpha, all_entries=False):
+    """(row_ptr [M+1], col [entries]) of alpha's support (alpha != 0, or every entry)."""
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    M = alpha.shape[0]
+    row_ptr = np.zeros(M + 1, dtype=np.int32)
+    col = np.zeros(max(M * M, 1), dtype=np.int32)
+    rc = _load().oracle_support_rows(M, _ptr(alpha), int(bool(all_entries)), _ptr(row_ptr),
+                                     _ptr(col))
+    if rc:
+        raise OracleError(rc)
+    return row_ptr, col[:row_ptr[M]]
+
+
+def mark_sort(c, M, L):
+    """(start [nseg*M + 1], order [N]) of the events ordered by (segment of L events, mark,
+    index)."""
+    c = np.ascontiguousarray(c, dtype=np.int32)
+    N = c.shape[0]
+    nseg = (N + L - 1) // L
+    start = np.zeros(nseg * M + 1, dtype=np.int32)
+    order = np.zeros(max(N, 1), dtype=np.int32)
+    rc = _load().oracle_mark_sort(N, _ptr(c), int(M), int(L), _ptr(start), _ptr(order))
+    if rc:
+        raise OracleError(rc)
+    return start, order[:N]
 
 
 def condition(t, c, T, mu, alpha, beta):

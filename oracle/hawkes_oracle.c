@@ -369,6 +369,105 @@ int oracle_mark_counts(int64_t N, const int32_t* c, int32_t M, int64_t* counts)
     return OR_OK;
 }
 
+/* Lazy per-component form for a sparse alpha, with the gradient on alpha's support.
+ *
+ * The same model and results as oracle_loglik_grad (paper, Section 2, Eq.
+ * hawkes_excitation with one decay per source; Eq. general_hawkes_likelihood; Appendix B,
+ * Eqs. grad_mu, grad_alpha, grad_gamma), computed so that an event costs O(nonzeros of its
+ * row of alpha) instead of O(M): component j of the source-indexed state is kept only as
+ * its value S_j, G_j just after the last event of mark j (at time last_j), and decayed to
+ * the time t it is read at:
+ *     S_j(t) = S_j e^{-beta_j (t - last_j)},  G_j(t) = e^{-beta_j (t - last_j)} (G_j + (t - last_j) S_j),
+ * the closed form of the recurrence S_k = D_k (S_{k-1} + e_{c_{k-1}}) between two events of
+ * mark j.  An event of mark i reads the components j with alpha[i][j] != 0 only (the others
+ * add nothing to its intensity or to dL/dbeta_j), and then adds its own jump to S_i.
+ *   ll, dmu [M], dbeta [M]: as oracle_loglik_grad (exact for any alpha).
+ *   dalpha [M*M]: dL/dalpha_ij for the entries with alpha[i][j] != 0 (the support: the
+ *                 interactions the model has), 0 for the entries outside it.
+ * Ties follow index order, as in oracle_loglik_grad (dt = 0 gives weight 1). */
+int oracle_loglik_grad_support(int64_t N, const double* t, const int32_t* c, double T,
+                               int32_t M, const double* mu, const double* alpha,
+                               const double* beta, double* ll, double* dmu, double* dalpha,
+                               double* dbeta)
+{
+    int rc = check_inputs(N, t, c, T, M, mu, alpha, beta);
+    if (rc) return rc;
+    int64_t* rowp = calloc((size_t)M + 1, sizeof(int64_t));
+    double *S = calloc((size_t)M, sizeof(double)), *G = calloc((size_t)M, sizeof(double));
+    double *last = calloc((size_t)M, sizeof(double)), *E = calloc((size_t)M, sizeof(double));
+    double *F = calloc((size_t)M, sizeof(double)), *xs = calloc((size_t)M, sizeof(double));
+    double *xg = calloc((size_t)M, sizeof(double));
+    if (!rowp || !S || !G || !last || !E || !F || !xs || !xg) { rc = OR_INVALID; goto done; }
+    int64_t nnz = 0;
+    for (int32_t i = 0; i < M; ++i) {
+        rowp[i] = nnz;
+        for (int32_t j = 0; j < M; ++j) nnz += alpha[(size_t)i * M + j] != 0.0;
+    }
+    rowp[M] = nnz;
+    int32_t* col = malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!col) { rc = OR_INVALID; goto done; }
+    for (int32_t i = 0, e = 0; i < M; ++i)
+        for (int32_t j = 0; j < M; ++j)
+            if (alpha[(size_t)i * M + j] != 0.0) col[e++] = j;
+    memset(dmu, 0, sizeof(double) * (size_t)M);
+    memset(dalpha, 0, sizeof(double) * (size_t)M * M);
+    memset(dbeta, 0, sizeof(double) * (size_t)M);
+    double logsum = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+        const int32_t i = c[k];
+        const double* arow = alpha + (size_t)i * M;
+        double lk = mu[i];
+        for (int64_t e = rowp[i]; e < rowp[i + 1]; ++e) {       /* read the row's components */
+            const int32_t j = col[e];
+            const double dt = t[k] - last[j];
+            const double d = exp(-beta[j] * dt);
+            xs[e - rowp[i]] = S[j] * d;
+            xg[e - rowp[i]] = d * (G[j] + dt * S[j]);
+            lk += arow[j] * beta[j] * xs[e - rowp[i]];
+        }
+        if (!(lk > 0.0)) { rc = OR_NONPOS; break; }
+        logsum += log(lk);
+        const double w = 1.0 / lk;
+        dmu[i] += w;
+        for (int64_t e = rowp[i]; e < rowp[i + 1]; ++e) {
+            const int32_t j = col[e];
+            dalpha[(size_t)i * M + j] += w * xs[e - rowp[i]];
+            dbeta[j] += w * arow[j] * (xs[e - rowp[i]] - beta[j] * xg[e - rowp[i]]);
+        }
+        {                                                        /* the event's own jump */
+            const double dt = t[k] - last[i];
+            const double d = exp(-beta[i] * dt);
+            G[i] = d * (G[i] + dt * S[i]);
+            S[i] = d * S[i] + 1.0;
+            last[i] = t[k];
+        }
+        const double x = T - t[k];
+        E[i] += -expm1(-beta[i] * x);
+        F[i] += x * exp(-beta[i] * x);
+    }
+    if (rc == OR_OK) {
+        double summu = 0.0, comp = 0.0;
+        for (int32_t r = 0; r < M; ++r) summu += mu[r];
+        for (int32_t j = 0; j < M; ++j) {
+            double cs = 0.0;
+            for (int32_t r = 0; r < M; ++r) cs += alpha[(size_t)r * M + j];
+            comp += cs * E[j];
+            dbeta[j] -= cs * F[j];
+        }
+        *ll = logsum - T * summu - comp;
+        for (int32_t r = 0; r < M; ++r) dmu[r] -= T;
+        for (int32_t r = 0; r < M; ++r)
+            for (int64_t e = rowp[r]; e < rowp[r + 1]; ++e) {
+                const int32_t j = col[e];
+                dalpha[(size_t)r * M + j] = beta[j] * dalpha[(size_t)r * M + j] - E[j];
+            }
+    }
+    free(col);
+done:
+    free(rowp); free(S); free(G); free(last); free(E); free(F); free(xs); free(xg);
+    return rc;
+}
+
 /* Integer pass: the chunk table of B sequences cut into chunks of C consecutive
  * events (paper, Section 3.3: the stream is processed in contiguous batches, each
  * depending on the earlier ones only through one carried state).  Sequence s owns
@@ -421,6 +520,44 @@ int oracle_bucket_order(int64_t N, const int32_t* c, int32_t M, int32_t C, int32
         if (r != (int32_t)(s1 - s0)) return OR_MARK;
     }
     return OR_OK;
+}
+
+/* Integer pass: the support of alpha row by row, in column order: the entries with
+ * alpha[i][j] != 0, or every entry when `all` is set.  row_ptr [M+1]; col holds row_ptr[M]
+ * entries (at most M*M). */
+int oracle_support_rows(int32_t M, const double* alpha, int32_t all, int32_t* row_ptr,
+                        int32_t* col)
+{
+    if (M <= 0) return OR_INVALID;
+    int32_t e = 0;
+    for (int32_t i = 0; i < M; ++i) {
+        row_ptr[i] = e;
+        for (int32_t j = 0; j < M; ++j)
+            if (all || alpha[(size_t)i * M + j] != 0.0) col[e++] = j;
+    }
+    row_ptr[M] = e;
+    return OR_OK;
+}
+
+/* Integer pass: the events cut into segments of L consecutive events and ordered by
+ * (segment, mark, index).  start [nseg*M + 1]: the first position of each (segment, mark)
+ * in that order (start[nseg*M] = N); order [N]: the index of the event at each position. */
+int oracle_mark_sort(int64_t N, const int32_t* c, int32_t M, int64_t L, int32_t* start,
+                     int32_t* order)
+{
+    if (N < 0 || M <= 0 || L <= 0) return OR_INVALID;
+    int64_t nseg = N / L + (N % L != 0 ? 1 : 0);
+    int64_t r = 0;
+    for (int64_t s = 0; s < nseg; ++s) {
+        int64_t s0 = s * L, s1 = s0 + L < N ? s0 + L : N;
+        for (int32_t m = 0; m < M; ++m) {
+            start[s * M + m] = (int32_t)r;
+            for (int64_t k = s0; k < s1; ++k)
+                if (c[k] == m) order[r++] = (int32_t)k;
+        }
+    }
+    start[nseg * M] = (int32_t)r;
+    return r == N ? OR_OK : OR_MARK;
 }
 
 /* Conditioning scales of the results (for stating errors of near-zero results):

@@ -38,14 +38,17 @@ EXPORTED = (
 class HawkesOpts(ctypes.Structure):
     _fields_ = [("beta_shared", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("kernels", ctypes.c_int32)]
+                ("kernels", ctypes.c_int32), ("support", ctypes.c_int32)]
 
 
 class HawkesTables(ctypes.Structure):
     _fields_ = [("mark_counts", ctypes.c_void_p), ("chunk_base", ctypes.c_void_p),
                 ("chunk_seq", ctypes.c_void_p), ("bucket_start", ctypes.c_void_p),
                 ("bucket_slots", ctypes.c_void_p), ("chunk", ctypes.c_int32),
-                ("mark_blocks", ctypes.c_int32)]
+                ("mark_blocks", ctypes.c_int32), ("support_row_ptr", ctypes.c_void_p),
+                ("support_col", ctypes.c_void_p), ("mark_start", ctypes.c_void_p),
+                ("mark_slots", ctypes.c_void_p), ("segment_events", ctypes.c_int64),
+                ("segments", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class HawkesError(RuntimeError):
@@ -117,9 +120,9 @@ def lib():
 
 
 def make_opts(beta_shared: bool, chunk: int = 0, validate: bool = True, path: int = 0,
-              kernels: int = 1):
+              kernels: int = 1, support: bool = False):
     return HawkesOpts(int(bool(beta_shared)), int(chunk), int(bool(validate)), int(path),
-                      int(kernels))
+                      int(kernels), int(bool(support)))
 
 
 def _check(rc: int, where: str):

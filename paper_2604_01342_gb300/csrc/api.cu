@@ -27,7 +27,8 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr int kDefaultChunkWalk = 128;
 constexpr int kDefaultChunkGemm = 192;
 
-enum Path { PATH_WALK = 1, PATH_GEMM = 2 };
+enum Path { PATH_WALK = 1, PATH_GEMM = 2, PATH_MARKS = 3 };
+constexpr int kMarksPrepChunk = 4096;   // chunks of the validation pass on the mark-major path
 
 struct Plan {
     int path;
@@ -39,6 +40,10 @@ struct Plan {
         off_grp_dt, off_grp_reset, off_seg_comp, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
         off_dal_gemm, off_al_p, off_S_p, off_G_p, off_Wt_p, off_St_p, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf, off_delta, off_Dspan, off_Tmt,
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
+    // mark-major walk
+    size_t off_rowptr, off_supcol, off_supval, off_tcnt, off_segoff, off_segt, off_segf;
+    int64_t seg_len;
+    int nseg, ntiles, seg_tiles, tile_warps;
     int64_t ldk, ldt, nbp;
     int dal_parts_max;
     int K;                 // decay kernels (one workspace slice each)
@@ -52,18 +57,33 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     const int shared = o ? o->beta_shared : 0;
     int path = o ? o->path : 0;
     const int K = (o && o->kernels > 1) ? o->kernels : 1;
+    const int support = o ? o->support : 0;
     if (K > hk::kMaxKernels) return HAWKES_ERR_INVALID_ARG;
     if (K > 1) {
         // several kernels, each with one shared decay: chunk-GEMM path, one sequence
         if (!shared || B != 1 || path == PATH_WALK) return HAWKES_ERR_UNSUPPORTED;
         path = PATH_GEMM;
     }
-    if (path == 0) path = (shared && M > hk::walk_max_m(grad)) ? PATH_GEMM : PATH_WALK;
+    if (path == 0) {
+        if (M <= hk::walk_max_m(grad)) path = PATH_WALK;
+        else path = shared ? PATH_GEMM : PATH_MARKS;
+    }
     if (path == PATH_WALK && M > hk::walk_max_m(grad)) return HAWKES_ERR_UNSUPPORTED;
     if (path == PATH_GEMM && (!shared || B != 1)) return HAWKES_ERR_UNSUPPORTED;
-    if (path != PATH_WALK && path != PATH_GEMM) return HAWKES_ERR_INVALID_ARG;
-    int C = (o && o->chunk > 0) ? o->chunk : (path == PATH_WALK ? kDefaultChunkWalk
-                                                                : kDefaultChunkGemm);
+    if (path == PATH_MARKS) {
+        // one sequence, one kernel; dense rows must fit the walk's lane groups (the rows of a
+        // support are checked on the device); slots and indices are int32
+        if (B != 1 || K > 1) return HAWKES_ERR_UNSUPPORTED;
+        if (!support && M > hk::marks_row_max()) return HAWKES_ERR_UNSUPPORTED;
+        if (N >= ((int64_t)1 << 31) - hk::marks_tile_events() || M > 32768)
+            return HAWKES_ERR_UNSUPPORTED;
+        if (o && o->chunk < 0) return HAWKES_ERR_INVALID_ARG;
+    }
+    if (path != PATH_WALK && path != PATH_GEMM && path != PATH_MARKS) return HAWKES_ERR_INVALID_ARG;
+    int C = path == PATH_MARKS ? kMarksPrepChunk
+                               : (o && o->chunk > 0) ? o->chunk
+                                                     : (path == PATH_WALK ? kDefaultChunkWalk
+                                                                          : kDefaultChunkGemm);
     if (C < 1 || C > 4096) return HAWKES_ERR_INVALID_ARG;
     if (path == PATH_GEMM && C > 1024) return HAWKES_ERR_INVALID_ARG;
     if (path == PATH_GEMM && M > 128 * 128) return HAWKES_ERR_UNSUPPORTED;
@@ -81,13 +101,40 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->P = (int)P;
     }
     pl->nb_max = (N + C - 1) / C + B;
+    pl->off_rowptr = pl->off_supcol = pl->off_supval = pl->off_tcnt = pl->off_segoff = 0;
+    pl->off_segt = pl->off_segf = 0;
+    pl->seg_len = 0;
+    pl->nseg = pl->ntiles = pl->seg_tiles = pl->tile_warps = 0;
+    if (path == PATH_MARKS) {
+        // tiles of the sort, and segments of whole tiles: enough (segment, mark) work items for
+        // about 64 warps per SM, at most 64 tiles (1M events) per segment, or the caller's
+        // segment length (opts->chunk events, rounded up to whole tiles)
+        const int64_t TE = hk::marks_tile_events();
+        const int64_t ntiles = (N + TE - 1) / TE;
+        int64_t tps;
+        if (o && o->chunk > 0) {
+            tps = ((int64_t)o->chunk + TE - 1) / TE;
+        } else {
+            const int64_t want_seg = (152 * 64 + (int64_t)M - 1) / M;
+            tps = (ntiles + want_seg - 1) / want_seg;
+            if (tps > 64) tps = 64;
+        }
+        if (tps < 1) tps = 1;
+        pl->ntiles = (int)ntiles;
+        pl->seg_tiles = (int)tps;
+        pl->nseg = (int)((ntiles + tps - 1) / tps);
+        pl->seg_len = tps * TE;
+        int wpb = (int)((200 * 1024) / (4 * (int64_t)M));
+        pl->tile_warps = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
+    }
     int64_t target_groups = 2432;  // ~16 blocks of 128 threads per SM on 152 SMs
     int64_t gc = (pl->nb_max + target_groups - 1) / target_groups;
     if (gc < 1) gc = 1;
     if (gc > 64) gc = 64;
     pl->Gc = (int)gc;
     pl->ng_max = (pl->nb_max + gc - 1) / gc;
-    const size_t nbM = (size_t)pl->nb_max * M, ngM = (size_t)pl->ng_max * M;
+    const size_t nbM = (size_t)(path == PATH_MARKS ? pl->nseg : pl->nb_max) * M;
+    const size_t ngM = (size_t)(path == PATH_MARKS ? 0 : pl->ng_max) * M;
     size_t o_ = align_up(sizeof(hk::WsHeader));
     auto take = [&](size_t bytes) { size_t at = o_; o_ = align_up(o_ + bytes); return at; };
     pl->off_counts = take(sizeof(int64_t) * (size_t)B * M);
@@ -99,7 +146,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->off_grp_g = grad ? take(sizeof(float) * ngM) : 0;
     pl->off_grp_dt = take(sizeof(double) * (size_t)pl->ng_max);
     pl->off_grp_reset = take(sizeof(int32_t) * (size_t)pl->ng_max);
-    pl->off_seg_comp = take(sizeof(float) * 5 * (size_t)hk::kCarrySegments * M);
+    pl->off_seg_comp = path == PATH_MARKS ? 0 : take(sizeof(float) * 5 * (size_t)hk::kCarrySegments * M);
     pl->off_carry_S = take(sizeof(float) * ngM);
     pl->off_carry_G = grad ? take(sizeof(float) * ngM) : 0;
     size_t n_acc = (size_t)B * (1 + 4 * (size_t)M) + (grad ? (size_t)B * M * M : 0);
@@ -139,7 +186,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_delta = take(sizeof(float) * (size_t)(N > 0 ? N : 1));
         pl->off_Dspan = take(sizeof(float) * (size_t)pl->nb_max);
         pl->off_Tmt = take(sizeof(float) * (size_t)pl->nb_max);
-        pl->off_cen = take(sizeof(float) * (6 * (size_t)M + 1));
+        pl->off_cen = take(sizeof(float) * ((4 + 2 * 32) * (size_t)M + 1));   // 32 = kCentreSlices
         pl->off_wsum = take(sizeof(double) * (size_t)M);
         pl->off_Y = take(sizeof(float) * nbM);
         pl->off_isc = take(sizeof(float) * (3 * (size_t)M + 2 * (size_t)pl->nb_max));
@@ -154,6 +201,17 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
             pl->off_Wt_p = take(h * (size_t)M * pl->ldt);
             pl->off_St_p = take(h * (size_t)M * pl->ldt);
         }
+    }
+    if (path == PATH_MARKS) {
+        const size_t nnz_max = (size_t)M * M;
+        pl->off_rowptr = take(sizeof(int32_t) * ((size_t)M + 1));
+        pl->off_supcol = take(sizeof(int32_t) * nnz_max);
+        pl->off_supval = take(sizeof(float) * nnz_max);
+        pl->off_tcnt = take(sizeof(int32_t) * (size_t)pl->ntiles * M);
+        pl->off_segoff = take(sizeof(int32_t) * ((size_t)pl->nseg * M + 1));
+        pl->off_segt = take(sizeof(double) * 3 * (size_t)pl->nseg);
+        pl->off_segf = take(sizeof(float) * 4 * (size_t)pl->nseg);
+        pl->off_recs = take(16 * (size_t)(N > 0 ? N : 1));
     }
     pl->scratch_off = path == PATH_GEMM ? take(sizeof(float) * ((size_t)M + 2)) : 0;
     pl->K = K;
@@ -234,6 +292,17 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.Gc = pl.Gc;
     p.nb_max = pl.nb_max;
     p.ng_max = pl.ng_max;
+    p.row_ptr = at<int32_t>(ws, pl.off_rowptr);
+    p.sup_col = at<int32_t>(ws, pl.off_supcol);
+    p.sup_val = at<float>(ws, pl.off_supval);
+    p.tile_cnt = at<int32_t>(ws, pl.off_tcnt);
+    p.seg_off = at<int32_t>(ws, pl.off_segoff);
+    p.seg_time = at<double>(ws, pl.off_segt);
+    p.seg_f = at<float>(ws, pl.off_segf);
+    p.nseg = pl.nseg;
+    p.ntiles = pl.ntiles;
+    p.seg_tiles = pl.seg_tiles;
+    p.tile_warps = pl.tile_warps;
 }
 
 int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {
@@ -249,14 +318,19 @@ int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStr
         g_prof.n = 0;
         cudaEventRecord(g_prof.ev[0], s);
     }
+    p.support = o ? o->support : 0;
     cudaError_t err = hk::launch_prepare(p, s, validate, &nl);
-    if (err == cudaSuccess) err = hk::launch_scan(p, s, &nl);
     if (err == cudaSuccess) {
-        if (pl.path == PATH_WALK) {
-            err = hk::launch_walk(p, s, &nl);
-            if (err == cudaSuccess) err = hk::launch_finalize(p, s, &nl);
+        if (pl.path == PATH_MARKS) {
+            err = hk::launch_marks(p, pl.seg_len, s, &nl);
         } else {
-            err = hk::launch_gemm_path(p, s, &nl);
+            err = hk::launch_scan(p, s, &nl);
+            if (err == cudaSuccess && pl.path == PATH_WALK) {
+                err = hk::launch_walk(p, s, &nl);
+                if (err == cudaSuccess) err = hk::launch_finalize(p, s, &nl);
+            } else if (err == cudaSuccess) {
+                err = hk::launch_gemm_path(p, s, &nl);
+            }
         }
     }
     g_last_launches = nl;
@@ -291,6 +365,7 @@ int run_multi(hk::Problem& base, const hawkes_opts* o, void* ws, size_t ws_bytes
         p[q].alpha = base.alpha + (size_t)q * M * M;
         p[q].beta = base.beta + q;
         p[q].validated = validate ? 1 : 0;
+        p[q].support = o ? o->support : 0;
         if (base.grad) {
             p[q].d_alpha = base.d_alpha + (size_t)q * M * M;
             p[q].d_beta = base.d_beta + q;
@@ -368,6 +443,7 @@ hawkes_opts hawkes_default_opts(void) {
     o.validate = 1;
     o.path = 0;
     o.kernels = 1;
+    o.support = 0;
     return o;
 }
 
@@ -618,10 +694,18 @@ hawkes_status hawkes_integer_tables(void* workspace, int64_t N, int32_t M, int32
     out->mark_counts = at<int64_t>(workspace, pl.off_counts);
     out->chunk_base = at<int64_t>(workspace, pl.off_chunk_base);
     out->chunk_seq = at<int32_t>(workspace, pl.off_chunk_seq);
-    out->bucket_start = pl.path == PATH_GEMM ? at<int32_t>(workspace, pl.off_bstart) : nullptr;
-    out->bucket_slots = pl.path == PATH_GEMM ? at<uint32_t>(workspace, pl.off_recs) : nullptr;
+    const bool gemm = pl.path == PATH_GEMM, marks = pl.path == PATH_MARKS;
+    out->bucket_start = gemm ? at<int32_t>(workspace, pl.off_bstart) : nullptr;
+    out->bucket_slots = gemm ? at<uint32_t>(workspace, pl.off_recs) : nullptr;
     out->chunk = pl.C;
-    out->mark_blocks = pl.path == PATH_GEMM ? pl.P : 0;
+    out->mark_blocks = gemm ? pl.P : 0;
+    out->support_row_ptr = marks ? at<int32_t>(workspace, pl.off_rowptr) : nullptr;
+    out->support_col = marks ? at<int32_t>(workspace, pl.off_supcol) : nullptr;
+    out->mark_start = marks ? at<int32_t>(workspace, pl.off_segoff) : nullptr;
+    out->mark_slots = marks ? at<uint32_t>(workspace, pl.off_recs) : nullptr;
+    out->segment_events = marks ? pl.seg_len : 0;
+    out->segments = marks ? pl.nseg : 0;
+    out->reserved = 0;
     return HAWKES_OK;
 }
 

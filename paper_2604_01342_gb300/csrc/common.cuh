@@ -113,11 +113,25 @@ struct Problem {
     float* bias_Y;           // [M] alpha . cen_S  (FP64-accumulated)
     float* cen_Z;            // [M] mean of (S^_b - beta G^_b)[j] over the sampled chunks
     float* bias_Z;           // [M] alpha . cen_Z  (FP64-accumulated)
-    float* cen_acc;          // [2M + 1] column sums of the sampled rows, then their number
+    float* cen_acc;          // [32][2M] column sums of the sampled rows per row slice, then
+                             // the number of sampled rows
     double* wsum_acc;        // [M] sum_b W[b][i]
     int64_t ldk;             // 64 ceil(M / 32): halves per paired row of K = M elements
     int64_t ldt;             // 64 ceil(nbp / 32): halves per paired row of K = nbp elements
     int64_t nbp;             // nb_max rounded up to 8
+    // mark-major walk (one decay per source, large M)
+    int32_t support;         // 1: dalpha on alpha's support only (entries alpha == 0 get 0)
+    int32_t* row_ptr;        // [M+1] support rows of alpha
+    int32_t* sup_col;        // [nnz] column of each support entry, by row
+    float* sup_val;          // [nnz] its value
+    int32_t* tile_cnt;       // [ntiles][M] events per mark of each tile, then prefix in segment
+    int32_t* seg_off;        // [nseg*M + 1] first sorted slot of every (segment, mark)
+    double* seg_time;        // [3 nseg] first time, span to the next segment, T - first time
+    float* seg_f;            // [4 nseg] the span and T - first time as FP32 (hi, lo) pairs
+    int32_t nseg;            // segments
+    int32_t ntiles;          // tiles of the sort
+    int32_t seg_tiles;       // tiles per segment
+    int32_t tile_warps;      // tiles (warps) per block of the sort kernels
     // outputs
     double* out_ll;          // [B]
     float* d_mu;
@@ -249,6 +263,11 @@ cudaError_t launch_epilogue_multi(const Problem& p0, const MultiSlices& ms, cuda
 cudaError_t launch_finalize_multi(const Problem& p0, const MultiSlices& ms, cudaStream_t s,
                                   int* nlaunch);
 cudaError_t launch_finalize(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int* nlaunch);
+// the mark-major walk (marks.cu): segment length L events
+cudaError_t launch_marks(const Problem& p, int64_t L, cudaStream_t s, int* nlaunch);
+int marks_row_max();
+int marks_tile_events();
 cudaError_t launch_slice_aggregate(const Problem& p, double t_next, float* agg_S, float* agg_G,
                                    cudaStream_t s, int* nlaunch);
 int walk_max_m(int grad);

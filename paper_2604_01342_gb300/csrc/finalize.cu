@@ -70,6 +70,8 @@ __global__ void k_finalize_vec(Problem p, const double* colsum) {
 }
 
 // dalpha for all sequences, elementwise.
+// Entries outside alpha's support are 0 when the caller asked for the gradient on the
+// support (p.support).
 // mode 0: X = dal_acc (already carries beta_j);
 // mode 1: X = beta * (dal_gemm + m_j wsum_i + sum_r part_r[i][j])  (chunk-GEMM path, one
 //         shared beta; the GEMM ran on S^ - m, so m_j sum_b W[b][i] restores the centre;
@@ -86,7 +88,8 @@ __global__ void k_finalize_alpha(Problem p, int mode) {
              e += (int64_t)gridDim.x * blockDim.x) {
             const int64_t s = e / ((int64_t)M * M), ij = e % ((int64_t)M * M);
             const int j = (int)(ij % M);
-            const double v = p.dal_acc[e] - p.E_acc[s * M + j];
+            double v = p.dal_acc[e] - p.E_acc[s * M + j];
+            if (p.support && p.alpha[e] == 0.f) v = 0.0;     // outside alpha's support
             p.d_alpha[e] = bad ? (float)nanv : (float)v;
         }
         return;
@@ -116,7 +119,8 @@ __global__ void k_finalize_alpha(Problem p, int mode) {
         const int64_t ij = (int64_t)i * M + j;
         const double x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] +
                                          (double)pairs);
-        const double v = x - p.E_acc[j];
+        double v = x - p.E_acc[j];
+        if (p.support && p.alpha[ij] == 0.f) v = 0.0;       // outside alpha's support
         p.d_alpha[ij] = bad ? (float)nanv : (float)v;
     }
 }

@@ -19,8 +19,6 @@
 
 namespace hk {
 
-cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int* nl);
-
 // Tensor-core GEMM and fp16 hi/lo splitting of row-scaled operands into paired rows
 // (tc_gemm.cu).
 cudaError_t tc_gemm_f16x3(const __half* A, int64_t lda, const __half* B, int64_t ldb, float* D,
@@ -58,8 +56,9 @@ constexpr int kCentreRows = 1024;
 constexpr int kCentreSlices = 32;     // row slices of the column sums, one block row each
 
 // Column sums of S^ and S^ - beta G^ over the sampled chunks: block (x, y) takes 256
-// columns and every kCentreSlices-th sampled row from slice y; sums into acc [2 M] (zeroed
-// before), the number of sampled rows into acc_n.
+// columns and every kCentreSlices-th sampled row from slice y, and writes its sums to
+// acc[y][2 M] (no atomics: the centres, and so the rounding of the GEMMs, are the same in
+// every call); the number of sampled rows goes to acc_n.
 __global__ void k_col_sums(Problem p, int want_z, float* acc, int* acc_n) {
     const int M = p.M;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,28 +73,37 @@ __global__ void k_col_sums(Problem p, int want_z, float* acc, int* acc_n) {
         s += v;
         if (want_z) z += v - beta * p.Ghat[b * M + j];
     }
-    if (s != 0.f) atomicAdd(&acc[j], s);
-    if (want_z && z != 0.f) atomicAdd(&acc[M + j], z);
+    acc[(int64_t)blockIdx.y * 2 * M + j] = s;
+    acc[(int64_t)blockIdx.y * 2 * M + M + j] = z;
 }
 
-// The centres cen_S, cen_Z (column means: the sums of k_col_sums over the sampled rows)
-// and bias_Y = alpha . cen_S, bias_Z = alpha . cen_Z in FP64, one warp per row of alpha.
-__global__ void k_centres(Problem p, int want_z, const float* acc, const int* acc_n) {
+// The centres cen_S, cen_Z: the column means over the sampled rows (the slices' sums added
+// in slice order), one thread per column.
+__global__ void k_centre_means(Problem p, int want_z, const float* acc, const int* acc_n) {
+    const int M = p.M;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const float inv = *acc_n > 0 ? 1.f / (float)*acc_n : 0.f;
+    float s = 0.f, z = 0.f;
+    for (int y = 0; y < kCentreSlices; ++y) {
+        s += acc[(int64_t)y * 2 * M + j];
+        z += acc[(int64_t)y * 2 * M + M + j];
+    }
+    p.cen_S[j] = s * inv;
+    if (want_z) p.cen_Z[j] = z * inv;
+}
+
+// bias_Y = alpha . cen_S and bias_Z = alpha . cen_Z in FP64, one warp per row of alpha.
+__global__ void k_centres(Problem p, int want_z) {
     const int M = p.M;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const float inv = *acc_n > 0 ? 1.f / (float)*acc_n : 0.f;
-    if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < M; j += blockDim.x) {
-            p.cen_S[j] = acc[j] * inv;
-            if (want_z) p.cen_Z[j] = acc[M + j] * inv;
-        }
     for (int i = warp; i < M; i += nwarps) {
         double y = 0.0, z = 0.0;
         for (int j = lane; j < M; j += 32) {
             const double a = (double)p.alpha[(int64_t)i * M + j];
-            y += a * (double)(acc[j] * inv);
-            if (want_z) z += a * (double)(acc[M + j] * inv);
+            y += a * (double)p.cen_S[j];
+            if (want_z) z += a * (double)p.cen_Z[j];
         }
         for (int o = 16; o >= 1; o >>= 1) {
             y += __shfl_xor_sync(HK_FULL, y, o);
@@ -694,12 +702,12 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     const int64_t M = p.M, nb = p.nb_max;
     // Y = S^ alpha^T and Z = (S^ - beta G^) alpha^T on the tensor cores (rows = chunks)
     cudaMemsetAsync(p.wsum_acc, 0, sizeof(double) * (size_t)M, s);
-    cudaMemsetAsync(p.cen_acc, 0, sizeof(float) * (2 * (size_t)M + 1), s);
-    int* acc_n = (int*)(p.cen_acc + 2 * (size_t)M);
+    int* acc_n = (int*)(p.cen_acc + 2 * (size_t)kCentreSlices * M);
     k_col_sums<<<dim3((unsigned)((M + 255) / 256), kCentreSlices), 256, 0, s>>>(p, p.grad,
                                                                               p.cen_acc, acc_n);
-    k_centres<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(p, p.grad, p.cen_acc, acc_n);
-    *nl += 2;
+    k_centre_means<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(p, p.grad, p.cen_acc, acc_n);
+    k_centres<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(p, p.grad);
+    *nl += 3;
     prof_mark(s, "centres");
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int64_t* nb_dev = p.chunk_base + p.B;   // number of chunks, on the device

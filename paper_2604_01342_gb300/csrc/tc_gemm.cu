@@ -28,9 +28,7 @@
 // (measured with TF32 operands: ~1.6e-6 after 64 of K, ~2.6e-5 after 1024), so every 64 of
 // K (two k-tiles) is accumulated into one of two TMEM banks and then promoted: eight warps
 // read the finished bank with tcgen05.ld and add it to FP32 registers while the MMAs fill
-// the other bank.  Within a group the eight small cross-product MMAs are issued before the
-// four hi x hi ones, so that the truncation of each MMA's sum happens at the small
-// products' own scale and only the last four are truncated at the scale of the result.  The output tile is staged in the (then free) stage buffers and stored as
+// the other bank.  The output tile is staged in the (then free) stage buffers and stored as
 // whole row pieces.  Every mbarrier wait is bounded; on timeout the kernel records an error
 // in the status word, waits (bounded) for its MMAs and copies, frees its tensor memory and
 // returns.
@@ -238,55 +236,39 @@ k_gemm_f16x3(const __grid_constant__ Maps maps, float* D, int64_t ldd, int Mdim,
         if (lane == 0 && KT > 0) {
             const uint32_t idesc = idesc_f16(BM, BN);
             bool ok = true;
-            for (int g = 0; g < ngroups && ok; ++g) {
-                const int i0 = g * kTilesPerGroup;
-                const int i1 = i0 + kTilesPerGroup < KT ? i0 + kTilesPerGroup : KT;
-                const int bank = g & 1;
-                if (g >= 2) {
+            for (int i = 0; i < KT; ++i) {
+                const int s = i % STAGES;
+                if (!mbar_wait_or_abort(&full[s], (uint32_t)((i / STAGES) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint8_t* st = smem + s * STAGE_BYTES;
+                const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
+                const int g = i / kTilesPerGroup, bank = g & 1;
+                const bool first_in_group = (i % kTilesPerGroup) == 0;
+                if (first_in_group && g >= 2) {
                     // the epilogue must have read this bank's previous group
                     if (!mbar_wait(&bank_empty[bank], (uint32_t)(((g >> 1) - 1) & 1))) {
                         ok = false;
                         break;
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
-                for (int i = i0; i < i1 && ok; ++i)
-                    if (!mbar_wait_or_abort(&full[i % STAGES], (uint32_t)((i / STAGES) & 1),
-                                            abort_flag))
-                        ok = false;
-                if (!ok) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t acc_t = tmem + (uint32_t)(bank * BN);
-                // The accumulator truncates each MMA's sum toward zero at its own magnitude,
-                // so the group's small cross products (hi x lo, lo x hi) go first, into the
-                // fresh bank while it is small, and the large hi x hi products last: only
-                // those (and the first of them) are truncated at the scale of the result.
-                uint32_t acc = 0u;
-                for (int i = i0; i < i1; ++i) {
-                    uint8_t* st = smem + (i % STAGES) * STAGE_BYTES;
-                    const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        // 16 fp16 = 32 bytes along the 128-byte swizzled row: the high parts
-                        // at bytes 0-63, the low parts at 64-127
-                        const uint64_t oh = (uint64_t)(kk * 32) >> 4;
-                        const uint64_t ol = (uint64_t)(64 + kk * 32) >> 4;
-                        mma_f16(acc_t, da + oh, db + ol, idesc, acc);
-                        acc = 1u;
-                        mma_f16(acc_t, da + ol, db + oh, idesc, 1u);
-                    }
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    // 16 fp16 = 32 bytes along the 128-byte swizzled row: the high parts
+                    // at bytes 0-63, the low parts at 64-127
+                    const uint64_t oh = (uint64_t)(kk * 32) >> 4;
+                    const uint64_t ol = (uint64_t)(64 + kk * 32) >> 4;
+                    const uint32_t acc0 = (!first_in_group || kk > 0) ? 1u : 0u;
+                    mma_f16(acc_t, da + oh, db + oh, idesc, acc0);
+                    mma_f16(acc_t, da + oh, db + ol, idesc, 1u);
+                    mma_f16(acc_t, da + ol, db + oh, idesc, 1u);
                 }
-                for (int i = i0; i < i1; ++i) {
-                    uint8_t* st = smem + (i % STAGES) * STAGE_BYTES;
-                    const uint64_t da = sw128_desc(st), db = sw128_desc(st + A_TILE);
-#pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t oh = (uint64_t)(kk * 32) >> 4;
-                        mma_f16(acc_t, da + oh, db + oh, idesc, 1u);
-                    }
-                }
-                mma_commit(&bank_full[bank]);
-                // the group's stages may be refilled once these MMAs are done
-                for (int i = i0; i < i1; ++i) mma_commit(&empty[i % STAGES]);
+                if ((i % kTilesPerGroup) == kTilesPerGroup - 1 || i == KT - 1) mma_commit(&bank_full[bank]);
+                mma_commit(&empty[s]);           // the stage may be refilled once these are done
             }
             if (!ok) {
                 *abort_flag = 1;

@@ -57,13 +57,15 @@ def _stream(device):
 
 
 def loglik_grad(t, c, T, mu, alpha, beta, beta_shared=None, chunk: int = 0, path: int = 0,
-                validate: bool = True, check: bool = True, grad: bool = True):
-    """L (float64 0-d) and, if ``grad``, (dmu, dalpha, dbeta) as float32 tensors."""
+                validate: bool = True, check: bool = True, grad: bool = True,
+                support: bool = False):
+    """L (float64 0-d) and, if ``grad``, (dmu, dalpha, dbeta) as float32 tensors.
+    ``support=True``: dalpha on alpha's support (entries alpha == 0 get 0)."""
     t, c, mu, alpha, beta = _prep(t, c, mu, alpha, beta)
     dev = t.device
     N, M = t.shape[0], mu.shape[0]
     shared = _shared(beta, M, beta_shared)
-    opts = _b.make_opts(shared, chunk, validate, path)
+    opts = _b.make_opts(shared, chunk, validate, path, support=support)
     nbytes = _b.hawkes_workspace_size(N, M, 1, grad, opts)
     ws = _workspace(nbytes, dev)
     out_ll = torch.empty((), dtype=torch.float64, device=dev)
@@ -192,14 +194,16 @@ class HawkesLogLik(torch.autograd.Function):
     saved gradient by grad_output (no second pass over the events)."""
 
     @staticmethod
-    def forward(ctx, t, c, T, mu, alpha, beta, beta_shared, chunk, path):
+    def forward(ctx, t, c, T, mu, alpha, beta, beta_shared, chunk, path, support):
         need = any(ctx.needs_input_grad[3:6])
         if need:
-            ll, dmu, dal, dbe = loglik_grad(t, c, T, mu, alpha, beta, beta_shared, chunk, path)
+            ll, dmu, dal, dbe = loglik_grad(t, c, T, mu, alpha, beta, beta_shared, chunk, path,
+                                            support=support)
             ctx.save_for_backward(dmu, dal, dbe)
             ctx.beta_shape = beta.shape
         else:
-            ll = loglik_grad(t, c, T, mu, alpha, beta, beta_shared, chunk, path, grad=False)
+            ll = loglik_grad(t, c, T, mu, alpha, beta, beta_shared, chunk, path, grad=False,
+                             support=support)
         return ll
 
     @staticmethod
@@ -207,7 +211,7 @@ class HawkesLogLik(torch.autograd.Function):
         dmu, dal, dbe = ctx.saved_tensors
         g32 = g.to(torch.float32)
         return (None, None, None, g32 * dmu, g32 * dal, (g32 * dbe).reshape(ctx.beta_shape),
-                None, None, None)
+                None, None, None, None)
 
 
 class HawkesLogLikVarlen(torch.autograd.Function):
@@ -233,9 +237,11 @@ class HawkesLogLikVarlen(torch.autograd.Function):
                 (gb * dbe).reshape(ctx.beta_shape), None, None, None)
 
 
-def loglik(t, c, T, mu, alpha, beta, beta_shared=None, chunk: int = 0, path: int = 0):
-    """Differentiable exact log-likelihood of one sequence (0-d float64)."""
-    return HawkesLogLik.apply(t, c, T, mu, alpha, beta, beta_shared, chunk, path)
+def loglik(t, c, T, mu, alpha, beta, beta_shared=None, chunk: int = 0, path: int = 0,
+           support: bool = False):
+    """Differentiable exact log-likelihood of one sequence (0-d float64).  ``support=True``
+    takes the gradient with respect to alpha on its support (entries alpha == 0 get 0)."""
+    return HawkesLogLik.apply(t, c, T, mu, alpha, beta, beta_shared, chunk, path, support)
 
 
 def loglik_varlen(t, c, offsets, T, mu, alpha, beta, beta_shared=None, chunk: int = 0,

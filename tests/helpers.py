@@ -34,7 +34,7 @@ def oracle_ref(p, grad=True):
     return out
 
 
-def gpu_run(p, grad=True, path=0, chunk=0, check=True, validate=True):
+def gpu_run(p, grad=True, path=0, chunk=0, check=True, validate=True, support=False):
     import torch
     from paper_2604_01342_gb300 import torch_api
     dev = torch.device("cuda")
@@ -44,7 +44,8 @@ def gpu_run(p, grad=True, path=0, chunk=0, check=True, validate=True):
     al = torch.tensor(p.alpha, dtype=torch.float32, device=dev)
     be = torch.tensor(p.beta[:1] if p.shared_beta else p.beta, dtype=torch.float32, device=dev)
     r = torch_api.loglik_grad(t, c, p.T, mu, al, be, beta_shared=p.shared_beta, chunk=chunk,
-                              path=path, check=check, grad=grad, validate=validate)
+                              path=path, check=check, grad=grad, validate=validate,
+                              support=support)
     if grad:
         ll, dmu, dal, dbe = r
         return {"ll": float(ll.item()), "dmu": dmu.cpu().numpy().astype(np.float64),

@@ -28,3 +28,27 @@ def test_bucket_order_matches_stable_sort(N, M, C, P):
         np.testing.assert_array_equal(order[b * C: b * C + cc.shape[0]], want)
         blocks = np.bincount(cc % P, minlength=P)
         np.testing.assert_array_equal(bs[b], np.concatenate([[0], np.cumsum(blocks)]))
+
+
+@pytest.mark.parametrize("M,density,all_entries", [(7, 0.3, False), (40, 0.05, False),
+                                                   (5, 0.0, False), (9, 0.5, True)])
+def test_support_rows_match_numpy(M, density, all_entries):
+    rng = np.random.default_rng(M)
+    a = rng.uniform(0.1, 1.0, (M, M)) * (rng.random((M, M)) < density)
+    row_ptr, col = oracle.support_rows(a, all_entries)
+    mask = np.ones_like(a, bool) if all_entries else a != 0
+    np.testing.assert_array_equal(row_ptr, np.concatenate([[0], np.cumsum(mask.sum(1))]))
+    np.testing.assert_array_equal(col, np.nonzero(mask)[1])
+
+
+@pytest.mark.parametrize("N,M,L", [(100, 7, 30), (1, 3, 5), (0, 4, 8), (1000, 50, 1000), (257, 1, 16)])
+def test_mark_sort_matches_stable_sort(N, M, L):
+    c = np.random.default_rng(N + 3).integers(0, M, N).astype(np.int32)
+    start, order = oracle.mark_sort(c, M, L)
+    seg = np.arange(N) // L
+    want = np.lexsort((np.arange(N), c, seg))
+    np.testing.assert_array_equal(order, want)
+    nseg = (N + L - 1) // L
+    counts = np.zeros(nseg * M, np.int64)
+    np.add.at(counts, seg * M + c, 1)
+    np.testing.assert_array_equal(start, np.concatenate([[0], np.cumsum(counts)]))
