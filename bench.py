@@ -16,8 +16,12 @@ through the host-buffer entry point (pinned inputs copied in, L and gradients
 copied out, inside the timed region).  ``roofline`` reports the dominant
 kernel's achieved rate from per-kernel CUDA events (a separate instrumented
 pass over the same steps).  ``cpu_baseline`` times the FP64 oracle on a
-bounded prefix of the same stream on one host core.
-``--impl reference`` times the oracle itself as the reference arm.
+bounded prefix of the same stream on one host core; ``precision`` compares, on
+that prefix, the CUDA path's result under each precision option (the FP64 and
+FP32 log-sums, and the FP32-times ablation) with that oracle result.
+``workload5`` times the fifth workload (one decay per source, M=4096, N=5e7) on
+the mark-major path.  ``--impl reference`` times the oracle itself as the
+reference arm.
 """
 from __future__ import annotations
 
@@ -119,7 +123,7 @@ def workload(n_events=None):
     return synth.workload(4, n_events=n_events or None)
 
 
-def time_oracle(p, n_sample=CPU_SAMPLE_EVENTS):
+def time_oracle(p, n_sample=CPU_SAMPLE_EVENTS, want_result=False):
     """The FP64 oracle as it stands on one host core, on the first n_sample events."""
     import oracle
     n = min(n_sample, p.N)
@@ -128,11 +132,97 @@ def time_oracle(p, n_sample=CPU_SAMPLE_EVENTS):
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)  # noqa: E731
     oracle.build()
     t0 = time.perf_counter()
-    oracle.loglik_grad(t, c, T, f32(p.mu), f32(p.alpha), np.full(p.M, f32(p.beta[:1])[0]))
+    res = oracle.loglik_grad(t, c, T, f32(p.mu), f32(p.alpha), np.full(p.M, f32(p.beta[:1])[0]))
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+    line = {"value": n / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
             "sample": f"first {n} events of the same stream (T = t of the last one), "
                       f"FP64 log-likelihood + gradient, single thread, {dt:.2f} s"}
+    if want_result:
+        res["dbeta"] = np.array([res["dbeta"].sum()])        # one shared decay
+        return line, res
+    return line
+
+
+def precision_report(p, dev, ref, n_sample=CPU_SAMPLE_EVENTS):
+    """Error of each precision option of the CUDA path against the FP64 oracle, per result,
+    on the oracle's sample (the first n_sample events): the default (FP64 time differences,
+    FP64 log-sum partials), Kahan-compensated FP32 and plain FP32 log-sums, and the FP32-times
+    ablation."""
+    import torch
+    from paper_2604_01342_gb300 import torch_api
+    n = min(n_sample, p.N)
+    t = torch.from_numpy(p.t[:n]).to(dev)
+    c = torch.from_numpy(p.c[:n]).to(dev)
+    mu = torch.tensor(p.mu, dtype=torch.float32, device=dev)
+    al = torch.tensor(p.alpha, dtype=torch.float32, device=dev)
+    be = torch.tensor(p.beta[:1], dtype=torch.float32, device=dev)
+    T = float(p.t[n - 1])
+    out = {"sample": f"first {n} events of the workload, against the FP64 oracle: relative L "
+                     f"error, max-norm relative error per gradient block"}
+    for name, kw in (("default (FP64 dt, FP64 log-sum)", {}),
+                     ("Kahan FP32 log-sum", {"reduce": 1}), ("plain FP32 log-sum", {"reduce": 2}),
+                     ("FP32 times (ablation)", {"fp32_times": True})):
+        r = torch_api.loglik_grad(t, c, T, mu, al, be, beta_shared=True, check=False, **kw)
+        got = [float(r[0].item())] + [x.cpu().numpy().astype(np.float64) for x in r[1:]]
+        den = lambda a: max(float(np.max(np.abs(a))), 1e-300)  # noqa: E731
+        out[name] = {"ll": abs(got[0] - ref["ll"]) / abs(ref["ll"]),
+                     "dmu": float(np.max(np.abs(got[1] - ref["dmu"]))) / den(ref["dmu"]),
+                     "dalpha": float(np.max(np.abs(got[2] - ref["dalpha"]))) / den(ref["dalpha"]),
+                     "dbeta": float(np.max(np.abs(got[3] - ref["dbeta"]))) / den(ref["dbeta"])}
+    return out
+
+
+def workload5_line(dev, steps=3):
+    """The fifth workload (M=4096, one decay per source, alpha 1% dense, N=5e7, T ~ 1e7) on
+    the mark-major path, gradient on alpha's support: events/s over `steps` calls after one
+    warm-up call (inputs resident, L2 flushed between calls)."""
+    import torch
+    from paper_2604_01342_gb300 import binding as B, synth
+    p = synth.workload(5)
+    N, M = p.N, p.M
+    opts = B.make_opts(False, 0, True, 0, support=True)
+    t = torch.from_numpy(p.t).to(dev)
+    c = torch.from_numpy(p.c).to(dev)
+    mu = torch.tensor(p.mu, dtype=torch.float32, device=dev)
+    al = torch.tensor(p.alpha, dtype=torch.float32, device=dev)
+    be = torch.tensor(p.beta, dtype=torch.float32, device=dev)
+    nb = B.hawkes_workspace_size(N, M, 1, True, opts)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    ll = torch.empty((), dtype=torch.float64, device=dev)
+    dmu = torch.empty(M, dtype=torch.float32, device=dev)
+    dal = torch.empty(M, M, dtype=torch.float32, device=dev)
+    dbe = torch.empty(M, dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    sptr = torch.cuda.current_stream(dev).cuda_stream
+
+    def call():
+        B.hawkes_loglik_grad(t.data_ptr(), c.data_ptr(), N, p.T, M, mu.data_ptr(), al.data_ptr(),
+                             be.data_ptr(), opts, ws.data_ptr(), nb, ll.data_ptr(), dmu.data_ptr(),
+                             dal.data_ptr(), dbe.data_ptr(), sptr)
+
+    call()
+    rc = B.hawkes_last_device_status(ws.data_ptr(), sptr)
+    if rc:
+        raise B.HawkesError(rc, "workload 5")
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        call()
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(b))
+    B.hawkes_profile_enable(True)
+    call()
+    kern = {k: round(v, 3) for k, v in B.hawkes_profile_read()}
+    B.hawkes_profile_enable(False)
+    m = sum(ms) / len(ms)
+    return {"workload": "M=4096, beta_j ~ U[0.2,5] per source, alpha 1% dense at spectral "
+                        "radius 0.85, N=50,000,000 on [0, T~1e7], seed 4; gradient on "
+                        "alpha's support; mark-major path",
+            "value": N / (m * 1e-3), "unit": "events/s", "ms_per_step": m, "steps": steps,
+            "loglik": float(ll.item()), "kernels_ms": kern}
 
 
 # ------------------------------------------------------ plain FP64 scan (paper)
@@ -388,8 +478,12 @@ def run_ours(args):
     hbm, bf16, bf16_sus, sm_max, src = peaks()
     roof = roofline(kern_ms, N, M, args, hbm, bf16, bf16_sus, clk, src)
     path_roof = path_roofline(ms, N, M, hbm, clk, bf16)
-    cpu = time_oracle(p) if (world == 1 and not args.no_cpu) else None
+    cpu, precision = None, None
+    if world == 1 and not args.no_cpu:
+        cpu, ref = time_oracle(p, want_result=True)
+        precision = precision_report(p, dev, ref)
     fp64 = time_fp64_scan(p, dev) if (world == 1 and not args.no_fp64_scan) else None
+    w5 = workload5_line(dev) if (world == 1 and not args.no_workload5) else None
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -400,7 +494,7 @@ def run_ours(args):
                        "loglik": ll_val},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clk,
             "roofline": roof, "path_roofline": path_roof, "cpu_baseline": cpu,
-            "fp64_scan_baseline": fp64,
+            "fp64_scan_baseline": fp64, "precision": precision, "workload5": w5,
             "kernels_ms": {k: round(v, 4) for k, v in kern_ms.items()}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -520,7 +614,10 @@ def main():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--no-fp64-scan", action="store_true",
                     help="skip the plain FP64 scan comparison leg")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing leg")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the CPU oracle timing leg (and the precision report that uses it)")
+    ap.add_argument("--no-workload5", action="store_true",
+                    help="skip the fifth workload (per-source decays, M=4096, N=5e7)")
     ap.add_argument("--events", type=int, default=0,
                     help="use only the first N events of the workload (profiling runs)")
     args = ap.parse_args()

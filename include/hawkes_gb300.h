@@ -93,6 +93,15 @@ typedef struct {
                              0 (default): d_alpha in every entry.  Path 3 needs it for M > 128
                              (its rows of up to 128 support entries are checked on the device:
                              a longer row sets HAWKES_ERR_UNSUPPORTED in the status word).      */
+    int32_t reduce;       /* how the chunk-GEMM path (path 2, one kernel) sums the N terms
+                             log lambda_k: 0 (default) FP64 partial sums (per thread the running
+                             product of its FP32 intensities as an FP32 mantissa and an integer
+                             exponent, one FP64 log, FP64 sums across threads); 1 Kahan-
+                             compensated FP32 sums of FP32 logs (per thread, then across threads
+                             and blocks); 2 plain FP32 sums of FP32 logs.  Other paths: 0 only. */
+    int32_t fp32_times;   /* precision ablation only (path 2): 1 forms every time difference
+                             from the two times first rounded to FP32, instead of rounding
+                             their FP64 difference.  0 (default) for any real use.             */
 } hawkes_opts;
 
 /* Default options: per-source decay, default chunk, validation on, automatic path, one

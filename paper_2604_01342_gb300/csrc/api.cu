@@ -42,6 +42,7 @@ struct Plan {
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
     // mark-major walk
     size_t off_rowptr, off_supcol, off_supval, off_tcnt, off_segoff, off_segt, off_segf;
+    size_t off_llpart;
     int64_t seg_len;
     int nseg, ntiles, seg_tiles, tile_warps;
     int64_t ldk, ldt, nbp;
@@ -58,6 +59,8 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     int path = o ? o->path : 0;
     const int K = (o && o->kernels > 1) ? o->kernels : 1;
     const int support = o ? o->support : 0;
+    const int reduce = o ? o->reduce : 0, fp32_times = o ? o->fp32_times : 0;
+    if (reduce < 0 || reduce > 2 || fp32_times < 0 || fp32_times > 1) return HAWKES_ERR_INVALID_ARG;
     if (K > hk::kMaxKernels) return HAWKES_ERR_INVALID_ARG;
     if (K > 1) {
         // several kernels, each with one shared decay: chunk-GEMM path, one sequence
@@ -80,6 +83,8 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         if (o && o->chunk < 0) return HAWKES_ERR_INVALID_ARG;
     }
     if (path != PATH_WALK && path != PATH_GEMM && path != PATH_MARKS) return HAWKES_ERR_INVALID_ARG;
+    // the FP32 log-sums and the FP32-times ablation exist on the one-kernel chunk-GEMM path
+    if ((reduce != 0 || fp32_times != 0) && (path != PATH_GEMM || K > 1)) return HAWKES_ERR_UNSUPPORTED;
     int C = path == PATH_MARKS ? kMarksPrepChunk
                                : (o && o->chunk > 0) ? o->chunk
                                                      : (path == PATH_WALK ? kDefaultChunkWalk
@@ -103,6 +108,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->nb_max = (N + C - 1) / C + B;
     pl->off_rowptr = pl->off_supcol = pl->off_supval = pl->off_tcnt = pl->off_segoff = 0;
     pl->off_segt = pl->off_segf = 0;
+    pl->off_llpart = 0;
     pl->seg_len = 0;
     pl->nseg = pl->ntiles = pl->seg_tiles = pl->tile_warps = 0;
     if (path == PATH_MARKS) {
@@ -189,6 +195,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_cen = take(sizeof(float) * ((4 + 2 * 32) * (size_t)M + 1));   // 32 = kCentreSlices
         pl->off_wsum = take(sizeof(double) * (size_t)M);
         pl->off_Y = take(sizeof(float) * nbM);
+        pl->off_llpart = take(sizeof(float) * 2 * (size_t)hk::kLogSumBlocks);
         pl->off_isc = take(sizeof(float) * (3 * (size_t)M + 2 * (size_t)pl->nb_max));
         pl->off_colmax = take(sizeof(uint32_t) * (size_t)M);
         pl->off_al_p = take(h * (size_t)M * pl->ldk);
@@ -303,6 +310,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.ntiles = pl.ntiles;
     p.seg_tiles = pl.seg_tiles;
     p.tile_warps = pl.tile_warps;
+    p.ll_part = at<float>(ws, pl.off_llpart);
 }
 
 int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {
@@ -319,6 +327,8 @@ int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStr
         cudaEventRecord(g_prof.ev[0], s);
     }
     p.support = o ? o->support : 0;
+    p.reduce = o ? o->reduce : 0;
+    p.fp32_times = o ? o->fp32_times : 0;
     cudaError_t err = hk::launch_prepare(p, s, validate, &nl);
     if (err == cudaSuccess) {
         if (pl.path == PATH_MARKS) {
@@ -444,6 +454,8 @@ hawkes_opts hawkes_default_opts(void) {
     o.path = 0;
     o.kernels = 1;
     o.support = 0;
+    o.reduce = 0;
+    o.fp32_times = 0;
     return o;
 }
 

@@ -132,6 +132,10 @@ struct Problem {
     int32_t ntiles;          // tiles of the sort
     int32_t seg_tiles;       // tiles per segment
     int32_t tile_warps;      // tiles (warps) per block of the sort kernels
+    // precision options of the chunk-GEMM path
+    int32_t reduce;          // 0: FP64 log-sum; 1: Kahan FP32; 2: plain FP32
+    int32_t fp32_times;      // ablation: time differences of FP32-rounded times
+    float* ll_part;          // [2 * kLogSumBlocks] per-block (sum, error) of the FP32 log-sums
     // outputs
     double* out_ll;          // [B]
     float* d_mu;
@@ -178,6 +182,27 @@ __device__ __forceinline__ float exp_unbiased(float x) {
     if (ki > 127) return (y * 2.f) * __int_as_float((ki - 1 + 127) << 23);
     return y * __int_as_float((ki + 127) << 23);
 }
+
+// t_a - t_b as the kernels form a time difference: in FP64 (then rounded to FP32 by the
+// caller), or, for the precision ablation, from the two times rounded to FP32 first.
+__device__ __forceinline__ double tdiff(const Problem& p, double a, double b) {
+    return p.fp32_times ? (double)((float)a - (float)b) : a - b;
+}
+
+// Compensated FP32 sum (Neumaier's variant of Kahan summation): the value is s + e.
+struct SumF32 {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        e += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ void add(const SumF32& o) {
+        add(o.s);
+        e += o.e;
+    }
+};
+constexpr int kLogSumBlocks = 4096;   // capacity of the per-block log-sum partials
 
 __device__ __forceinline__ float beta_of(const Problem& p, int32_t seq, int32_t j) {
     return p.shared ? p.beta[seq] : p.beta[(int64_t)seq * p.M + j];

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             for (int w = e - e % W; w < e; ++w) before += __popc(msk[w]);
             bmask[b * P * W + e] = make_uint2(msk[e], (uint32_t)before);
         }
-        const bool isw = n > 0 && beta * (float)(p.t[s1 - 1] - p.t[s0]) > kWideLimit;
+        const bool isw = n > 0 && beta * (float)tdiff(p, p.t[s1 - 1], p.t[s0]) > kWideLimit;
         for (int i0 = 0; i0 < n; i0 += 32) {
             const int i = i0 + lane;
             const bool have = i < n;
@@ -619,14 +619,17 @@ __global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __r
     uint32_t* hcnt = (uint32_t*)(hmu + M);    // [M] events per mark (without validation)
     __shared__ double red_ll[16];
     __shared__ double red_db[16];
+    __shared__ SumF32 red_ls[16];
     if (failed(p.hdr)) return;
     const int64_t N = p.N, ldw = p.nbp;
+    const int mode = p.reduce;                // 0: FP64 log of running products; 1, 2: FP32 logs
     const float beta = p.beta[0];
     const double T = p.Tarr[0];
     const bool counted = p.validated != 0;
     for (int j = threadIdx.x; j < 4 * M; j += blockDim.x) sh[j] = 0.f;
     __syncthreads();
     LogProd lp;
+    SumF32 ls;
     float db = 0.f;
 #pragma unroll 4
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
@@ -640,10 +643,12 @@ __global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __r
         const float aS = ek * y + ak;
         const float lam = __ldg(p.mu + ck) + beta * aS;
         if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
-        lp.mul(lam);
+        if (mode == 0) lp.mul(lam);
+        else if (mode == 1) ls.add(logf(lam));
+        else ls.s += logf(lam);
         if (!counted) atomicAdd(&hcnt[ck], 1u);
         if (beta * (__ldg(p.Tmt + b) - delta) < kTailLimit + 1.f) {   // T - t_k, to within rounding
-            const float xT = (float)(T - p.t[k]);
+            const float xT = (float)tdiff(p, T, p.t[k]);
             if (beta * xT < kTailLimit) {
                 const float eT = exp_unbiased(-beta * xT);
                 atomicAdd(&hEt[ck], eT);
@@ -659,18 +664,39 @@ __global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __r
             atomicAdd(&hmu[ck], w);
         }
     }
-    double ll = lp.log_value();
+    double ll = mode == 0 ? lp.log_value() : 0.0;
     double dbd = (double)db;
     for (int o = 16; o >= 1; o >>= 1) {
         ll += __shfl_xor_sync(HK_FULL, ll, o);
         dbd += __shfl_xor_sync(HK_FULL, dbd, o);
+        if (mode != 0) {
+            SumF32 other;
+            other.s = __shfl_xor_sync(HK_FULL, ls.s, o);
+            other.e = __shfl_xor_sync(HK_FULL, ls.e, o);
+            if (mode == 1) ls.add(other);
+            else ls.s += other.s;
+        }
     }
-    if ((threadIdx.x & 31) == 0) { red_ll[threadIdx.x >> 5] = ll; red_db[threadIdx.x >> 5] = dbd; }
+    if ((threadIdx.x & 31) == 0) {
+        red_ll[threadIdx.x >> 5] = ll;
+        red_db[threadIdx.x >> 5] = dbd;
+        red_ls[threadIdx.x >> 5] = ls;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, d = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red_ll[w]; d += red_db[w]; }
-        atomicAdd(&p.ll_acc[0], a);
+        SumF32 bl;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red_ll[w];
+            d += red_db[w];
+            if (mode == 1) bl.add(red_ls[w]);
+            else bl.s += red_ls[w].s;
+        }
+        if (mode == 0) atomicAdd(&p.ll_acc[0], a);
+        else if (blockIdx.x < kLogSumBlocks) {       // combined in block order by k_logsum_combine
+            p.ll_part[2 * blockIdx.x] = bl.s;
+            p.ll_part[2 * blockIdx.x + 1] = mode == 1 ? bl.e : 0.f;
+        }
         if (GRAD) atomicAdd(&p.dbe_acc[0], d);
     }
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
@@ -682,6 +708,21 @@ __global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __r
             if (hmu[j] != 0.f) atomicAdd(&p.dmu_acc[j], (double)hmu[j]);
         }
     }
+}
+
+// The FP32 log-sums of the epilogue's blocks, in block order (mode 1 compensated, mode 2
+// plain), into ll_acc[0].
+__global__ void k_logsum_combine(Problem p, int blocks) {
+    if (threadIdx.x != 0 || failed(p.hdr)) return;
+    SumF32 s;
+    for (int b = 0; b < blocks; ++b) {
+        SumF32 x;
+        x.s = p.ll_part[2 * b];
+        x.e = p.ll_part[2 * b + 1];
+        if (p.reduce == 1) s.add(x);
+        else s.s += x.s;
+    }
+    p.ll_acc[0] = (double)(p.reduce == 1 ? s.s + s.e : s.s);
 }
 
 // Blocks of the epilogue kernels: three per SM (512 threads, each ~20 events at N = 1e7).
@@ -803,8 +844,14 @@ cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nl) {
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    kern<<<(unsigned)epilogue_blocks(p.N), 512, smem, s>>>(p, p.Aint, p.Bint, p.wbuf);
+    int blocks = epilogue_blocks(p.N);
+    if (p.reduce != 0 && blocks > kLogSumBlocks) blocks = kLogSumBlocks;
+    kern<<<(unsigned)blocks, 512, smem, s>>>(p, p.Aint, p.Bint, p.wbuf);
     ++*nl;
+    if (p.reduce != 0) {
+        k_logsum_combine<<<1, 32, 0, s>>>(p, blocks);
+        ++*nl;
+    }
     prof_mark(s, "epilogue");
     return cudaGetLastError();
 }

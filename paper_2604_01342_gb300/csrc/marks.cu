@@ -33,6 +33,7 @@ namespace hk {
 constexpr int kTileEv = 16384;          // events per tile: one warp histograms and scatters it
 constexpr int kMarkGroups = 4;          // 32-lane groups of a row: up to 128 support entries
 constexpr int kMarkRowMax = 32 * kMarkGroups;
+constexpr int kRowMaxWord = 9;          // header word: the longest support row (device)
 constexpr float kMarkTail = 104.f;      // exp(-x) is 0 in FP32 for x above this
 
 __device__ __forceinline__ float4 mark_sentinel() {
@@ -57,6 +58,7 @@ __global__ void k_csr_count(Problem p) {
         if (lane == 0) {
             p.row_ptr[i + 1] = n;
             if (n > kMarkRowMax) set_status(p.hdr, HAWKES_ERR_UNSUPPORTED);
+            atomicMax((unsigned long long*)&p.hdr->pad[kRowMaxWord], (unsigned long long)n);
         }
         if (i == 0 && lane == 0) p.row_ptr[0] = 0;
     }
@@ -315,9 +317,17 @@ __global__ void k_seg_carry(Problem p) {
 // Work items (segment, target mark) in segment-major order, taken from a counter so that the
 // warps work on the same few segments at a time (their sorted events stay in L2).  GRAD
 // adds the gradient sums; without it only lambda, its log and the compensator are formed.
-template <bool GRAD>
-__global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long long* counter) {
+// R lane groups hold rows of up to 32 R support entries; both variants are launched and the
+// one whose R fits the longest row (a header word written by k_csr_count) does the work, so
+// that rows of at most 64 entries run with half the registers and twice the warps per SM.
+// Each lane keeps the next two records of its source list in flight, and the warp the next
+// target record, because a walk step waits on little else than those loads.
+template <bool GRAD, int R>
+__global__ void __launch_bounds__(256, R == 2 ? 3 : 2) k_walk_marks(Problem p,
+                                                                    unsigned long long* counter) {
     if (failed(p.hdr)) return;
+    const unsigned long long rowmax = *(volatile unsigned long long*)&p.hdr->pad[kRowMaxWord];
+    if (R == 2 ? rowmax > 64 : rowmax <= 64) return;      // the other variant's work
     const int M = p.M, lane = threadIdx.x & 31;
     const int64_t nitems = (int64_t)p.nseg * M;
     const float4* __restrict__ rec = p.recs;
@@ -333,12 +343,11 @@ __global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long lon
         if (ta == tb) continue;
         const int r0 = p.row_ptr[i], r1 = p.row_ptr[i + 1];
         const int ng = (r1 - r0 + 31) >> 5;
-        float Sv[kMarkGroups], Gv[kMarkGroups], lh[kMarkGroups], ll[kMarkGroups];
-        float av[kMarkGroups], bv[kMarkGroups], dal[kMarkGroups], dbe[kMarkGroups];
-        int q[kMarkGroups], qe[kMarkGroups], jv[kMarkGroups];
-        float4 nx[kMarkGroups];
+        float Sv[R], Gv[R], lh[R], ll[R], av[R], bv[R], dal[R], dbe[R];
+        int q[R], qe[R], jv[R];
+        float4 nx[R], nx2[R];
 #pragma unroll
-        for (int g = 0; g < kMarkGroups; ++g) {
+        for (int g = 0; g < R; ++g) {
             const int e = r0 + 32 * g + lane;
             const bool valid = g < ng && e < r1;
             jv[g] = valid ? p.sup_col[e] : -1;
@@ -350,6 +359,7 @@ __global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long lon
             q[g] = valid ? soff[at] : 0;
             qe[g] = valid ? soff[at + 1] : 0;
             nx[g] = q[g] < qe[g] ? rec[q[g]] : sentinel;
+            nx2[g] = q[g] + 1 < qe[g] ? rec[q[g] + 1] : sentinel;
             lh[g] = 0.f;
             ll[g] = 0.f;
             dal[g] = 0.f;
@@ -359,13 +369,15 @@ __global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long lon
         LogProd lp;
         float dmu = 0.f;
         bool bad = false;
+        float4 tnext = rec[ta];
         for (int k = ta; k < tb; ++k) {
-            const float4 tk = rec[k];
+            const float4 tk = tnext;
+            if (k + 1 < tb) tnext = rec[k + 1];
             const int ik = __float_as_int(tk.z);
             float part = 0.f;
-            float sv[kMarkGroups], gv[kMarkGroups];
+            float sv[R], gv[R];
 #pragma unroll
-            for (int g = 0; g < kMarkGroups; ++g) {
+            for (int g = 0; g < R; ++g) {
                 sv[g] = 0.f;
                 gv[g] = 0.f;
                 if (g < ng) {
@@ -378,7 +390,8 @@ __global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long lon
                         lh[g] = nx[g].x;
                         ll[g] = nx[g].y;
                         ++q[g];
-                        nx[g] = q[g] < qe[g] ? rec[q[g]] : sentinel;
+                        nx[g] = nx2[g];
+                        nx2[g] = q[g] + 1 < qe[g] ? rec[q[g] + 1] : sentinel;
                     }
                     // the component at the target event's time
                     const float dt = (tk.x - lh[g]) + (tk.y - ll[g]);
@@ -397,7 +410,7 @@ __global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long lon
                 const float w = 1.f / lam;
                 if (lane == 0) dmu += w;
 #pragma unroll
-                for (int g = 0; g < kMarkGroups; ++g) {
+                for (int g = 0; g < R; ++g) {
                     dal[g] = fmaf(w, sv[g], dal[g]);
                     dbe[g] = fmaf(w * av[g], fmaf(-bv[g], gv[g], sv[g]), dbe[g]);
                 }
@@ -426,7 +439,7 @@ __global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long lon
         }
         if (GRAD) {
 #pragma unroll
-            for (int g = 0; g < kMarkGroups; ++g) {
+            for (int g = 0; g < R; ++g) {
                 if (jv[g] >= 0) {
                     atomicAdd(&p.dal_acc[(int64_t)i * M + jv[g]], (double)(bv[g] * dal[g]));
                     atomicAdd(&p.dbe_acc[jv[g]], (double)dbe[g]);
@@ -443,6 +456,19 @@ __global__ void __launch_bounds__(256) k_walk_marks(Problem p, unsigned long lon
             }
         }
     }
+}
+
+template <bool GRAD, int R>
+static cudaError_t launch_walk_marks(const Problem& p, int sms, int64_t nsm, cudaStream_t s) {
+    auto kern = k_walk_marks<GRAD, R>;
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (err != cudaSuccess) return err;
+    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (nsm + 7) / 8;
+    if (blocks > need) blocks = need;
+    kern<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, (unsigned long long*)&p.hdr->pad[8]);
+    return cudaGetLastError();
 }
 
 int marks_row_max() { return kMarkRowMax; }
@@ -496,16 +522,21 @@ cudaError_t launch_marks(const Problem& p, int64_t L, cudaStream_t s, int* nl) {
         ++*nl;
         prof_mark(s, "seg_states");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
-        // the walk
-        auto kern = p.grad ? k_walk_marks<true> : k_walk_marks<false>;
-        int per_sm = 0;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0)) != cudaSuccess)
-            return err;
-        int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-        const int64_t need = (nsm + 7) / 8;
-        if (blocks > need) blocks = need;
-        kern<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, (unsigned long long*)&p.hdr->pad[8]);
-        ++*nl;
+        // the walk: both variants when the support's longest row is known only on the
+        // device, the one that fits when every row is dense (M entries)
+        const bool two = !p.support ? M <= 64 : true, four = !p.support ? M > 64 : true;
+        if (two) {
+            err = p.grad ? launch_walk_marks<true, 2>(p, sms, nsm, s)
+                         : launch_walk_marks<false, 2>(p, sms, nsm, s);
+            if (err != cudaSuccess) return err;
+            ++*nl;
+        }
+        if (four) {
+            err = p.grad ? launch_walk_marks<true, 4>(p, sms, nsm, s)
+                         : launch_walk_marks<false, 4>(p, sms, nsm, s);
+            if (err != cudaSuccess) return err;
+            ++*nl;
+        }
         prof_mark(s, "walk_marks");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }

@@ -87,9 +87,9 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
         const double t0 = s0 < s1 ? p.t[s0] : 0.0;
         if (last) {
             if (PHASE == 0 && fast) {
-                if (threadIdx.x == 0 && s0 < s1) p.Tmt[b] = (float)(p.Tarr[seq] - t0);
+                if (threadIdx.x == 0 && s0 < s1) p.Tmt[b] = (float)tdiff(p, p.Tarr[seq], t0);
                 for (int64_t l = s0 + threadIdx.x; l < s1; l += blockDim.x)
-                    p.delta[l] = (float)(p.t[l] - t0);
+                    p.delta[l] = (float)tdiff(p, p.t[l], t0);
             }
             for (int j = threadIdx.x; j < M; j += blockDim.x) {
                 S[j] = 0.f;
@@ -107,13 +107,13 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
             narrow = beta_of(p, seq, 0) * D <= 16.f;
         } else {
             if (threadIdx.x == 0) {
-                const double span = tn - t0;
+                const double span = fast ? tdiff(p, tn, t0) : tn - t0;
                 D_sh = (float)span;
                 narrow_sh = fast && beta_of(p, seq, 0) * D_sh <= 16.f;
                 span_sh += span;
                 if (PHASE == 0 && fast) {
                     p.Dspan[b] = D_sh;
-                    p.Tmt[b] = (float)(p.Tarr[seq] - t0);
+                    p.Tmt[b] = (float)tdiff(p, p.Tarr[seq], t0);
                 }
             }
             __syncthreads();
@@ -134,12 +134,12 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
             if (fast) {
                 float dl;
                 if (PHASE == 0) {
-                    dl = (float)(p.t[l] - t0);
+                    dl = (float)tdiff(p, p.t[l], t0);
                     p.delta[l] = dl;
                 } else {
                     dl = p.delta[l];
                 }
-                x = narrow ? D - dl : (float)(tn - p.t[l]);
+                x = narrow ? D - dl : (float)tdiff(p, tn, p.t[l]);
             } else {
                 x = (float)(tn - p.t[l]);
             }
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(256) k_scan_states_fast(Problem p) {
         for (int64_t l = s0 + tid; l < s1; l += blockDim.x) {
             const int cl = l == s0 + tid ? c0 : __ldg(p.c + l);
             const float dl = l == s0 + tid ? d0 : __ldg(p.delta + l);
-            const float x = narrow ? D - dl : (float)(p.t[s1] - p.t[l]);
+            const float x = narrow ? D - dl : (float)tdiff(p, p.t[s1], p.t[l]);
             const float e = exp_unbiased(-beta * x);
             atomicAdd(&S[cl], e);
             if (GRAD) atomicAdd(&G[cl], x * e);

@@ -58,14 +58,16 @@ def _stream(device):
 
 def loglik_grad(t, c, T, mu, alpha, beta, beta_shared=None, chunk: int = 0, path: int = 0,
                 validate: bool = True, check: bool = True, grad: bool = True,
-                support: bool = False):
+                support: bool = False, reduce: int = 0, fp32_times: bool = False):
     """L (float64 0-d) and, if ``grad``, (dmu, dalpha, dbeta) as float32 tensors.
-    ``support=True``: dalpha on alpha's support (entries alpha == 0 get 0)."""
+    ``support=True``: dalpha on alpha's support (entries alpha == 0 get 0).  ``reduce`` and
+    ``fp32_times``: the precision options of hawkes_opts (chunk-GEMM path)."""
     t, c, mu, alpha, beta = _prep(t, c, mu, alpha, beta)
     dev = t.device
     N, M = t.shape[0], mu.shape[0]
     shared = _shared(beta, M, beta_shared)
-    opts = _b.make_opts(shared, chunk, validate, path, support=support)
+    opts = _b.make_opts(shared, chunk, validate, path, support=support, reduce=reduce,
+                        fp32_times=fp32_times)
     nbytes = _b.hawkes_workspace_size(N, M, 1, grad, opts)
     ws = _workspace(nbytes, dev)
     out_ll = torch.empty((), dtype=torch.float64, device=dev)

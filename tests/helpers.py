@@ -86,3 +86,13 @@ def assert_close(got, ref, grad=True, ll_rtol=LL_RTOL, grad_rtol=GRAD_RTOL, what
             e = maxnorm_rel(got[k], ref[k])
             assert e <= grad_rtol, f"{what} {k} max-norm rel err {e:.3e}"
     return used_scale
+
+
+def support_oracle_from_files(paths):
+    """The oracle's lazy per-component form on arrays stored in .npy files (a picklable
+    job for a spawned worker process): paths = (t, c, T, mu, alpha, beta)."""
+    import oracle
+    t, c = np.load(paths[0], mmap_mode="r"), np.load(paths[1], mmap_mode="r")
+    T = float(np.load(paths[2]))
+    mu, alpha, beta = (np.load(x) for x in paths[3:6])
+    return oracle.loglik_grad_support(np.asarray(t), np.asarray(c), T, mu, alpha, beta)
