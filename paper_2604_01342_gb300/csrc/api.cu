@@ -42,7 +42,7 @@ struct Plan {
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
     // mark-major walk
     size_t off_rowptr, off_supcol, off_supval, off_tcnt, off_segoff, off_segt, off_segf;
-    size_t off_llpart;
+    size_t off_llpart, off_redo;
     int64_t seg_len;
     int nseg, ntiles, seg_tiles, tile_warps;
     int64_t ldk, ldt, nbp;
@@ -109,6 +109,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->off_rowptr = pl->off_supcol = pl->off_supval = pl->off_tcnt = pl->off_segoff = 0;
     pl->off_segt = pl->off_segf = 0;
     pl->off_llpart = 0;
+    pl->off_redo = 0;
     pl->seg_len = 0;
     pl->nseg = pl->ntiles = pl->seg_tiles = pl->tile_warps = 0;
     if (path == PATH_MARKS) {
@@ -182,6 +183,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
             pl->dal_parts_max = (int)(r > 0 ? r : 1);
             const size_t tr = ((size_t)M + P - 1) / P;
             if (grad) pl->off_dal_part = take(sizeof(float) * (size_t)pl->dal_parts_max * P * P * tr * tr);
+            if (grad) pl->off_redo = take(sizeof(int32_t) * (size_t)pl->dal_parts_max * P * P);
         }
         pl->off_at = take(sizeof(float) * P * P * 128 * 128);
         pl->off_bstart = take(sizeof(int32_t) * (size_t)pl->nb_max * (P + 1));
@@ -311,6 +313,7 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.seg_tiles = pl.seg_tiles;
     p.tile_warps = pl.tile_warps;
     p.ll_part = at<float>(ws, pl.off_llpart);
+    p.pair_redo = at<int32_t>(ws, pl.off_redo);
 }
 
 int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {

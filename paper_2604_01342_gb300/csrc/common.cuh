@@ -70,6 +70,7 @@ struct Problem {
     float* dal_part;         // [dal_parts][P*P][128*128] backward pair tiles of the chunk-GEMM path
     int32_t dal_parts;       // chunk ranges of the backward pair kernel (set at launch)
     int32_t dal_parts_max;   // capacity of dal_part in ranges
+    int32_t* pair_redo;      // [dal_parts_max * P * P] blocks of the backward pairs to redo in FP32
     float* scratch;          // [M + 2] outputs of a slice that the caller does not see
     double* dbe_acc;         // [B*M] excitation part of dbeta
     double* E_acc;           // [B*M] sum (1 - exp(-beta (T - t))) per source

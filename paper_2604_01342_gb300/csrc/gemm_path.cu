@@ -15,6 +15,8 @@
 //   dL/dalpha_ij (excitation part) = beta [ sum_b W[b][i] S^_b[j]
 //                                          + sum_{pairs l<k in one chunk, c_k=i, c_l=j} w_k exp(-beta(t_k-t_l)) ]
 // with W[b][i] = sum_{k in b, c_k = i} w_k e_k, the second dense GEMM.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace hk {
@@ -458,6 +460,25 @@ __global__ void __launch_bounds__(256) k_bwd_prep(Problem p, const float4* __res
 // run of about T / 32 of them: each shared-memory add carries one item, whatever the
 // spread of the intervals.  Chunks too wide for the factorised weights take one exp per
 // pair over all (k, l) instead.
+//
+// FIXED: the tile holds unsigned fixed-point numbers (value x 2^s, rounded to nearest) and
+// every add is a native 32-bit shared-memory atomic (an FP32 shared-memory atomic is a load
+// and a compare-and-swap on this part, a third of the rate).  Every item is at most 32 w_max
+// (w_max = the largest 1 / lambda_k: U_k ep_l <= sum of w over the row group), and s puts 64
+// such items below 2^32 (s from k_pair_scale, at most 2^-12 absolute resolution at the bench
+// workload, far below the 1e-4 max-norm tolerance of dalpha); an add that would wrap is
+// detected from the atomic's returned value and marks the block, whose (tile, chunk range)
+// the FP32 variant (FIXED = false, flagged blocks only) then recomputes.
+__device__ __forceinline__ void tile_add(float* t, int at, float v, float, bool&) {
+    atomicAdd(t + at, v);
+}
+__device__ __forceinline__ void tile_add(uint32_t* t, int at, float v, float scale, bool& wrap) {
+    const uint32_t x = __float2uint_rn(v * scale);
+    const uint32_t old = atomicAdd(t + at, x);
+    wrap |= old > 0xffffffffu - x;
+}
+
+template <bool FIXED>
 __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const float4* __restrict__ recs,
                                                    const float2* __restrict__ lrec,
                                                    const uint2* __restrict__ bmask,
@@ -465,13 +486,22 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                                                    const int32_t* __restrict__ bstart,
                                                    const uint8_t* __restrict__ wide,
                                                    const float* __restrict__ wbuf,
-                                                   int chunks_per_cta) {
-    extern __shared__ float dtile[];      // [kTile][kTileLd], then per-warp scratch
+                                                   int chunks_per_cta, int* redo) {
+    using TileT = typename std::conditional<FIXED, uint32_t, float>::type;
+    extern __shared__ float sm_bwd[];
+    TileT* dtile = (TileT*)sm_bwd;          // [kTile][kTileLd], then per-warp scratch
+    __shared__ int wrap_sh;
     if (failed(p.hdr)) return;
+    const int block_id = blockIdx.y * gridDim.x + blockIdx.x;
+    if (FIXED ? redo[block_id] != 0 : !redo[block_id]) return;   // the other variant's block
+    // 2^s of the fixed-point tile, from the exponent k_pair_scale left in the header
+    const int sexp = FIXED ? (int)p.hdr->pad[10] : 0;
+    const float scale = FIXED ? ldexpf(1.f, sexp) : 1.f;
+    bool wrap = false;
     const int P = p.P;
     const int I = blockIdx.x / P, J = blockIdx.x % P;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    char* scratch = (char*)(dtile + kTile * kTileLd) + warp * kBwdWarpScratch;
+    char* scratch = (char*)(sm_bwd + kTile * kTileLd) + warp * kBwdWarpScratch;
     int4* kd = (int4*)scratch;                          // [32] per-lane item ranges
     float2* lst = (float2*)(kd + 32);                   // [kLStage] sources of bucket J
     float4* stage = (float4*)scratch;                   // wide chunks: [kStage] records
@@ -480,7 +510,8 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
     const int b1 = min(b0 + chunks_per_cta, nb);    // may be empty: the tile is still written
     const float beta = p.beta[0];
     const int C = p.C, W = (C + 31) >> 5;
-    for (int e = threadIdx.x; e < kTile * kTileLd; e += blockDim.x) dtile[e] = 0.f;
+    for (int e = threadIdx.x; e < kTile * kTileLd; e += blockDim.x) dtile[e] = (TileT)0;
+    if (threadIdx.x == 0) wrap_sh = 0;
     __syncthreads();
     for (int b = b0 + warp; b < b1; b += nwarps) {
         const int64_t s0 = (int64_t)b * C;
@@ -549,7 +580,8 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                         if (gi >= ko.w) ko = kd[min(++j, 31)];     // next owner (at most one step)
                         if (gi < g1) {
                             const float2 l = lst[gi + ko.z];
-                            atomicAdd(dtile + ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x);
+                            tile_add(dtile, ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x,
+                                     scale, wrap);
                         }
                     }
                 } else {
@@ -559,7 +591,8 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                         if (gi >= ko.w) ko = kd[min(++j, 31)];
                         if (gi < g1) {
                             const float2 l = __ldg(lrec + s0 + l0 + gi + ko.z);
-                            atomicAdd(dtile + ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x);
+                            tile_add(dtile, ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x,
+                                     scale, wrap);
                         }
                     }
                 }
@@ -568,7 +601,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                 const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int ik = have ? rec_idx(rk) : -1;
                 const float wk = have ? wbuf[s0 + ik] : 0.f;
-                float* drow = dtile + (have ? rec_pos(rk) : 0) * kTileLd;
+                const int drow = (have ? rec_pos(rk) : 0) * kTileLd;
                 for (int lb = 0; lb < nJ; lb += kStage) {
                     const int ns = min(kStage, nJ - lb);
                     __syncwarp();
@@ -578,19 +611,49 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const 
                     for (int l = 0; l < ns; ++l) {
                         const float4 rl = stage[l];
                         if (__float_as_int(rl.w) < ik)
-                            atomicAdd(drow + __float_as_int(rl.z), wk * expf(-beta * (rk.x - rl.x)));
+                            tile_add(dtile, drow + __float_as_int(rl.z),
+                                     wk * expf(-beta * (rk.x - rl.x)), scale, wrap);
                     }
                 }
             }
         }
     }
+    if (FIXED && wrap) atomicOr(&wrap_sh, 1);
     __syncthreads();
+    if (FIXED && wrap_sh) {                 // recomputed by the FP32 variant
+        if (threadIdx.x == 0) redo[block_id] = 1;
+        return;
+    }
     // this block's tile (TR = ceil(M / P) rows and columns are used), summed over the chunk
     // ranges in a fixed order by the finalisation
     const int TR = (p.M + P - 1) / P;
     float* out = p.dal_part + ((int64_t)blockIdx.y * P * P + blockIdx.x) * TR * TR;
+    const float inv = FIXED ? ldexpf(1.f, -sexp) : 1.f;
     for (int e = threadIdx.x; e < TR * TR; e += blockDim.x)
-        out[e] = dtile[(e / TR) * kTileLd + (e % TR)];
+        out[e] = (float)dtile[(e / TR) * kTileLd + (e % TR)] * inv;
+}
+
+// The exponent s of the fixed-point pair tiles: w_max = the largest w_k (one pass over w),
+// then s with 32 w_max 2^s <= 2^26; written to the header.  A tile whose adds would wrap is
+// still exact (the FP32 variant redoes it); s below kFixedMinExp (w_max above ~2^9) sends
+// every block to the FP32 variant, so that the fixed-point resolution 2^-s stays fine.
+constexpr int kFixedMinExp = 8;
+__global__ void k_pair_wmax(Problem p, const float* __restrict__ w, unsigned* wmax_bits) {
+    float m = 0.f;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.N;
+         k += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, w[k]);
+    for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(HK_FULL, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(wmax_bits, __float_as_uint(m));
+}
+__global__ void k_pair_scale(Problem p, const unsigned* wmax_bits, int* redo, int nblocks) {
+    const float wmax = __uint_as_float(*wmax_bits);
+    int e = 0;
+    if (wmax > 0.f && isfinite(wmax)) frexpf(32.f * wmax, &e);     // 32 wmax < 2^e
+    const int s = 26 - e;
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.hdr->pad[10] = s;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblocks; b += gridDim.x * blockDim.x)
+        redo[b] = s < kFixedMinExp ? 1 : 0;
 }
 
 // Per-event epilogue: lambda, log, w, the W entries of the dalpha GEMM, the dbeta sum and
@@ -879,13 +942,15 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
     if (p.grad) {
         // backward pairs: tile (I, J) x chunk range
         const size_t smem = sizeof(float) * kTile * kTileLd + kBwdWarpScratch * kPairWarps;
-        err = cudaFuncSetAttribute(k_pairs_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
+        for (const void* k : {(const void*)k_pairs_bwd<true>, (const void*)k_pairs_bwd<false>}) {
+            err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+        }
         // Blocks of equal work: pick the number R of chunk ranges per tile that minimises
         // (waves of resident blocks) x (chunks per block + the cost of one tile flush,
         // counted as kFlushChunks chunks).
         int per_sm = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_bwd, kPairThreads, smem);
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_bwd<true>, kPairThreads, smem);
         if (err != cudaSuccess) return err;
         const int64_t slots = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
         const int64_t tiles = (int64_t)P * P;
@@ -901,9 +966,24 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
         R = (nb + per - 1) / per;
         if (R < 1) R = 1;
         dal_parts = R;
-        k_pairs_bwd<<<dim3((unsigned)(P * P), (unsigned)R), kPairThreads, smem, s>>>(
-            p, p.recs, p.lrec, p.bmask, p.kprep, p.bstart, p.wide, p.wbuf, (int)per);
-        ++*nl;
+        // the fixed-point scale from the largest w, then the fixed-point pass, then the FP32
+        // pass over the blocks it could not hold
+        const int nblocks = (int)(tiles * R);
+        unsigned* wmax_bits = (unsigned*)&p.hdr->pad[11];
+        cudaMemsetAsync(wmax_bits, 0, sizeof(unsigned), s);
+        {
+            int64_t wb = (p.N + 255) / 256;
+            if (wb > (int64_t)sms * 4) wb = (int64_t)sms * 4;
+            k_pair_wmax<<<(unsigned)(wb > 0 ? wb : 1), 256, 0, s>>>(p, p.wbuf, wmax_bits);
+            k_pair_scale<<<(unsigned)((nblocks + 255) / 256), 256, 0, s>>>(p, wmax_bits, p.pair_redo,
+                                                                           nblocks);
+        }
+        const dim3 bgrid((unsigned)(P * P), (unsigned)R);
+        k_pairs_bwd<true><<<bgrid, kPairThreads, smem, s>>>(
+            p, p.recs, p.lrec, p.bmask, p.kprep, p.bstart, p.wide, p.wbuf, (int)per, p.pair_redo);
+        k_pairs_bwd<false><<<bgrid, kPairThreads, smem, s>>>(
+            p, p.recs, p.lrec, p.bmask, p.kprep, p.bstart, p.wide, p.wbuf, (int)per, p.pair_redo);
+        *nl += 4;
         prof_mark(s, "pairs_bwd");
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }

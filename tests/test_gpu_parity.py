@@ -234,3 +234,16 @@ def test_host_errors():
     with pytest.raises(binding.HawkesError) as ei:
         binding.hawkes_loglik(None, None, 5, 1.0, 3, None, None, None, opts, None, 0, None, None)
     assert ei.value.code == 1
+
+
+def test_gemm_path_fixed_point_overflow_falls_back():
+    """One mark dominates and the decay is slow, so that a single cell of the backward pair
+    tile collects far more than the fixed-point range of one block (every pair of a 1024-event
+    chunk of that mark adds about w_max): the wrapping adds are detected and those blocks are
+    recomputed in FP32; the result matches the oracle."""
+    p = synth.random_problem(2, 20_000, 42, True, rho=0.5, beta_range=(0.02, 0.03),
+                             mu_range=(0.5, 0.5))
+    p.mu = np.array([5.0, 0.01])
+    p = synth.Problem(t=p.t, c=np.where(np.arange(p.N) % 50 == 0, 1, 0).astype(np.int32),
+                      T=p.T, mu=p.mu, alpha=p.alpha, beta=p.beta, shared_beta=True)
+    assert_close(gpu_run(p, path=2, chunk=1024), oracle_ref(p), what="fixed-point overflow")
