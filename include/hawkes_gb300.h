@@ -102,6 +102,10 @@ typedef struct {
     int32_t fp32_times;   /* precision ablation only (path 2): 1 forms every time difference
                              from the two times first rounded to FP32, instead of rounding
                              their FP64 difference.  0 (default) for any real use.             */
+    int32_t walk_lanes;   /* path 1: lanes of one walker (the threads that share one chunk's
+                             state; a warp walks 32 / lanes chunks at once): 8 or 16 (one mark
+                             per lane: M <= lanes) or 32 (M <= 64); 0 = chosen from M (8 for
+                             M <= 8, 16 for M <= 16, else 32).  Other paths ignore it.          */
 } hawkes_opts;
 
 /* Default options: per-source decay, default chunk, validation on, automatic path, one

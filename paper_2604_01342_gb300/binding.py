@@ -39,7 +39,8 @@ class HawkesOpts(ctypes.Structure):
     _fields_ = [("beta_shared", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("kernels", ctypes.c_int32), ("support", ctypes.c_int32),
-                ("reduce", ctypes.c_int32), ("fp32_times", ctypes.c_int32)]
+                ("reduce", ctypes.c_int32), ("fp32_times", ctypes.c_int32),
+                ("walk_lanes", ctypes.c_int32)]
 
 
 class HawkesTables(ctypes.Structure):
@@ -122,9 +123,10 @@ def lib():
 
 def make_opts(beta_shared: bool, chunk: int = 0, validate: bool = True, path: int = 0,
               kernels: int = 1, support: bool = False, reduce: int = 0,
-              fp32_times: bool = False):
+              fp32_times: bool = False, walk_lanes: int = 0):
     return HawkesOpts(int(bool(beta_shared)), int(chunk), int(bool(validate)), int(path),
-                      int(kernels), int(bool(support)), int(reduce), int(bool(fp32_times)))
+                      int(kernels), int(bool(support)), int(reduce), int(bool(fp32_times)),
+                      int(walk_lanes))
 
 
 def _check(rc: int, where: str):

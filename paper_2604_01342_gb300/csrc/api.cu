@@ -60,6 +60,9 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     const int K = (o && o->kernels > 1) ? o->kernels : 1;
     const int support = o ? o->support : 0;
     const int reduce = o ? o->reduce : 0, fp32_times = o ? o->fp32_times : 0;
+    const int lanes = o ? o->walk_lanes : 0;
+    if (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32) return HAWKES_ERR_INVALID_ARG;
+    if (lanes != 0 && lanes < 32 && lanes < M) return HAWKES_ERR_INVALID_ARG;   // one mark per lane
     if (reduce < 0 || reduce > 2 || fp32_times < 0 || fp32_times > 1) return HAWKES_ERR_INVALID_ARG;
     if (K > hk::kMaxKernels) return HAWKES_ERR_INVALID_ARG;
     if (K > 1) {
@@ -232,6 +235,16 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
 template <typename T>
 T* at(void* ws, size_t off) { return off ? (T*)((char*)ws + off) : nullptr; }
 
+// Events of a single sequence that arrive on the device in pieces (the host-buffer entry
+// point): events [0, end[i]) (and the one event after, when there is one) are on the device
+// once ev[i] has completed.  Piece ends are whole scan groups.
+constexpr int kMaxPieces = 8;
+struct Pieces {
+    int n;
+    int64_t end[kMaxPieces];
+    cudaEvent_t ev[kMaxPieces];
+};
+
 void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int grad) {
     p.hdr = (hk::WsHeader*)ws;
     p.counts = at<int64_t>(ws, pl.off_counts);
@@ -316,7 +329,8 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.pair_redo = at<int32_t>(ws, pl.off_redo);
 }
 
-int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStream_t s) {
+int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStream_t s,
+        const Pieces* pieces = nullptr) {
     Plan pl;
     int rc = make_plan(p.N, p.M, p.B, p.grad, o, &pl);
     if (rc) return rc;
@@ -332,12 +346,38 @@ int run(hk::Problem& p, const hawkes_opts* o, void* ws, size_t ws_bytes, cudaStr
     p.support = o ? o->support : 0;
     p.reduce = o ? o->reduce : 0;
     p.fp32_times = o ? o->fp32_times : 0;
-    cudaError_t err = hk::launch_prepare(p, s, validate, &nl);
+    p.walk_lanes = o ? o->walk_lanes : 0;
+    cudaError_t err;
+    if (!pieces) {
+        err = hk::launch_prepare(p, s, validate, &nl);
+        if (err == cudaSuccess && pl.path != PATH_MARKS) err = hk::launch_scan_reduce(p, s, 0, pl.ng_max, &nl);
+    } else {
+        // every piece's events are checked, then composed by the scan's reduce pass, as soon as
+        // they are on the device, while the later pieces are still being copied; the checks of
+        // a piece come before any kernel that indexes with its marks
+        err = hk::launch_prepare_head(p, s, validate, &nl);
+        int64_t b_done = 0, g_done = 0;
+        for (int i = 0; i < pieces->n && err == cudaSuccess; ++i) {
+            const bool last = i == pieces->n - 1;
+            const int64_t b_end = last ? pl.nb_max : pieces->end[i] / pl.C;
+            err = cudaStreamWaitEvent(s, pieces->ev[i], 0);
+            if (err == cudaSuccess && validate) err = hk::launch_validate_chunks(p, s, b_done, b_end, &nl);
+            if (err == cudaSuccess && pl.path != PATH_MARKS) {
+                const int64_t g_end = last ? pl.ng_max : b_end / pl.Gc;
+                err = hk::launch_scan_reduce(p, s, g_done, g_end, &nl);
+                g_done = g_end;
+            }
+            if (err == cudaSuccess && pl.path == PATH_GEMM)
+                err = hk::launch_bucket_range(p, s, b_done, b_end, &nl);
+            b_done = b_end;
+        }
+        p.bucket_done = pl.path == PATH_GEMM ? 1 : 0;
+    }
     if (err == cudaSuccess) {
         if (pl.path == PATH_MARKS) {
             err = hk::launch_marks(p, pl.seg_len, s, &nl);
         } else {
-            err = hk::launch_scan(p, s, &nl);
+            err = hk::launch_scan_rest(p, s, &nl);
             if (err == cudaSuccess && pl.path == PATH_WALK) {
                 err = hk::launch_walk(p, s, &nl);
                 if (err == cudaSuccess) err = hk::launch_finalize(p, s, &nl);
@@ -459,6 +499,7 @@ hawkes_opts hawkes_default_opts(void) {
     o.support = 0;
     o.reduce = 0;
     o.fp32_times = 0;
+    o.walk_lanes = 0;
     return o;
 }
 
@@ -495,7 +536,7 @@ static hawkes_status single(const double* t, const int32_t* c, int64_t N, double
                             const hawkes_opts* opts, void* ws, size_t ws_bytes, double* out_ll,
                             float* d_mu, float* d_alpha, float* d_beta, int grad, void* stream,
                             const float* carry_S = nullptr, const float* carry_G = nullptr,
-                            int base_term = 1) {
+                            int base_term = 1, const Pieces* pieces = nullptr) {
     int rc = hk::check_single_args(t, c, N, T, M, mu, alpha, beta, opts, out_ll, d_mu, d_alpha,
                                    d_beta, grad);
     if (rc) return (hawkes_status)rc;
@@ -521,7 +562,7 @@ static hawkes_status single(const double* t, const int32_t* c, int64_t N, double
         if (carry_S || carry_G || !base_term) return HAWKES_ERR_UNSUPPORTED;
         return (hawkes_status)run_multi(p, opts, ws, ws_bytes, s);
     }
-    return (hawkes_status)run(p, opts, ws, ws_bytes, s);
+    return (hawkes_status)run(p, opts, ws, ws_bytes, s, pieces);
 }
 
 hawkes_status hawkes_loglik(const double* t, const int32_t* c, int64_t N, double T, int32_t M,
@@ -631,6 +672,30 @@ size_t hawkes_workspace_size_host(int64_t N, int32_t M, const hawkes_opts* opts)
     return align_up(dev) + host_staging_bytes(N, M, opts ? opts->beta_shared : 0);
 }
 
+// The host entry point's copy stream and events, created once per thread and device.
+struct HostPipe {
+    int dev = -1;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t start = nullptr;
+    cudaEvent_t ev[kMaxPieces] = {};
+};
+thread_local HostPipe g_pipe;
+
+static cudaError_t host_pipe() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (g_pipe.dev == dev) return cudaSuccess;
+    HostPipe h;
+    h.dev = dev;
+    e = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming);
+    for (int i = 0; i < kMaxPieces && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&h.ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) g_pipe = h;     // (a thread that changes devices keeps the old ones)
+    return e;
+}
+
 hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t N, double T,
                                       int32_t M, const float* mu, const float* alpha,
                                       const float* beta, const hawkes_opts* opts,
@@ -645,6 +710,8 @@ hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t
     if (!dev) return HAWKES_ERR_UNSUPPORTED;
     if (!workspace || workspace_bytes < hawkes_workspace_size_host(N, M, opts))
         return HAWKES_ERR_WORKSPACE;
+    Plan pl;
+    make_plan(N, M, 1, 1, opts, &pl);
     const int shared = opts ? opts->beta_shared : 0;
     const size_t nbeta = shared ? 1 : (size_t)M;
     char* st = (char*)workspace + align_up(dev);
@@ -660,10 +727,34 @@ hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t
     double* ll_d = (double*)take(sizeof(double));
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
+    // The events go to the device in pieces of whole scan groups on a second stream (one
+    // cudaMemcpyAsync per array and piece), each followed by an event that the kernels wait
+    // for, so that the checks and the scan's reduce pass of a piece run while the next
+    // piece is copied.  The copies wait for the work queued on `stream` before this call.
+    Pieces pieces{};
     if (N > 0) {
-        e = cudaMemcpyAsync(t_d, t, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c_d, c, sizeof(int32_t) * (size_t)N, cudaMemcpyHostToDevice, s);
+        e = host_pipe();
+        const int64_t unit = pl.path == PATH_MARKS ? (int64_t)pl.C : (int64_t)pl.Gc * pl.C;
+        int64_t np = N / ((int64_t)1 << 21);
+        if (np < 1) np = 1;
+        if (np > kMaxPieces) np = kMaxPieces;
+        int64_t len = (N + np - 1) / np;
+        len = (len + unit - 1) / unit * unit;
+        if (e == cudaSuccess) e = cudaEventRecord(g_pipe.start, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g_pipe.copy, g_pipe.start, 0);
+        for (int64_t a0 = 0; a0 < N && e == cudaSuccess; a0 += len) {
+            const int64_t b0 = a0 + len < N ? a0 + len : N;
+            const int64_t tb = b0 < N ? b0 + 1 : N;     // and the next piece's first time
+            e = cudaMemcpyAsync(t_d + a0, t + a0, sizeof(double) * (size_t)(tb - a0),
+                                cudaMemcpyHostToDevice, g_pipe.copy);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c_d + a0, c + a0, sizeof(int32_t) * (size_t)(b0 - a0),
+                                    cudaMemcpyHostToDevice, g_pipe.copy);
+            if (e == cudaSuccess) e = cudaEventRecord(g_pipe.ev[pieces.n], g_pipe.copy);
+            pieces.end[pieces.n] = b0;
+            pieces.ev[pieces.n] = g_pipe.ev[pieces.n];
+            ++pieces.n;
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(mu_d, mu, sizeof(float) * M, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
@@ -671,9 +762,13 @@ hawkes_status hawkes_loglik_grad_host(const double* t, const int32_t* c, int64_t
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(be_d, beta, sizeof(float) * nbeta, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return HAWKES_ERR_CUDA;
-    hawkes_status rc = hawkes_loglik_grad(t_d, c_d, N, T, M, mu_d, al_d, be_d, opts, workspace,
-                                          dev, ll_d, dmu_d, dal_d, dbe_d, stream);
-    if (rc != HAWKES_OK) return rc;
+    hawkes_status rc = single(t_d, c_d, N, T, M, mu_d, al_d, be_d, opts, workspace, dev, ll_d,
+                              dmu_d, dal_d, dbe_d, 1, stream, nullptr, nullptr, 1,
+                              pieces.n > 0 ? &pieces : nullptr);
+    if (rc != HAWKES_OK) {
+        cudaStreamSynchronize(g_pipe.copy);      // no copy may outlive the call
+        return rc;
+    }
     e = cudaMemcpyAsync(out_ll, ll_d, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_mu, dmu_d, sizeof(float) * M, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)

@@ -137,6 +137,8 @@ struct Problem {
     int32_t reduce;          // 0: FP64 log-sum; 1: Kahan FP32; 2: plain FP32
     int32_t fp32_times;      // ablation: time differences of FP32-rounded times
     float* ll_part;          // [2 * kLogSumBlocks] per-block (sum, error) of the FP32 log-sums
+    int32_t bucket_done;     // 1: the chunks were bucketed piece by piece as the events arrived
+    int32_t walk_lanes;      // state walk: lanes per walker (0 = from M)
     // outputs
     double* out_ll;          // [B]
     float* d_mu;
@@ -256,11 +258,19 @@ struct LogProd {
 // launch helpers implemented in the .cu files
 namespace hk {
 cudaError_t launch_prepare(const Problem& p, cudaStream_t s, int validate, int* nlaunch);
+cudaError_t launch_prepare_head(const Problem& p, cudaStream_t s, int validate, int* nlaunch);
+cudaError_t launch_validate_chunks(const Problem& p, cudaStream_t s, int64_t b_begin,
+                                   int64_t b_end, int* nlaunch);
 cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_scan_reduce(const Problem& p, cudaStream_t s, int64_t g_begin, int64_t g_end,
+                               int* nlaunch);
+cudaError_t launch_scan_rest(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_bucket_range(const Problem& p, cudaStream_t s, int64_t b_begin, int64_t b_end,
+                                int* nlaunch);
 cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nlaunch);
 
 // Several decay kernels: one workspace slice per kernel, each a complete single-kernel

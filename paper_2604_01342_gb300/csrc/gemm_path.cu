@@ -195,7 +195,8 @@ __host__ __device__ inline size_t bucket_smem_bytes(int P, int C, int M, int war
 }
 
 __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2* lrec,
-                                                uint2* bmask, int32_t* bstart, uint8_t* wide) {
+                                                uint2* bmask, int32_t* bstart, uint8_t* wide,
+                                                int64_t b_begin, int64_t b_end) {
     extern __shared__ int32_t sm_i[];
     const int P = p.P, C = p.C, W = (C + 31) >> 5;
     const int TR = (p.M + P - 1) / P, PT = P * TR;
@@ -211,9 +212,10 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
     for (int c = threadIdx.x; c < p.M; c += blockDim.x) qtab[c] = ((c / P) << 16) | (c % P);
     __syncthreads();
     const float beta = p.beta[0];
-    const int64_t nb = num_chunks(p);
+    const int64_t nb = num_chunks(p) < b_end ? num_chunks(p) : b_end;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t b = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += nw) {
+    for (int64_t b = b_begin + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); b < nb;
+         b += nw) {
         int64_t s0, s1;
         chunk_range(p, b, 0, s0, s1);
         const int n = (int)(s1 - s0);
@@ -799,8 +801,35 @@ int epilogue_blocks(int64_t N) {
     return (int)(blocks > 0 ? blocks : 1);
 }
 
+// Bucketing of chunks [b_begin, b_end) (clipped to the chunks of the call); it needs only
+// the chunks' offsets from the scan's reduce pass and their marks.
+cudaError_t launch_bucket_range(const Problem& p, cudaStream_t s, int64_t b_begin, int64_t b_end,
+                                int* nl) {
+    cudaError_t err;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int P = p.P;
+    if (b_end > p.nb_max) b_end = p.nb_max;
+    int warps = 8;
+    while (warps > 1 && bucket_smem_bytes(P, p.C, p.M, warps) > 227 * 1024) --warps;
+    const size_t smem = bucket_smem_bytes(P, p.C, p.M, warps);
+    if (smem > 48 * 1024) {
+        err = cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    int64_t grid = (b_end - b_begin + warps - 1) / warps;
+    if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+    k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 32 * warps, smem, s>>>(p, p.recs, p.lrec, p.bmask,
+                                                                    p.bstart, p.wide, b_begin, b_end);
+    ++*nl;
+    prof_mark(s, "bucket");
+    return cudaGetLastError();
+}
+
 // Everything of the chunk-GEMM path before the per-event epilogue: operand centres and
-// splits, Y and Z on the tensor cores, bucketing and the forward pairs.
+// splits, Y and Z on the tensor cores, bucketing (unless done piece by piece) and the
+// forward pairs.
 cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
     cudaError_t err;
     const int64_t M = p.M, nb = p.nb_max;
@@ -866,20 +895,10 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
         if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
         k_alpha_tiles<<<(unsigned)blocks, 256, 0, s>>>(p, p.at);
         ++*nl;
-        int warps = 8;
-        while (warps > 1 && bucket_smem_bytes(P, p.C, (int)M, warps) > 227 * 1024) --warps;
-        const size_t smem = bucket_smem_bytes(P, p.C, (int)M, warps);
-        if (smem > 48 * 1024) {
-            err = cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (!p.bucket_done) {
+            err = launch_bucket_range(p, s, 0, nb, nl);
             if (err != cudaSuccess) return err;
         }
-        int64_t grid = (nb + warps - 1) / warps;
-        if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
-        k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 32 * warps, smem, s>>>(p, p.recs, p.lrec,
-                                                                          p.bmask, p.bstart, p.wide);
-        ++*nl;
-        prof_mark(s, "bucket");
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     {
         // forward pairs: work items (row block, kFwdChunksPerItem chunks) from a counter in the header

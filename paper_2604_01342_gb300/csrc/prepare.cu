@@ -125,11 +125,12 @@ __device__ __forceinline__ uint64_t time_key(double t) {
     return (u >> 63) ? ~0ull : u;
 }
 
-__global__ void k_validate_events(Problem p, int chunks_per_block) {
+// Chunks [b_begin, b_end) of the call (b_end clipped to the number of chunks).
+__global__ void k_validate_events(Problem p, int chunks_per_block, int64_t b_begin, int64_t b_end) {
     __shared__ int32_t hist[kHistMax];
     if (failed(p.hdr)) return;
-    const int64_t nb = num_chunks(p);
-    const int64_t b0 = (int64_t)blockIdx.x * chunks_per_block;
+    const int64_t nb = num_chunks(p) < b_end ? num_chunks(p) : b_end;
+    const int64_t b0 = b_begin + (int64_t)blockIdx.x * chunks_per_block;
     if (b0 >= nb) return;
     const int64_t b1 = b0 + chunks_per_block < nb ? b0 + chunks_per_block : nb;
     const int32_t seq0 = p.chunk_seq[b0], seq1 = p.chunk_seq[b1 - 1];
@@ -169,10 +170,12 @@ __global__ void k_validate_events(Problem p, int chunks_per_block) {
             if (hist[i])
                 atomicAdd((unsigned long long*)&p.counts[(int64_t)seq0 * p.M + i],
                           (unsigned long long)hist[i]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.hdr->validated = 1;
+    if (b0 == 0 && threadIdx.x == 0) p.hdr->validated = 1;
 }
 
-cudaError_t launch_prepare(const Problem& p, cudaStream_t s, int validate, int* nl) {
+// Everything of the preparation that reads no event: accumulators, header, parameter checks,
+// chunk table.
+cudaError_t launch_prepare_head(const Problem& p, cudaStream_t s, int validate, int* nl) {
     // accumulators are one contiguous run of doubles starting at ll_acc
     int64_t n_acc = (int64_t)p.B * (1 + 4 * (int64_t)p.M) +
                     (p.grad ? (int64_t)p.B * p.M * p.M : 0);
@@ -190,15 +193,26 @@ cudaError_t launch_prepare(const Problem& p, cudaStream_t s, int validate, int* 
     k_chunk_seq<<<p.B < 4096 ? p.B : 4096, 128, 0, s>>>(p);
     *nl += 2;
     prof_mark(s, "chunk_seq");
-    if (validate) {
-        const int cpb = 16;
-        int64_t blocks = (p.nb_max + cpb - 1) / cpb;
-        if (blocks < 1) blocks = 1;
-        k_validate_events<<<(unsigned)blocks, 256, 0, s>>>(p, cpb);
-        ++*nl;
-        prof_mark(s, "validate_events");
-    }
     return cudaGetLastError();
+}
+
+// The event checks and counts of chunks [b_begin, b_end).
+cudaError_t launch_validate_chunks(const Problem& p, cudaStream_t s, int64_t b_begin,
+                                   int64_t b_end, int* nl) {
+    const int cpb = 16;
+    if (b_end > p.nb_max) b_end = p.nb_max;
+    int64_t blocks = (b_end - b_begin + cpb - 1) / cpb;
+    if (blocks < 1) blocks = 1;
+    k_validate_events<<<(unsigned)blocks, 256, 0, s>>>(p, cpb, b_begin, b_end);
+    ++*nl;
+    prof_mark(s, "validate_events");
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(const Problem& p, cudaStream_t s, int validate, int* nl) {
+    cudaError_t err = launch_prepare_head(p, s, validate, nl);
+    if (err == cudaSuccess && validate) err = launch_validate_chunks(p, s, 0, p.nb_max, nl);
+    return err;
 }
 
 }  // namespace hk

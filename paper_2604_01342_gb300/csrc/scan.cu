@@ -34,7 +34,7 @@ __host__ __device__ inline size_t scan_smem_floats(int M, int threads) {
 }
 
 template <int PHASE, bool GRAD>
-__global__ void __launch_bounds__(256) k_scan_group(Problem p) {
+__global__ void __launch_bounds__(256) k_scan_group(Problem p, int64_t g_begin) {
     extern __shared__ float sm[];
     float* S = sm;
     float* G = sm + p.M;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_scan_group(Problem p) {
     __shared__ int reset_sh;
     if (failed(p.hdr)) return;
     const int64_t nb = num_chunks(p);
-    const int64_t g = blockIdx.x;
+    const int64_t g = g_begin + blockIdx.x;
     const int64_t b0 = g * p.Gc;
     if (b0 >= nb) return;
     const int64_t b1 = b0 + p.Gc < nb ? b0 + p.Gc : nb;
@@ -377,9 +377,12 @@ __global__ void __launch_bounds__(256) k_scan_states_fast(Problem p) {
 // the chunk-GEMM path's pass C: one sequence, one shared decay, offsets written by pass A
 static bool fast_states(const Problem& p) { return p.delta != nullptr && p.shared && p.B == 1; }
 
-cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
-    const size_t smem_fast = sizeof(float) * 2 * (size_t)p.M;
-    size_t smem = sizeof(float) * scan_smem_floats(p.M, 128);
+static size_t scan_smem_bytes(const Problem& p) {
+    return sizeof(float) * scan_smem_floats(p.M, 128);
+}
+
+static cudaError_t scan_attributes(const Problem& p) {
+    const size_t smem = scan_smem_bytes(p);
     if (smem > 48 * 1024) {       // large M on the chunk-GEMM path: opt in to more shared memory
         const void* kerns[] = {(const void*)k_scan_group<0, true>, (const void*)k_scan_group<1, true>,
                                (const void*)k_scan_group<0, false>, (const void*)k_scan_group<1, false>,
@@ -389,6 +392,29 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
             if (e != cudaSuccess) return e;
         }
     }
+    return cudaSuccess;
+}
+
+// Pass A over the scan groups [g_begin, g_end) (clipped to the groups of the call).
+cudaError_t launch_scan_reduce(const Problem& p, cudaStream_t s, int64_t g_begin, int64_t g_end,
+                               int* nl) {
+    cudaError_t err = scan_attributes(p);
+    if (err != cudaSuccess) return err;
+    if (g_end > p.ng_max) g_end = p.ng_max;
+    const unsigned grid = (unsigned)(g_end > g_begin ? g_end - g_begin : 1);
+    if (p.grad) k_scan_group<0, true><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
+    else k_scan_group<0, false><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
+    ++*nl;
+    prof_mark(s, "scan_reduce");
+    return cudaGetLastError();
+}
+
+// Passes B and C: the carry into every group, then the chunk-start states.
+cudaError_t launch_scan_rest(const Problem& p, cudaStream_t s, int* nl) {
+    cudaError_t err = scan_attributes(p);
+    if (err != cudaSuccess) return err;
+    const size_t smem_fast = sizeof(float) * 2 * (size_t)p.M;
+    const size_t smem = scan_smem_bytes(p);
     unsigned grid = (unsigned)(p.ng_max > 0 ? p.ng_max : 1);
     // segments of the carry pass: enough (mark, segment) threads for every SM, at least
     // four groups per segment
@@ -398,26 +424,28 @@ cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
     if (Q < 1) Q = 1;
     const dim3 cgrid((unsigned)((p.M + 127) / 128), (unsigned)Q);
     if (p.grad) {
-        k_scan_group<0, true><<<grid, 128, smem, s>>>(p);
-        prof_mark(s, "scan_reduce");
         k_carry_compose<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<true><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
         if (fast_states(p)) k_scan_states_fast<true><<<grid, 128, smem_fast, s>>>(p);
-        else k_scan_group<1, true><<<grid, 128, smem, s>>>(p);
+        else k_scan_group<1, true><<<grid, 128, smem, s>>>(p, 0);
         prof_mark(s, "scan_states");
     } else {
-        k_scan_group<0, false><<<grid, 128, smem, s>>>(p);
-        prof_mark(s, "scan_reduce");
         k_carry_compose<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         k_carry_walk<false><<<cgrid, 128, 0, s>>>(p, (int)Q, p.seg_comp);
         prof_mark(s, "scan_carry");
         if (fast_states(p)) k_scan_states_fast<false><<<grid, 128, smem_fast, s>>>(p);
-        else k_scan_group<1, false><<<grid, 128, smem, s>>>(p);
+        else k_scan_group<1, false><<<grid, 128, smem, s>>>(p, 0);
         prof_mark(s, "scan_states");
     }
-    *nl += 4;
+    *nl += 3;
     return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const Problem& p, cudaStream_t s, int* nl) {
+    cudaError_t err = launch_scan_reduce(p, s, 0, p.ng_max, nl);
+    if (err == cudaSuccess) err = launch_scan_rest(p, s, nl);
+    return err;
 }
 
 }  // namespace hk

@@ -348,7 +348,7 @@ cudaError_t launch_walk(const Problem& p, cudaStream_t s, int* nl) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // a walker is a group of W lanes (W = 8 or 16 when every mark fits one lane of it, so
     // that a warp walks 32 / W chunks at a time)
-    const int W = p.M <= 8 ? 8 : (p.M <= 16 ? 16 : 32);
+    const int W = p.walk_lanes ? p.walk_lanes : (p.M <= 8 ? 8 : (p.M <= 16 ? 16 : 32));
     const int groups = 32 / W;
     const int warps_per_block = 4;
     const int per_walker = walk_floats_per_warp(p.M, p.grad != 0);

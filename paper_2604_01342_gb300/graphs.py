@@ -54,7 +54,7 @@ class GraphedLogLikGrad:
 
     @classmethod
     def single(cls, t, c, T: float, mu, alpha, beta, beta_shared=None, chunk: int = 0,
-               path: int = 0):
+               path: int = 0, walk_lanes: int = 0):
         """One sequence: t float64 [N], c int32 [N], mu [M], alpha [M,M], beta [1] or [M]."""
         for x, dt, n in ((t, torch.float64, "t"), (c, torch.int32, "c"), (mu, torch.float32, "mu"),
                          (alpha, torch.float32, "alpha"), (beta, torch.float32, "beta")):
@@ -62,7 +62,7 @@ class GraphedLogLikGrad:
         dev = t.device
         N, M = t.shape[0], mu.shape[0]
         shared = bool(beta_shared) if beta_shared is not None else (beta.numel() == 1 and M != 1)
-        opts = _b.make_opts(shared, chunk, True, path)
+        opts = _b.make_opts(shared, chunk, True, path, walk_lanes=walk_lanes)
         nbytes = _b.hawkes_workspace_size(N, M, 1, True, opts)
         ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
         ll = torch.empty((), dtype=torch.float64, device=dev)
@@ -79,7 +79,7 @@ class GraphedLogLikGrad:
 
     @classmethod
     def varlen(cls, t, c, offsets, T, mu, alpha, beta, beta_shared=None, chunk: int = 0,
-               path: int = 0):
+               path: int = 0, walk_lanes: int = 0):
         """B sequences: offsets int64 [B+1], T float64 [B], mu [B,M], alpha [B,M,M], beta [B] or [B,M]."""
         for x, dt, n in ((t, torch.float64, "t"), (c, torch.int32, "c"),
                          (offsets, torch.int64, "offsets"), (T, torch.float64, "T"),
@@ -89,7 +89,7 @@ class GraphedLogLikGrad:
         dev = t.device
         B, N, M = offsets.shape[0] - 1, t.shape[0], mu.shape[-1]
         shared = bool(beta_shared) if beta_shared is not None else (beta.numel() == B and M != 1)
-        opts = _b.make_opts(shared, chunk, True, path)
+        opts = _b.make_opts(shared, chunk, True, path, walk_lanes=walk_lanes)
         nbytes = _b.hawkes_workspace_size(N, M, B, True, opts)
         ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
         ll = torch.empty(B, dtype=torch.float64, device=dev)

@@ -58,7 +58,8 @@ def _stream(device):
 
 def loglik_grad(t, c, T, mu, alpha, beta, beta_shared=None, chunk: int = 0, path: int = 0,
                 validate: bool = True, check: bool = True, grad: bool = True,
-                support: bool = False, reduce: int = 0, fp32_times: bool = False):
+                support: bool = False, reduce: int = 0, fp32_times: bool = False,
+                walk_lanes: int = 0):
     """L (float64 0-d) and, if ``grad``, (dmu, dalpha, dbeta) as float32 tensors.
     ``support=True``: dalpha on alpha's support (entries alpha == 0 get 0).  ``reduce`` and
     ``fp32_times``: the precision options of hawkes_opts (chunk-GEMM path)."""
@@ -67,7 +68,7 @@ def loglik_grad(t, c, T, mu, alpha, beta, beta_shared=None, chunk: int = 0, path
     N, M = t.shape[0], mu.shape[0]
     shared = _shared(beta, M, beta_shared)
     opts = _b.make_opts(shared, chunk, validate, path, support=support, reduce=reduce,
-                        fp32_times=fp32_times)
+                        fp32_times=fp32_times, walk_lanes=walk_lanes)
     nbytes = _b.hawkes_workspace_size(N, M, 1, grad, opts)
     ws = _workspace(nbytes, dev)
     out_ll = torch.empty((), dtype=torch.float64, device=dev)
@@ -94,7 +95,7 @@ def loglik_grad(t, c, T, mu, alpha, beta, beta_shared=None, chunk: int = 0, path
 
 def loglik_grad_varlen(t, c, offsets, T, mu, alpha, beta, beta_shared=None, chunk: int = 0,
                        path: int = 0, validate: bool = True, check: bool = True,
-                       grad: bool = True):
+                       grad: bool = True, walk_lanes: int = 0):
     """Per-sequence L [B] (float64) and, if ``grad``, dmu [B,M], dalpha [B,M,M], dbeta [B] or [B,M]."""
     t, c, mu, alpha, beta = _prep(t, c, mu, alpha, beta)
     dev = t.device
@@ -104,7 +105,7 @@ def loglik_grad_varlen(t, c, offsets, T, mu, alpha, beta, beta_shared=None, chun
     N = t.shape[0]
     M = mu.shape[-1]
     shared = bool(beta_shared) if beta_shared is not None else (beta.numel() == B and M != 1)
-    opts = _b.make_opts(shared, chunk, validate, path)
+    opts = _b.make_opts(shared, chunk, validate, path, walk_lanes=walk_lanes)
     nbytes = _b.hawkes_workspace_size(N, M, B, grad, opts)
     ws = _workspace(nbytes, dev)
     out_ll = torch.empty(B, dtype=torch.float64, device=dev)

@@ -94,3 +94,26 @@ def test_missing_workspace_is_reported_without_a_gpu(lib):
     rc = lib.hawkes_loglik(ptr(t), ptr(c), 5, 1.0, 3, ptr(mu), ptr(al), ptr(be),
                            ctypes.byref(opts), None, 0, ptr(ll), None)
     assert rc == 7   # workspace missing
+
+
+def test_walk_lanes_option_is_checked(lib):
+    ok = binding.make_opts(False, 0, True, 1, walk_lanes=8)
+    assert lib.hawkes_workspace_size(1000, 8, 1, 1, ctypes.byref(ok)) > 0
+    for lanes, M in ((8, 9), (16, 17), (12, 4)):
+        bad = binding.make_opts(False, 0, True, 1, walk_lanes=lanes)
+        assert lib.hawkes_workspace_size(1000, M, 1, 1, ctypes.byref(bad)) == 0
+
+
+def test_autotune_file_cache_round_trip(tmp_path):
+    from paper_2604_01342_gb300 import autotune
+    path = str(tmp_path / "sub" / "tune.json")
+    autotune._store_file(path, "gpu|sms=152|N=10|B=1|M=4|shared=1", {"path": 1, "chunk": 64})
+    autotune._store_file(path, "gpu|sms=152|N=20|B=1|M=4|shared=1", {"path": 2, "chunk": 192})
+    data = autotune._load_file(path)
+    assert data["gpu|sms=152|N=10|B=1|M=4|shared=1"]["chunk"] == 64
+    assert len(data) == 2
+    assert autotune._load_file(str(tmp_path / "missing.json")) == {}
+    # candidates: lanes for small M on the walk, segment lengths on the mark-major path
+    assert (1, 128, 8) in autotune._candidates(8, False, 1)
+    assert (1, 128, 16) not in autotune._candidates(20, False, 1)
+    assert all(p == 3 for p, _, _ in autotune._candidates(4096, False, 1))

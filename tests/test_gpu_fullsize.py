@@ -157,6 +157,9 @@ def test_m1024_full_size_matches_oracle(c4, c4_oracle, c4_gpu):
 def test_m1024_full_size_dbeta(c4, c4_oracle, c4_gpu):
     ref = c4_oracle.get()
     e = maxnorm_rel(c4_gpu["dbeta"], ref["dbeta"])
+    whole = maxnorm_rel(np.concatenate([c4_gpu[k].ravel() for k in ("dmu", "dalpha", "dbeta")]),
+                        np.concatenate([ref[k].ravel() for k in ("dmu", "dalpha", "dbeta")]))
     print(f"M=1024 full 1e7: dbeta rel err {e:.3e} (gpu {c4_gpu['dbeta'][0]!r}, "
-          f"oracle {ref['dbeta'][0]!r})")
+          f"oracle {ref['dbeta'][0]!r}); max-norm relative error of the whole gradient "
+          f"(mu, alpha, beta together) {whole:.3e}")
     assert e <= 1e-4

@@ -92,18 +92,25 @@ def test_graph_single_gemm_path():
     assert_close(got, oracle_ref(p), what="graphed gemm path")
 
 
-def test_autotune_returns_cached_valid_choice():
+def test_autotune_returns_cached_valid_choice(tmp_path):
     import torch
     from paper_2604_01342_gb300 import autotune, torch_api
     p = synth.random_problem(48, 20000, seed=24, shared_beta=True)
     t, c, T, mu, al, be = _dev_single(p)
-    best = autotune.tune(t, c, T, mu, al, be, beta_shared=True)
+    path = str(tmp_path / "tune.json")
+    best = autotune.tune(t, c, T, mu, al, be, beta_shared=True, cache_path=path)
     print("autotune:", best)
-    cands = autotune._candidates(48, True)
-    assert (best["path"], best["chunk"]) in cands
-    assert autotune.tune(t, c, T, mu, al, be, beta_shared=True) is best
+    cands = autotune._candidates(48, True, 1)
+    assert (best["path"], best["chunk"], best["walk_lanes"]) in cands
+    assert autotune.tune(t, c, T, mu, al, be, beta_shared=True, cache_path=path) is best
+    # a new process (an empty memory cache) finds it in the file
+    autotune._cache.clear()
+    again = autotune.tune(t, c, T, mu, al, be, beta_shared=True, cache_path=path)
+    assert (again["path"], again["chunk"], again["walk_lanes"]) == \
+        (best["path"], best["chunk"], best["walk_lanes"])
     ll, dmu, dal, dbe = torch_api.loglik_grad(t, c, T, mu, al, be, beta_shared=True,
-                                              chunk=best["chunk"], path=best["path"])
+                                              chunk=best["chunk"], path=best["path"],
+                                              walk_lanes=best["walk_lanes"])
     torch.cuda.synchronize()
     got = {"ll": float(ll.item()), "dmu": dmu.cpu().numpy().astype(np.float64),
            "dalpha": dal.cpu().numpy().astype(np.float64),
@@ -118,9 +125,11 @@ def test_batched_workload_as_one_graph():
     from paper_2604_01342_gb300.graphs import GraphedLogLikGrad
     vp = synth.workload(3)
     t, c, off, T, mu, al, be = _dev_varlen(vp)
-    best = autotune.tune(t, c, T, mu, al, be, beta_shared=False, offsets=off)
+    best = autotune.tune(t, c, T, mu, al, be, beta_shared=False, offsets=off, cache_path=None)
+    assert best["walk_lanes"] in (8, 16, 32)        # the lanes of a walker are tuned too (M = 8)
     g = GraphedLogLikGrad.varlen(t, c, off, T, mu, al, be, beta_shared=False,
-                                 chunk=best["chunk"], path=best["path"])
+                                 chunk=best["chunk"], path=best["path"],
+                                 walk_lanes=best["walk_lanes"])
     for _ in range(3):
         g.replay()
     s = torch.cuda.current_stream()
