@@ -38,7 +38,7 @@ struct Plan {
     int64_t nb_max, ng_max;
     size_t off_counts, off_chunk_base, off_chunk_seq, off_Shat, off_Ghat, off_grp_v, off_grp_g,
         off_grp_dt, off_grp_reset, off_seg_comp, off_carry_S, off_carry_G, off_acc, off_Y, off_Z, off_W,
-        off_dal_gemm, off_al_p, off_S_p, off_G_p, off_Wt_p, off_St_p, off_recs, off_lrec, off_bmask, off_kprep, off_dal_part, off_bstart, off_wide, off_Aint, off_Bint, off_wbuf, off_delta, off_Dspan, off_Tmt,
+        off_dal_gemm, off_al_p, off_S_p, off_G_p, off_Wt_p, off_St_p, off_recs, off_src, off_kprep, off_dal_part, off_bstart, off_bsub, off_pwork, off_pcum, off_ptot, off_plan_b, off_wide, off_Aint, off_Bint, off_wbuf, off_delta, off_Dspan, off_Tmt,
         off_cen, off_wsum, off_colsum, off_at, off_isc, off_colmax, total;
     // mark-major walk
     size_t off_rowptr, off_supcol, off_supval, off_tcnt, off_segoff, off_segt, off_segf;
@@ -46,7 +46,7 @@ struct Plan {
     int64_t seg_len;
     int nseg, ntiles, seg_tiles, tile_warps;
     int64_t ldk, ldt, nbp;
-    int dal_parts_max;
+    hk::PairRows rows;     // row blocks of the pair kernels
     int K;                 // decay kernels (one workspace slice each)
     size_t scratch_off;
     size_t slice;          // bytes of one slice
@@ -167,26 +167,28 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
     pl->ldt = (pl->nbp + 31) / 32 * 64;
     pl->off_Y = pl->off_Z = pl->off_W = pl->off_dal_gemm = 0;
     pl->off_al_p = pl->off_S_p = pl->off_G_p = pl->off_Wt_p = pl->off_St_p = 0;
-    pl->off_recs = pl->off_lrec = pl->off_bmask = pl->off_kprep = pl->off_dal_part = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
+    pl->off_recs = pl->off_src = pl->off_kprep = pl->off_dal_part = pl->off_bstart = pl->off_wide = pl->off_Aint = pl->off_Bint = pl->off_wbuf = 0;
+    pl->off_bsub = pl->off_pwork = pl->off_pcum = pl->off_ptot = pl->off_plan_b = 0;
     pl->off_delta = pl->off_Dspan = pl->off_Tmt = 0;
     pl->off_cen = pl->off_wsum = pl->off_at = pl->off_isc = pl->off_colmax = 0;
-    pl->dal_parts_max = 0;
+    pl->rows = hk::pair_rows(M, pl->P);
     if (path == PATH_GEMM) {
         const size_t h = 2;   // fp16 operand halves
         const size_t P = (size_t)pl->P;
         pl->off_recs = take(16 * (size_t)(N > 0 ? N : 1));
-        pl->off_lrec = take(8 * (size_t)(N > 0 ? N : 1));
-        pl->off_bmask = take(sizeof(uint2) * (size_t)pl->nb_max * P * (size_t)((C + 31) / 32));
+        pl->off_src = take(8 * (size_t)(N > 0 ? N : 1));
         if (grad) pl->off_kprep = take(16 * (size_t)(N > 0 ? N : 1));
-        // backward pair tiles (ceil(M / P) square each): up to 2560 / P^2 chunk ranges per
-        // tile, at most one per chunk, at least one
+        // row blocks of the backward pairs: their first slots per chunk, work per chunk and
+        // its prefix, the plan, and one R x M partial per plan block
         {
-            int64_t r = 2560 / (int64_t)(P * P);
-            if (r > pl->nb_max) r = pl->nb_max;
-            pl->dal_parts_max = (int)(r > 0 ? r : 1);
-            const size_t tr = ((size_t)M + P - 1) / P;
-            if (grad) pl->off_dal_part = take(sizeof(float) * (size_t)pl->dal_parts_max * P * P * tr * tr);
-            if (grad) pl->off_redo = take(sizeof(int32_t) * (size_t)pl->dal_parts_max * P * P);
+            const size_t n_rb = (size_t)pl->rows.n_rb, slots = (size_t)pl->rows.slots;
+            pl->off_bsub = take(sizeof(int32_t) * (size_t)pl->nb_max * (n_rb + 1));
+            pl->off_pwork = take(sizeof(int32_t) * n_rb * (size_t)pl->nb_max);
+            pl->off_pcum = take(sizeof(int64_t) * n_rb * ((size_t)pl->nb_max + 1));
+            pl->off_ptot = take(sizeof(int64_t) * n_rb);
+            pl->off_plan_b = take(sizeof(int32_t) * (1 + 2 * n_rb + slots));
+            if (grad) pl->off_dal_part = take(sizeof(float) * slots * ((size_t)M << pl->rows.lgR));
+            if (grad) pl->off_redo = take(sizeof(int32_t) * slots);
         }
         pl->off_at = take(sizeof(float) * P * P * 128 * 128);
         pl->off_bstart = take(sizeof(int32_t) * (size_t)pl->nb_max * (P + 1));
@@ -278,14 +280,20 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.Wt_p = at<__half>(ws, pl.off_Wt_p);
     p.St_p = at<__half>(ws, pl.off_St_p);
     p.recs = at<float4>(ws, pl.off_recs);
-    p.lrec = at<float2>(ws, pl.off_lrec);
-    p.bmask = at<uint2>(ws, pl.off_bmask);
+    p.src = at<float2>(ws, pl.off_src);
     p.kprep = at<int4>(ws, pl.off_kprep);
     p.dal_part = at<float>(ws, pl.off_dal_part);
-    p.dal_parts_max = pl.dal_parts_max;
-    p.dal_parts = 0;
     p.scratch = at<float>(ws, pl.scratch_off);
+    p.bsub = at<int32_t>(ws, pl.off_bsub);
+    p.pwork = at<int32_t>(ws, pl.off_pwork);
+    p.pcum = at<int64_t>(ws, pl.off_pcum);
+    p.ptot = at<int64_t>(ws, pl.off_ptot);
     p.at = at<float>(ws, pl.off_at);
+    p.plan_b = at<int32_t>(ws, pl.off_plan_b);
+    p.lgR = pl.rows.lgR;
+    p.nrb = pl.rows.nrb;
+    p.n_rb = pl.rows.n_rb;
+    p.pair_slots = pl.rows.slots;
     p.bstart = at<int32_t>(ws, pl.off_bstart);
     p.wide = at<uint8_t>(ws, pl.off_wide);
     p.Aint = at<float>(ws, pl.off_Aint);

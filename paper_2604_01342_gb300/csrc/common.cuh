@@ -67,10 +67,8 @@ struct Problem {
     double* ll_acc;          // [B]   sum of log lambda
     double* dmu_acc;         // [B*M] sum of w over events of each mark
     double* dal_acc;         // [B*M*M]
-    float* dal_part;         // [dal_parts][P*P][128*128] backward pair tiles of the chunk-GEMM path
-    int32_t dal_parts;       // chunk ranges of the backward pair kernel (set at launch)
-    int32_t dal_parts_max;   // capacity of dal_part in ranges
-    int32_t* pair_redo;      // [dal_parts_max * P * P] blocks of the backward pairs to redo in FP32
+    float* dal_part;         // [pair_slots][R][M] partial dalpha rows of the backward pair blocks
+    int32_t* pair_redo;      // [pair_slots] blocks of the backward pairs to redo in FP32
     float* scratch;          // [M + 2] outputs of a slice that the caller does not see
     double* dbe_acc;         // [B*M] excitation part of dbeta
     double* E_acc;           // [B*M] sum (1 - exp(-beta (T - t))) per source
@@ -93,12 +91,23 @@ struct Problem {
     uint32_t* colmax;        // [M] column maxima scratch of the transposed operands
     // intra-chunk pair kernels
     float4* recs;            // [N]  events bucketed by mark block inside each chunk
-    float2* lrec;            // [N]  (ep, column) of the same buckets, each in index order
-    uint2* bmask;            // [nb_max * P * W] bucket membership words and the members
-                             // in the words before, W = ceil(C / 32)
+    float2* src;             // [N]  (ep, mark) of every event in index order (backward sources)
     int4* kprep;             // [N]  backward row-group data of every bucket slot
-    float* at;               // [P*P*128*128] alpha in tile-major order
+    float* at;               // [P*P*128*128] alpha in tile-major order (forward pairs)
     int32_t* bstart;         // [nb_max * (P+1)] bucket offsets inside each chunk
+    // row blocks of the backward pairs: R (a power of two) positions of one mark block, i.e.
+    // marks I + P pos for pos in [q R, q R + R), row block I * nrb + q
+    int32_t lgR;             // log2 R
+    int32_t nrb;             // row blocks per mark block, ceil(ceil(M / P) / R)
+    int32_t n_rb;            // P * nrb
+    int32_t pair_slots;      // blocks the pair plan can hand out (target blocks + n_rb)
+    int32_t* bsub;           // [nb_max * (n_rb + 1)] first bucket slot of every row block, then n
+    int32_t* pwork;          // [n_rb * nb_max] backward work of every (row block, chunk)
+    int64_t* pcum;           // [n_rb * (nb_max + 1)] its prefix over the chunks
+    int64_t* ptot;           // [n_rb] its total
+    int32_t* plan_b;         // backward pair plan: [0] blocks used, [1 + rb] blocks of row
+                             //   block rb, [1 + n_rb + rb] its first block, then
+                             //   [1 + 2 n_rb + x] = rb << 16 | k for block x
     uint8_t* wide;           // [nb_max] chunk spans too wide for the factorised weights
     float* Aint;             // [N]  sum_{l<k in chunk} P_kl alpha[c_k][c_l]
     float* Bint;             // [N]  same, weighted by (t_k - t_l)
@@ -272,6 +281,37 @@ cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nlaunch)
 cudaError_t launch_bucket_range(const Problem& p, cudaStream_t s, int64_t b_begin, int64_t b_end,
                                 int* nlaunch);
 cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nlaunch);
+
+// ---------------------------------------------------------------------------
+// Intra-chunk pairs of the chunk-GEMM path (pairs.cu, with the bucketing in gemm_path.cu).
+// A bucketed record is (delta, em, ep, index << 16 | position): delta = t - t of the chunk's
+// first event, em = exp(-beta delta), ep = exp(+beta delta) (0 in a wide chunk), the
+// event's index in its chunk and the position c / P of its mark c in mark block c mod P.
+// ---------------------------------------------------------------------------
+constexpr float kWideLimit = 64.f;      // beta * span above which sums of exp(+beta delta) may overflow
+constexpr int kPairTileFloats = 32768;  // shared-memory rows of one backward pair block: R M <= this
+constexpr int kPairBlocksMax = 1024;    // thread blocks the backward pair plan aims at, at most
+__device__ __forceinline__ int rec_idx(float4 r) { return __float_as_int(r.w) >> 16; }
+__device__ __forceinline__ int rec_pos(float4 r) { return __float_as_int(r.w) & 0xffff; }
+// Row blocks of the backward pairs: R = 2^lgR positions of one mark block (the largest power of two with R M
+// words in kPairTileFloats, and no larger than the block's ceil(M / P) positions need),
+// nrb of them per mark block, n_rb = P nrb in all.
+struct PairRows {
+    int lgR, nrb, n_rb, slots;
+};
+__host__ __device__ inline PairRows pair_rows(int M, int P) {
+    const int TR = (M + P - 1) / P;
+    int lg = 0;
+    while ((int64_t)(2 << lg) * M <= kPairTileFloats && (1 << lg) < TR) ++lg;
+    PairRows r;
+    r.lgR = lg;
+    r.nrb = (TR + (1 << lg) - 1) >> lg;
+    r.n_rb = P * r.nrb;
+    r.slots = kPairBlocksMax + r.n_rb;
+    return r;
+}
+cudaError_t launch_pairs_forward(const Problem& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_pairs_backward(const Problem& p, cudaStream_t s, int* nlaunch);
 
 // Several decay kernels: one workspace slice per kernel, each a complete single-kernel
 // problem; the epilogue and the last step of the finalisation combine the slices.

@@ -73,11 +73,10 @@ __global__ void k_finalize_vec(Problem p, const double* colsum) {
 // Entries outside alpha's support are 0 when the caller asked for the gradient on the
 // support (p.support).
 // mode 0: X = dal_acc (already carries beta_j);
-// mode 1: X = beta * (dal_gemm + m_j wsum_i + sum_r part_r[i][j])  (chunk-GEMM path, one
+// mode 1: X = beta * (dal_gemm + m_j wsum_i + sum_k part_k[i][j])  (chunk-GEMM path, one
 //         shared beta; the GEMM ran on S^ - m, so m_j sum_b W[b][i] restores the centre;
-//         part_r are the intra-chunk pair tiles of chunk range r (ceil(M / P) square,
-//         tile-major), summed in range order).  Mode 1 walks the elements in the tiles'
-//         order, so that the reads of the R pair tiles are contiguous.
+//         part_k are the shares of row i's row block written by the backward pair blocks of
+//         the plan, rows of M floats, summed in share order).
 __global__ void k_finalize_alpha(Problem p, int mode) {
     const int M = p.M;
     const bool bad = failed(p.hdr);
@@ -95,28 +94,29 @@ __global__ void k_finalize_alpha(Problem p, int mode) {
         return;
     }
     const float beta = p.beta[0];
-    const int P = p.P, TR = (M + P - 1) / P;
-    const int64_t stride = (int64_t)P * P * TR * TR;
-    for (int64_t at = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; at < stride;
-         at += (int64_t)gridDim.x * blockDim.x) {
-        // at = ((qi * P + qj) * TR + ti) * TR + tj  <->  i = ti * P + qi, j = tj * P + qj
-        const int tj = (int)(at % TR);
-        const int64_t r1 = at / TR;
-        const int ti = (int)(r1 % TR);
-        const int q = (int)(r1 / TR);
-        const int qi = q / P, qj = q % P;
-        const int i = ti * P + qi, j = tj * P + qj;
-        if (i >= M || j >= M) continue;
-        // compensated FP32 sum of the chunk ranges' tiles (FP64 arithmetic runs at 1/64 of
-        // the FP32 rate here)
-        float pairs = 0.f, comp = 0.f;
-        for (int r = 0; r < p.dal_parts; ++r) {
-            const float y = p.dal_part[r * stride + at] - comp;
-            const float t = pairs + y;
-            comp = (t - pairs) - y;
-            pairs = t;
+    const int P = p.P, n_rb = p.n_rb, R = 1 << p.lgR;
+    const int64_t total = (int64_t)M * M;
+    for (int64_t ij = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ij < total;
+         ij += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(ij / M), j = (int)(ij % M);
+        float pairs = 0.f;
+        if (!bad) {
+            // row i = I + P pos is row pos mod R of row block I nrb + pos / R
+            const int I = i % P, pos = i / P;
+            const int rb = I * p.nrb + (pos >> p.lgR);
+            const int nr = p.plan_b[1 + rb], base = p.plan_b[1 + n_rb + rb];
+            const float* part = p.dal_part + ((((int64_t)base << p.lgR) + (pos & (R - 1))) * M + j);
+            const int64_t step = (int64_t)R * M;
+            // compensated FP32 sum of the shares (FP64 arithmetic runs at 1/64 of the FP32
+            // rate here)
+            float comp = 0.f;
+            for (int k = 0; k < nr; ++k) {
+                const float y = part[k * step] - comp;
+                const float t = pairs + y;
+                comp = (t - pairs) - y;
+                pairs = t;
+            }
         }
-        const int64_t ij = (int64_t)i * M + j;
         const double x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] +
                                          (double)pairs);
         double v = x - p.E_acc[j];

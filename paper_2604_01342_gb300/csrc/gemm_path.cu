@@ -119,93 +119,48 @@ __global__ void k_centres(Problem p, int want_z) {
 }
 
 // ---------------------------------------------------------------------------
-// Intra-chunk pairs through shared-memory tiles of alpha.
+// Bucketing of every chunk's events for the intra-chunk pairs (pairs.cu).
 //
-// The pairs (k, l) of one chunk with l before k need alpha[c_k][c_l].  Gathering
-// those from L2 costs a 32-byte sector per pair, so instead the marks are dealt
-// round-robin into P = ceil(M / 128) blocks (block of mark c = c mod P, position
-// c / P; dealing spreads the few very frequent marks of a skewed mark distribution
-// over all blocks), alpha is copied once into tile-major order, and every chunk's
-// events are bucketed by block (k_bucket).  The forward kernel takes work items
-// (row block I, range of chunks) from a global counter and, for each column block J,
-// keeps tile (I, J) of alpha in shared memory while pairing the chunk's bucket-I
-// events (one per lane) with its bucket-J events.  The backward kernel owns one
-// tile (I, J) of dalpha in shared memory per block of threads.
-// Pair weights are exp(-beta (t_k - t_l)) = em_k * ep_l with em = exp(-beta delta),
-// ep = exp(+beta delta), delta = t - tau_b; a chunk whose span would overflow ep is
-// flagged "wide" and uses one exp per pair instead.
+// The marks are dealt round-robin into P mark blocks (block of mark c = c mod P, position
+// c / P; dealing spreads the few very frequent marks of a skewed mark distribution over all
+// blocks) and every chunk's events are bucketed by block, each bucket sorted by (position,
+// index), so that the targets of one row block (R consecutive positions of one block) are a
+// contiguous run of slots.  Pair weights are exp(-beta (t_k - t_l)) = em_k * ep_l with
+// em = exp(-beta delta), ep = exp(+beta delta), delta = t - tau_b; a chunk whose span would
+// overflow ep is flagged "wide" and uses one exp per pair instead.
 // ---------------------------------------------------------------------------
-constexpr int kTile = 128;
-constexpr int kTileLd = kTile + 1;      // padded row stride against bank conflicts
-constexpr float kWideLimit = 64.f;      // beta * span above which sums of exp(+beta delta) may overflow
-constexpr int kFwdChunksPerItem = 256;
-constexpr int kStage = 64;              // source records staged per warp at a time
-constexpr int kFlushChunks = 64;       // cost of writing out and summing one dalpha tile, in chunks
-// backward per-warp scratch: 32 item ranges, then up to kLStage staged sources (the
-// staging of wide chunks reuses the same bytes)
-constexpr int kLStage = 256;
-constexpr size_t kBwdWarpScratch = 32 * sizeof(int4) + kLStage * sizeof(float2);
-static_assert(kBwdWarpScratch >= kStage * sizeof(float4), "wide-chunk staging fits the scratch");
-
-__device__ __forceinline__ int rec_idx(float4 r) { return __float_as_int(r.w) >> 16; }
-__device__ __forceinline__ int rec_pos(float4 r) { return __float_as_int(r.w) & 0xffff; }
-// a source record as the pair loops read it: (delta, ep, column, index)
-__device__ __forceinline__ float4 unpack_rec(float4 r) {
-    return make_float4(r.x, r.z, __int_as_float(rec_pos(r)), __int_as_float(rec_idx(r)));
-}
-
-// alpha in tile-major order, arranged for conflict-free staging into shared memory:
-// float4 number e = rr * 128 + q of tile (I, J) holds column q of rows rr, rr + 32, rr + 64,
-// rr + 96, that is at[(((I * P + J) * 4096 + e) * 4 + s] = alpha[I + P (rr + 32 s)][J + P q]
-// (zero outside the matrix).
-__global__ void k_alpha_tiles(Problem p, float* at) {
-    const int M = p.M, P = p.P;
-    const int64_t total = (int64_t)P * P * kTile * kTile;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(e & 3);
-        const int f = (int)((e >> 2) % (kTile * kTile / 4));
-        const int tile = (int)(e / ((int64_t)kTile * kTile));
-        const int rr = f >> 7, q = f & 127;
-        const int I = tile / P, J = tile % P;
-        const int i = I + P * (rr + 32 * s), j = J + P * q;
-        at[e] = (i < M && j < M) ? p.alpha[(int64_t)i * M + j] : 0.f;
-    }
-}
-
 // One warp per chunk (up to eight chunks per block at a time, no block-wide barrier after
 // the mark table): bucket the chunk's events by mark block, each bucket sorted by (position
-// of the mark in its block, index in the chunk) in recs; the same buckets in index order in
-// lrec (source side of the backward pairs), and the membership bits of every bucket over
-// the chunk's event indices in bmask, each 32-bit word with the number of members in the
-// words before it.  The sorted order comes from counts: per (block, position) - one mark -
-// the number of the chunk's events, an exclusive scan of those counts in (block, position)
-// order (the first slot of every mark), and the events taking their slots in index order
-// (the lanes of one mark in one 32-event step ordered by lane).
-// the per-mark counts are stored with one padding word after every 32, so that the
-// lanes' contiguous runs of the scan fall in distinct banks
+// of the mark in its block, index in the chunk) in recs, with the first slot of every row
+// block of the backward pairs in bsub, and every event's (ep, mark) in index order in src
+// (the backward pairs' sources).  The sorted order comes from counts: per (block,
+// position) - one mark - the number of the chunk's events, an exclusive scan of those counts
+// in (block, position) order (the first slot of every mark), and the events taking their
+// slots in index order (the lanes of one mark in one 32-event step ordered by lane).
+// The per-mark counts are stored with one padding word after every 32, so that the
+// lanes' contiguous runs of the scan fall in distinct banks.
 __host__ __device__ inline int bucket_pad(int e) { return e + (e >> 5); }
 __host__ __device__ inline int bucket_ints_per_warp(int P, int C, int M) {
     const int TR = (M + P - 1) / P;
-    return 2 * P + 1 + bucket_pad(P * TR) + 1 + P * ((C + 31) >> 5);
+    return 2 * P + 1 + bucket_pad(P * TR) + 1;
 }
 // shared memory of k_bucket: each warp's scratch, then the mark -> (block, position) table
 __host__ __device__ inline size_t bucket_smem_bytes(int P, int C, int M, int warps) {
     return sizeof(int32_t) * ((size_t)warps * bucket_ints_per_warp(P, C, M) + (size_t)M);
 }
 
-__global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2* lrec,
-                                                uint2* bmask, int32_t* bstart, uint8_t* wide,
+__global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2* src,
+                                                int32_t* bstart, uint8_t* wide,
                                                 int64_t b_begin, int64_t b_end) {
     extern __shared__ int32_t sm_i[];
-    const int P = p.P, C = p.C, W = (C + 31) >> 5;
+    const int P = p.P, C = p.C;
     const int TR = (p.M + P - 1) / P, PT = P * TR;
+    const int n_rb = p.n_rb, nrb = p.nrb, lgR = p.lgR;
     const int lane = threadIdx.x & 31;
     int32_t* cnt = sm_i + (threadIdx.x >> 5) * bucket_ints_per_warp(P, C, p.M);   // [P]
     int32_t* base = cnt + P;              // [P+1]
     int32_t* slot = base + P + 1;         // [P * TR] per (block, position), padded: count, then next slot
     const int PTP = bucket_pad(PT) + 1;
-    uint32_t* msk = (uint32_t*)(slot + PTP);  // [P * W] membership bits
     // mark c -> (position c / P) << 16 | (block c mod P), so that no event divides by P
     int32_t* qtab = sm_i + (blockDim.x >> 5) * bucket_ints_per_warp(P, C, p.M);
     if (failed(p.hdr)) return;
@@ -220,7 +175,6 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
         chunk_range(p, b, 0, s0, s1);
         const int n = (int)(s1 - s0);
         for (int q = lane; q < P; q += 32) cnt[q] = 0;
-        for (int q = lane; q < P * W; q += 32) msk[q] = 0u;
         for (int e = lane; e < PTP; e += 32) slot[e] = 0;
         __syncwarp();
         for (int i = lane; i < n; i += 32) {
@@ -228,7 +182,6 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             const int q = qp & 0xffff;
             atomicAdd(&cnt[q], 1);
             atomicAdd(&slot[bucket_pad(q * TR + (qp >> 16))], 1);
-            atomicOr(&msk[q * W + (i >> 5)], 1u << (i & 31));
         }
         __syncwarp();
         if (lane == 0) {
@@ -262,16 +215,20 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             }
         }
         __syncwarp();
-        for (int e = lane; e < P * W; e += 32) {
-            int before = 0;
-            for (int w = e - e % W; w < e; ++w) before += __popc(msk[w]);
-            bmask[b * P * W + e] = make_uint2(msk[e], (uint32_t)before);
+        // first slot of every row block (block e / nrb, first position (e mod nrb) R)
+        int32_t* bs = p.bsub + b * (n_rb + 1);
+        for (int e = lane; e < n_rb; e += 32) {
+            const int q = e / nrb;
+            bs[e] = slot[bucket_pad(q * TR + ((e - q * nrb) << lgR))];
         }
+        if (lane == 0) bs[n_rb] = n;
+        __syncwarp();
         const bool isw = n > 0 && beta * (float)tdiff(p, p.t[s1 - 1], p.t[s0]) > kWideLimit;
         for (int i0 = 0; i0 < n; i0 += 32) {
             const int i = i0 + lane;
             const bool have = i < n;
-            const int qp = have ? qtab[__ldg(p.c + s0 + i)] : 0;
+            const int ci = have ? __ldg(p.c + s0 + i) : 0;
+            const int qp = have ? qtab[ci] : 0;
             const int q = qp & 0xffff, pos = qp >> 16;
             // the lanes of one mark take consecutive slots in lane (= index) order
             const int key = have ? q * TR + pos : -1 - lane;
@@ -282,14 +239,11 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
             first = __shfl_sync(HK_FULL, first, leader);
             if (have) {
                 const int at = first + __popc(peers & ((1u << lane) - 1u));   // from the chunk's start
-                const uint32_t* mq = msk + q * W;
-                int irank = __popc(mq[i >> 5] & ((1u << (i & 31)) - 1u));
-                for (int w = 0; w < (i >> 5); ++w) irank += __popc(mq[w]);
                 const float d = p.delta[s0 + i];
                 const float em = exp_unbiased(-beta * d);
                 const float ep = isw ? 0.f : exp_unbiased(beta * d);
                 recs[s0 + at] = make_float4(d, em, ep, __int_as_float((i << 16) | pos));
-                lrec[s0 + base[q] + irank] = make_float2(ep, __int_as_float(pos));
+                src[s0 + i] = make_float2(ep, __int_as_float(ci));
             }
         }
         if (lane == 0) wide[b] = isw ? 1 : 0;
@@ -297,365 +251,63 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
     }
 }
 
-// Forward pairs: for every event k,
-//   A_k = sum_{l<k in chunk} P_kl alpha[c_k][c_l],  B_k = sum (t_k - t_l) P_kl alpha[c_k][c_l].
-// With P_kl = em_k ep_l the lane of k sums a = sum ep_l alpha and d = sum delta_l ep_l alpha
-// and returns A_k = em_k a, B_k = em_k (delta_k a - d).  One thread owns A_k and B_k for all
-// column blocks J, so its updates for J > 0 (reductions without a returned value, issued
-// in J order) keep a fixed summation order.
-constexpr int kPairThreads = 512;
-constexpr int kPairWarps = kPairThreads / 32;
-
-// Stage tile (I, J) of alpha (laid out by k_alpha_tiles) into rows of kTileLd floats.
-__device__ __forceinline__ void load_alpha_tile(float* tile, const float* __restrict__ at, int tile_id) {
-    const float4* src = (const float4*)(at + (int64_t)tile_id * kTile * kTile);
-    for (int e = threadIdx.x; e < kTile * kTile / 4; e += blockDim.x) {
-        const float4 v = __ldg(src + e);
-        float* d = tile + (e >> 7) * kTileLd + (e & 127);
-        d[0] = v.x;
-        d[32 * kTileLd] = v.y;
-        d[64 * kTileLd] = v.z;
-        d[96 * kTileLd] = v.w;
-    }
-}
-
-__global__ void __launch_bounds__(kPairThreads, 2) k_pairs_fwd(Problem p, const float4* __restrict__ recs,
-                                                   const int32_t* __restrict__ bstart,
-                                                   const uint8_t* __restrict__ wide,
-                                                   const float* __restrict__ at, float* Aout,
-                                                   float* Bout, int* counter) {
-    extern __shared__ float tile[];       // [kTile][kTileLd], then per-warp staging
-    __shared__ int item_sh;
-    if (failed(p.hdr)) return;
-    const int P = p.P;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    float4* stage = (float4*)(tile + kTile * kTileLd) + warp * kStage;
-    const int nb = (int)num_chunks(p);
-    const int nranges = (nb + kFwdChunksPerItem - 1) / kFwdChunksPerItem;
-    const int nitems = nranges * P;
-    const float beta = p.beta[0];
-    const int C = p.C;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1);
-        __syncthreads();
-        const int item = item_sh;
-        if (item >= nitems) break;
-        const int I = item % P, range = item / P;
-        const int b0 = range * kFwdChunksPerItem;
-        const int b1 = min(b0 + kFwdChunksPerItem, nb);
-        for (int J = 0; J < P; ++J) {
-            __syncthreads();
-            load_alpha_tile(tile, at, I * P + J);
-            __syncthreads();
-            for (int b = b0 + warp; b < b1; b += nwarps) {
-                const int64_t s0 = (int64_t)b * C;
-                const int32_t* bs = bstart + (int64_t)b * (P + 1);
-                const int k0 = bs[I], k1 = bs[I + 1];
-                const int l0 = bs[J], nJ = bs[J + 1] - l0;
-                const bool isw = wide[b] != 0;
-                for (int kb = k0; kb < k1; kb += 32) {
-                    const int kk = kb + lane;
-                    const bool have = kk < k1;
-                    const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const int ik = have ? rec_idx(rk) : -1;
-                    const float* trow = tile + rec_pos(rk) * kTileLd;
-                    float a = 0.f, d = 0.f;
-                    for (int lb = 0; lb < nJ; lb += kStage) {
-                        const int ns = min(kStage, nJ - lb);
-                        __syncwarp();
-                        for (int q = lane; q < ns; q += 32)
-                            stage[q] = unpack_rec(__ldg(recs + s0 + l0 + lb + q));
-                        __syncwarp();
-                        if (!isw) {
-                            float a2 = 0.f, d2 = 0.f;
-                            int l = 0;
-#pragma unroll 2
-                            for (; l + 1 < ns; l += 2) {
-                                const float4 r0 = stage[l], r1 = stage[l + 1];
-                                const float v0 = r0.y * trow[__float_as_int(r0.z)];
-                                const float v1 = r1.y * trow[__float_as_int(r1.z)];
-                                if (__float_as_int(r0.w) < ik) { a += v0; d = fmaf(r0.x, v0, d); }
-                                if (__float_as_int(r1.w) < ik) { a2 += v1; d2 = fmaf(r1.x, v1, d2); }
-                            }
-                            if (l < ns) {
-                                const float4 r0 = stage[l];
-                                const float v0 = r0.y * trow[__float_as_int(r0.z)];
-                                if (__float_as_int(r0.w) < ik) { a += v0; d = fmaf(r0.x, v0, d); }
-                            }
-                            a += a2;
-                            d += d2;
-                        } else {
-                            for (int l = 0; l < ns; ++l) {
-                                const float4 rl = stage[l];
-                                if (__float_as_int(rl.w) < ik) {
-                                    const float v = expf(-beta * (rk.x - rl.x)) * trow[__float_as_int(rl.z)];
-                                    a += v;
-                                    d = fmaf(rl.x, v, d);
-                                }
-                            }
-                        }
-                    }
-                    if (have) {
-                        const float em = isw ? 1.f : rk.y;
-                        const float A = em * a, B = em * fmaf(rk.x, a, -d);
-                        const int64_t k = s0 + ik;
-                        if (J == 0) { Aout[k] = A; Bout[k] = B; }
-                        else { atomicAdd(Aout + k, A); atomicAdd(Bout + k, B); }
-                    }
-                }
-            }
-        }
-    }
-}
-
-// Row groups of the backward pairs, once per (chunk, bucket) instead of once per tile:
-// for every 32-lane group of a bucket (sorted by (row, index)), u_k = w_k em_k, U_k = sum
-// of u over the lane's row group from k on, and the index of the previous event of the
-// same row in the group (-1 if none): kprep[slot] = (row * kTileLd, U_k, index, previous).
-// Chunks too wide for the factorised weights are skipped (their pairs take one exp each).
+// Row groups of the backward pairs, once per (chunk, bucket): for every 32-lane group of a
+// bucket (sorted by (position, index)), u_k = w_k em_k, U_k = sum of u over the lane's row
+// group (the events of its mark in the group) from k on, and the index of the previous
+// event of the same mark in the group (-1 if none): kprep[slot] = (position, U_k, index,
+// previous).  The target k then owes U_k ep_l to (c_k, c_l) for the sources l with index in
+// [previous, k) (from 0 without a previous one): every (mark, source) pair of the group gets
+// one add.  Also the backward pairs' work of every (row block, chunk) in pwork: per target its
+// 32-source steps plus one.  Chunks too wide for the factorised weights get only the work
+// (their pairs take one exp each, over all earlier sources).
 __global__ void __launch_bounds__(256) k_bwd_prep(Problem p, const float4* __restrict__ recs,
                                                   const int32_t* __restrict__ bstart,
                                                   const uint8_t* __restrict__ wide,
                                                   const float* __restrict__ wbuf, int4* kprep) {
+    __shared__ int32_t wsh[8][128];      // per warp: work of the bucket's row blocks
     if (failed(p.hdr)) return;
     const int P = p.P, C = p.C, lane = threadIdx.x & 31;
+    const int nrb = p.nrb, lgR = p.lgR;
+    int32_t* work = wsh[threadIdx.x >> 5];
     const int64_t nb = num_chunks(p);
     const int64_t nseg = nb * P;
     const int64_t wpb = blockDim.x >> 5;
     for (int64_t sgi = blockIdx.x * wpb + (threadIdx.x >> 5); sgi < nseg; sgi += (int64_t)gridDim.x * wpb) {
         const int64_t b = sgi / P;
         const int I = (int)(sgi % P);
-        if (wide[b]) continue;
+        const bool isw = wide[b] != 0;
         const int64_t s0 = b * C;
         const int k0 = bstart[b * (P + 1) + I], k1 = bstart[b * (P + 1) + I + 1];
+        for (int e = lane; e < nrb; e += 32) work[e] = 0;
+        __syncwarp();
         for (int kb = k0; kb < k1; kb += 32) {
             const int kk = kb + lane;
             const bool have = kk < k1;
             const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
             const int ik = have ? rec_idx(rk) : -1;
             const int row = have ? rec_pos(rk) : -1 - lane;   // distinct for idle lanes
-            const float wk = have ? wbuf[s0 + ik] : 0.f;
-            float U = wk * rk.y;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float up = __shfl_down_sync(HK_FULL, U, o);
-                const int rowo = __shfl_down_sync(HK_FULL, row, o);
-                if (lane + o < 32 && rowo == row) U += up;
-            }
-            const int prow = __shfl_up_sync(HK_FULL, row, 1);
-            const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
-            const int lo = (lane > 0 && prow == row) ? pidx : -1;
-            if (have) kprep[s0 + kk] = make_int4(row * kTileLd, __float_as_int(U), ik, lo);
-        }
-    }
-}
-
-// Backward pairs: dalpha_intra[c_k][c_l] += w_k P_kl over the pairs of tile (I, J).
-// Bucket I is sorted by (row, index), so lanes holding events of the same row are
-// adjacent.  With u_k = w_k em_k and U_k = sum of u over the lane's row group from k on
-// (inside the 32-lane group), the lane of k owes U_k ep_l to (row_k, column_l) for the
-// sources l of bucket J with index in [index of the previous event of its row, index of
-// k): every (row, l) gets one add per lane group.  In index order those sources are the
-// contiguous ranks [a_k, b_k) of bucket J (counted from its membership bits), so the
-// (k, l) items of a lane group are numbered 0 .. T-1 and every lane takes a contiguous
-// run of about T / 32 of them: each shared-memory add carries one item, whatever the
-// spread of the intervals.  Chunks too wide for the factorised weights take one exp per
-// pair over all (k, l) instead.
-//
-// FIXED: the tile holds unsigned fixed-point numbers (value x 2^s, rounded to nearest) and
-// every add is a native 32-bit shared-memory atomic (an FP32 shared-memory atomic is a load
-// and a compare-and-swap on this part, a third of the rate).  Every item is at most 32 w_max
-// (w_max = the largest 1 / lambda_k: U_k ep_l <= sum of w over the row group), and s puts 64
-// such items below 2^32 (s from k_pair_scale, at most 2^-12 absolute resolution at the bench
-// workload, far below the 1e-4 max-norm tolerance of dalpha); an add that would wrap is
-// detected from the atomic's returned value and marks the block, whose (tile, chunk range)
-// the FP32 variant (FIXED = false, flagged blocks only) then recomputes.
-__device__ __forceinline__ void tile_add(float* t, int at, float v, float, bool&) {
-    atomicAdd(t + at, v);
-}
-__device__ __forceinline__ void tile_add(uint32_t* t, int at, float v, float scale, bool& wrap) {
-    const uint32_t x = __float2uint_rn(v * scale);
-    const uint32_t old = atomicAdd(t + at, x);
-    wrap |= old > 0xffffffffu - x;
-}
-
-template <bool FIXED>
-__global__ void __launch_bounds__(kPairThreads, 2) k_pairs_bwd(Problem p, const float4* __restrict__ recs,
-                                                   const float2* __restrict__ lrec,
-                                                   const uint2* __restrict__ bmask,
-                                                   const int4* __restrict__ kprep,
-                                                   const int32_t* __restrict__ bstart,
-                                                   const uint8_t* __restrict__ wide,
-                                                   const float* __restrict__ wbuf,
-                                                   int chunks_per_cta, int* redo) {
-    using TileT = typename std::conditional<FIXED, uint32_t, float>::type;
-    extern __shared__ float sm_bwd[];
-    TileT* dtile = (TileT*)sm_bwd;          // [kTile][kTileLd], then per-warp scratch
-    __shared__ int wrap_sh;
-    if (failed(p.hdr)) return;
-    const int block_id = blockIdx.y * gridDim.x + blockIdx.x;
-    if (FIXED ? redo[block_id] != 0 : !redo[block_id]) return;   // the other variant's block
-    // 2^s of the fixed-point tile, from the exponent k_pair_scale left in the header
-    const int sexp = FIXED ? (int)p.hdr->pad[10] : 0;
-    const float scale = FIXED ? ldexpf(1.f, sexp) : 1.f;
-    bool wrap = false;
-    const int P = p.P;
-    const int I = blockIdx.x / P, J = blockIdx.x % P;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    char* scratch = (char*)(sm_bwd + kTile * kTileLd) + warp * kBwdWarpScratch;
-    int4* kd = (int4*)scratch;                          // [32] per-lane item ranges
-    float2* lst = (float2*)(kd + 32);                   // [kLStage] sources of bucket J
-    float4* stage = (float4*)scratch;                   // wide chunks: [kStage] records
-    const int nb = (int)num_chunks(p);
-    const int b0 = blockIdx.y * chunks_per_cta;
-    const int b1 = min(b0 + chunks_per_cta, nb);    // may be empty: the tile is still written
-    const float beta = p.beta[0];
-    const int C = p.C, W = (C + 31) >> 5;
-    for (int e = threadIdx.x; e < kTile * kTileLd; e += blockDim.x) dtile[e] = (TileT)0;
-    if (threadIdx.x == 0) wrap_sh = 0;
-    __syncthreads();
-    for (int b = b0 + warp; b < b1; b += nwarps) {
-        const int64_t s0 = (int64_t)b * C;
-        const int32_t* bs = bstart + (int64_t)b * (P + 1);
-        const int k0 = bs[I], k1 = bs[I + 1];
-        const int l0 = bs[J], nJ = bs[J + 1] - l0;
-        if (k0 == k1 || nJ == 0) continue;
-        const bool isw = wide[b] != 0;
-        // membership bits of bucket J (word w on lane w) and the members before each word
-        const uint2 mwc = lane < W ? __ldg(bmask + ((int64_t)b * P + J) * W + lane) : make_uint2(0u, 0u);
-        const uint32_t mw = mwc.x;
-        const int cw = (int)mwc.y;
-        const bool staged = !isw && nJ <= kLStage;
-        if (staged) {
-            __syncwarp();
-            for (int q = lane; q < nJ; q += 32) lst[q] = __ldg(lrec + s0 + l0 + q);
-            __syncwarp();
-        }
-        for (int kb = k0; kb < k1; kb += 32) {
-            const int kk = kb + lane;
-            const bool have = kk < k1;
+            int n = ik;                                        // sources of a wide chunk's target
             if (!isw) {
-                const int4 kp = have ? __ldg(kprep + s0 + kk) : make_int4(0, 0, -1, -1);
-                const int ik = kp.z, lo = kp.w;
-                const float U = __int_as_float(kp.y);
-                // ranks in bucket J (index order) of the sources before ik and before lo
-                const int xh = have ? ik : 0, xl = lo > 0 ? lo : 0;
-                const int bk = __shfl_sync(HK_FULL, cw, xh >> 5) +
-                               __popc(__shfl_sync(HK_FULL, mw, xh >> 5) & ((1u << (xh & 31)) - 1u));
-                const int ak = __shfl_sync(HK_FULL, cw, xl >> 5) +
-                               __popc(__shfl_sync(HK_FULL, mw, xl >> 5) & ((1u << (xl & 31)) - 1u));
-                const int n = have ? bk - (lo >= 0 ? ak : 0) : 0;
-                int incl = n;
+                const float wk = have ? wbuf[s0 + ik] : 0.f;
+                float U = wk * rk.y;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const int x = __shfl_up_sync(HK_FULL, incl, o);
-                    if (lane >= o) incl += x;
+                    const float up = __shfl_down_sync(HK_FULL, U, o);
+                    const int rowo = __shfl_down_sync(HK_FULL, row, o);
+                    if (lane + o < 32 && rowo == row) U += up;
                 }
-                const int excl = incl - n;
-                const int T = __shfl_sync(HK_FULL, incl, 31);
-                if (T == 0) continue;
-                // owners: the lanes with items, compacted in lane order (each has >= 1 item,
-                // so consecutive items advance by at most one owner)
-                const uint32_t amask = __ballot_sync(HK_FULL, n > 0);
-                __syncwarp();
-                if (n > 0)
-                    kd[__popc(amask & ((1u << lane) - 1u))] =
-                        make_int4(kp.x, __float_as_int(U), (lo >= 0 ? ak : 0) - excl, incl);
-                __syncwarp();
-                // items [g0, g1) of this lane, L per lane; the owner of g0 is the first lane
-                // whose last item is >= g0
-                const int L = (T + 31) >> 5;
-                const int g0 = lane * L;
-                const int g1 = min(g0 + L, T);
-                int pos = 0;
-#pragma unroll
-                for (int st = 16; st >= 1; st >>= 1) {
-                    const int in = __shfl_sync(HK_FULL, incl, pos + st - 1);
-                    if (in <= g0) pos += st;
-                }
-                int j = pos < 32 ? __popc(amask & ((1u << pos) - 1u)) : 0;
-                if (staged) {
-                    int4 ko = kd[j];
-                    for (int i = 0; i < L; ++i) {
-                        const int gi = g0 + i;
-                        if (gi >= ko.w) ko = kd[min(++j, 31)];     // next owner (at most one step)
-                        if (gi < g1) {
-                            const float2 l = lst[gi + ko.z];
-                            tile_add(dtile, ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x,
-                                     scale, wrap);
-                        }
-                    }
-                } else {
-                    int4 ko = kd[j];
-                    for (int i = 0; i < L; ++i) {
-                        const int gi = g0 + i;
-                        if (gi >= ko.w) ko = kd[min(++j, 31)];
-                        if (gi < g1) {
-                            const float2 l = __ldg(lrec + s0 + l0 + gi + ko.z);
-                            tile_add(dtile, ko.x + __float_as_int(l.y), __int_as_float(ko.y) * l.x,
-                                     scale, wrap);
-                        }
-                    }
-                }
-                __syncwarp();
-            } else {
-                const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const int ik = have ? rec_idx(rk) : -1;
-                const float wk = have ? wbuf[s0 + ik] : 0.f;
-                const int drow = (have ? rec_pos(rk) : 0) * kTileLd;
-                for (int lb = 0; lb < nJ; lb += kStage) {
-                    const int ns = min(kStage, nJ - lb);
-                    __syncwarp();
-                    for (int q = lane; q < ns; q += 32)
-                        stage[q] = unpack_rec(__ldg(recs + s0 + l0 + lb + q));
-                    __syncwarp();
-                    for (int l = 0; l < ns; ++l) {
-                        const float4 rl = stage[l];
-                        if (__float_as_int(rl.w) < ik)
-                            tile_add(dtile, drow + __float_as_int(rl.z),
-                                     wk * expf(-beta * (rk.x - rl.x)), scale, wrap);
-                    }
-                }
+                const int prow = __shfl_up_sync(HK_FULL, row, 1);
+                const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
+                const int lo = (lane > 0 && prow == row) ? pidx : -1;
+                if (have) kprep[s0 + kk] = make_int4(row, __float_as_int(U), ik, lo);
+                n = ik - (lo > 0 ? lo : 0);
             }
+            if (have) atomicAdd(&work[row >> lgR], ((n + 31) >> 5) + 1);
         }
+        __syncwarp();
+        for (int e = lane; e < nrb; e += 32) p.pwork[(int64_t)(I * nrb + e) * p.nb_max + b] = work[e];
+        __syncwarp();
     }
-    if (FIXED && wrap) atomicOr(&wrap_sh, 1);
-    __syncthreads();
-    if (FIXED && wrap_sh) {                 // recomputed by the FP32 variant
-        if (threadIdx.x == 0) redo[block_id] = 1;
-        return;
-    }
-    // this block's tile (TR = ceil(M / P) rows and columns are used), summed over the chunk
-    // ranges in a fixed order by the finalisation
-    const int TR = (p.M + P - 1) / P;
-    float* out = p.dal_part + ((int64_t)blockIdx.y * P * P + blockIdx.x) * TR * TR;
-    const float inv = FIXED ? ldexpf(1.f, -sexp) : 1.f;
-    for (int e = threadIdx.x; e < TR * TR; e += blockDim.x)
-        out[e] = (float)dtile[(e / TR) * kTileLd + (e % TR)] * inv;
-}
-
-// The exponent s of the fixed-point pair tiles: w_max = the largest w_k (one pass over w),
-// then s with 32 w_max 2^s <= 2^26; written to the header.  A tile whose adds would wrap is
-// still exact (the FP32 variant redoes it); s below kFixedMinExp (w_max above ~2^9) sends
-// every block to the FP32 variant, so that the fixed-point resolution 2^-s stays fine.
-constexpr int kFixedMinExp = 8;
-__global__ void k_pair_wmax(Problem p, const float* __restrict__ w, unsigned* wmax_bits) {
-    float m = 0.f;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.N;
-         k += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, w[k]);
-    for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(HK_FULL, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(wmax_bits, __float_as_uint(m));
-}
-__global__ void k_pair_scale(Problem p, const unsigned* wmax_bits, int* redo, int nblocks) {
-    const float wmax = __uint_as_float(*wmax_bits);
-    int e = 0;
-    if (wmax > 0.f && isfinite(wmax)) frexpf(32.f * wmax, &e);     // 32 wmax < 2^e
-    const int s = 26 - e;
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.hdr->pad[10] = s;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblocks; b += gridDim.x * blockDim.x)
-        redo[b] = s < kFixedMinExp ? 1 : 0;
 }
 
 // Per-event epilogue: lambda, log, w, the W entries of the dalpha GEMM, the dbeta sum and
@@ -820,8 +472,8 @@ cudaError_t launch_bucket_range(const Problem& p, cudaStream_t s, int64_t b_begi
     }
     int64_t grid = (b_end - b_begin + warps - 1) / warps;
     if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
-    k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 32 * warps, smem, s>>>(p, p.recs, p.lrec, p.bmask,
-                                                                    p.bstart, p.wide, b_begin, b_end);
+    k_bucket<<<(unsigned)(grid > 0 ? grid : 1), 32 * warps, smem, s>>>(p, p.recs, p.src, p.bstart,
+                                                                    p.wide, b_begin, b_end);
     ++*nl;
     prof_mark(s, "bucket");
     return cudaGetLastError();
@@ -884,35 +536,13 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
         ++*nl;
         prof_mark(s, "gemm_Z");
     }
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int P = p.P;
-    {
-        // alpha in tile-major order, and the events of every chunk bucketed by mark block
-        int64_t total = (int64_t)P * P * kTile * kTile;
-        int64_t blocks = (total + 255) / 256;
-        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-        k_alpha_tiles<<<(unsigned)blocks, 256, 0, s>>>(p, p.at);
-        ++*nl;
-        if (!p.bucket_done) {
-            err = launch_bucket_range(p, s, 0, nb, nl);
-            if (err != cudaSuccess) return err;
-        }
-    }
-    {
-        // forward pairs: work items (row block, kFwdChunksPerItem chunks) from a counter in the header
-        const size_t smem = sizeof(float) * kTile * kTileLd + sizeof(float4) * kStage * kPairWarps;
-        err = cudaFuncSetAttribute(k_pairs_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the events of every chunk bucketed by mark block (unless done piece by piece), then
+    // the forward pairs
+    if (!p.bucket_done) {
+        err = launch_bucket_range(p, s, 0, nb, nl);
         if (err != cudaSuccess) return err;
-        k_pairs_fwd<<<(unsigned)(sms * 2), kPairThreads, smem, s>>>(p, p.recs, p.bstart, p.wide, p.at,
-                                                           p.Aint, p.Bint,
-                                                           (int*)&p.hdr->pad[8]);
-        ++*nl;
-        prof_mark(s, "pairs_fwd");
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    return cudaSuccess;
+    return launch_pairs_forward(p, s, nl);
 }
 
 // The per-event epilogue of one kernel.
@@ -944,7 +574,6 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
     cudaError_t err;
     const int64_t M = p.M, nb = p.nb_max;
     const int64_t* nb_dev = p.chunk_base + p.B;   // number of chunks, on the device
-    int64_t dal_parts = 0;   // chunk ranges of the backward pair kernel
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -959,52 +588,8 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (p.grad) {
-        // backward pairs: tile (I, J) x chunk range
-        const size_t smem = sizeof(float) * kTile * kTileLd + kBwdWarpScratch * kPairWarps;
-        for (const void* k : {(const void*)k_pairs_bwd<true>, (const void*)k_pairs_bwd<false>}) {
-            err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (err != cudaSuccess) return err;
-        }
-        // Blocks of equal work: pick the number R of chunk ranges per tile that minimises
-        // (waves of resident blocks) x (chunks per block + the cost of one tile flush,
-        // counted as kFlushChunks chunks).
-        int per_sm = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_bwd<true>, kPairThreads, smem);
+        err = launch_pairs_backward(p, s, nl);
         if (err != cudaSuccess) return err;
-        const int64_t slots = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-        const int64_t tiles = (int64_t)P * P;
-        int64_t R = 1, best = -1;
-        for (int64_t r = 1; r <= 8 * slots / tiles + 1 && r <= (nb > 0 ? nb : 1) && r <= p.dal_parts_max;
-             ++r) {
-            const int64_t waves = (tiles * r + slots - 1) / slots;
-            const int64_t cost = waves * ((nb + r - 1) / r + kFlushChunks);
-            if (best < 0 || cost < best) { best = cost; R = r; }
-        }
-        int64_t per = (nb + R - 1) / R;
-        if (per < 1) per = 1;
-        R = (nb + per - 1) / per;
-        if (R < 1) R = 1;
-        dal_parts = R;
-        // the fixed-point scale from the largest w, then the fixed-point pass, then the FP32
-        // pass over the blocks it could not hold
-        const int nblocks = (int)(tiles * R);
-        unsigned* wmax_bits = (unsigned*)&p.hdr->pad[11];
-        cudaMemsetAsync(wmax_bits, 0, sizeof(unsigned), s);
-        {
-            int64_t wb = (p.N + 255) / 256;
-            if (wb > (int64_t)sms * 4) wb = (int64_t)sms * 4;
-            k_pair_wmax<<<(unsigned)(wb > 0 ? wb : 1), 256, 0, s>>>(p, p.wbuf, wmax_bits);
-            k_pair_scale<<<(unsigned)((nblocks + 255) / 256), 256, 0, s>>>(p, wmax_bits, p.pair_redo,
-                                                                           nblocks);
-        }
-        const dim3 bgrid((unsigned)(P * P), (unsigned)R);
-        k_pairs_bwd<true><<<bgrid, kPairThreads, smem, s>>>(
-            p, p.recs, p.lrec, p.bmask, p.kprep, p.bstart, p.wide, p.wbuf, (int)per, p.pair_redo);
-        k_pairs_bwd<false><<<bgrid, kPairThreads, smem, s>>>(
-            p, p.recs, p.lrec, p.bmask, p.kprep, p.bstart, p.wide, p.wbuf, (int)per, p.pair_redo);
-        *nl += 4;
-        prof_mark(s, "pairs_bwd");
-        if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (p.grad) {
         // dalpha_gemm[i][j] = sum_b W[b][i] S^[b][j] with the chunk index as the contiguous
@@ -1039,9 +624,7 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
         ++*nl;
         prof_mark(s, "gemm_dalpha");
     }
-    Problem q = p;
-    q.dal_parts = (int32_t)dal_parts;
-    return launch_finalize_mode(q, s, 1, nl);
+    return launch_finalize_mode(p, s, 1, nl);
 }
 
 // ---------------------------------------------------------------------------

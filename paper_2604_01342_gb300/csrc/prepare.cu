@@ -20,6 +20,7 @@ __global__ void k_init(Problem p, double* acc, int64_t n_acc) {
         p.hdr->nb = 0;
         p.hdr->pad[8] = 0;   // work counter of the forward pair kernel / the mark-major walk
         p.hdr->pad[9] = 0;   // longest support row (mark-major walk)
+        p.hdr->pad[12] = 0;  // ticket of the backward pair plan
         if (p.single) {
             p.hdr->pad[0] = 0;
             p.hdr->pad[1] = p.N;
