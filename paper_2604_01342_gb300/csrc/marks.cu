@@ -322,8 +322,16 @@ __global__ void k_seg_carry(Problem p) {
 // that rows of at most 64 entries run with half the registers and twice the warps per SM.
 // Each lane keeps the next two records of its source list in flight, and the warp the next
 // target record, because a walk step waits on little else than those loads.
+// A lane's state is its component at the previous target's time t' (the segment start
+// before the first target): at target k, S = exp(-beta_j (t_k - t')) S + sum of
+// exp(-beta_j (t_k - t_l)) over its source events l with index in [index of the previous
+// target, k), and G likewise with the weights (t_k - t_l) (G takes (t_k - t') S first).  The
+// one factor per target that multiplies the state goes through exp_unbiased (it is chained
+// along the targets); each source event's own term is used once and takes the hardware
+// exponential (__expf: a few ulp, nothing chained), which keeps a source step to a handful
+// of instructions.
 template <bool GRAD, int R>
-__global__ void __launch_bounds__(256, R == 2 ? 3 : 2) k_walk_marks(Problem p,
+__global__ void __launch_bounds__(256, R == 2 ? 4 : 2) k_walk_marks(Problem p,
                                                                     unsigned long long* counter) {
     if (failed(p.hdr)) return;
     const unsigned long long rowmax = *(volatile unsigned long long*)&p.hdr->pad[kRowMaxWord];
@@ -343,7 +351,7 @@ __global__ void __launch_bounds__(256, R == 2 ? 3 : 2) k_walk_marks(Problem p,
         if (ta == tb) continue;
         const int r0 = p.row_ptr[i], r1 = p.row_ptr[i + 1];
         const int ng = (r1 - r0 + 31) >> 5;
-        float Sv[R], Gv[R], lh[R], ll[R], av[R], bv[R], dal[R], dbe[R];
+        float Sv[R], Gv[R], av[R], bv[R], dal[R], dbe[R];
         int q[R], qe[R], jv[R];
         float4 nx[R], nx2[R];
 #pragma unroll
@@ -360,8 +368,6 @@ __global__ void __launch_bounds__(256, R == 2 ? 3 : 2) k_walk_marks(Problem p,
             qe[g] = valid ? soff[at + 1] : 0;
             nx[g] = q[g] < qe[g] ? rec[q[g]] : sentinel;
             nx2[g] = q[g] + 1 < qe[g] ? rec[q[g] + 1] : sentinel;
-            lh[g] = 0.f;
-            ll[g] = 0.f;
             dal[g] = 0.f;
             dbe[g] = 0.f;
         }
@@ -370,35 +376,33 @@ __global__ void __launch_bounds__(256, R == 2 ? 3 : 2) k_walk_marks(Problem p,
         float dmu = 0.f;
         bool bad = false;
         float4 tnext = rec[ta];
+        float ph = 0.f, pl = 0.f;          // the previous target's time (segment start first)
         for (int k = ta; k < tb; ++k) {
             const float4 tk = tnext;
             if (k + 1 < tb) tnext = rec[k + 1];
             const int ik = __float_as_int(tk.z);
+            const float dtp = (tk.x - ph) + (tk.y - pl);
+            ph = tk.x;
+            pl = tk.y;
             float part = 0.f;
-            float sv[R], gv[R];
 #pragma unroll
             for (int g = 0; g < R; ++g) {
-                sv[g] = 0.f;
-                gv[g] = 0.f;
                 if (g < ng) {
-                    // the source's events before the target event: decay and jump
+                    // the state carried from the previous target ...
+                    const float d = exp_unbiased(-bv[g] * dtp);
+                    if (GRAD) Gv[g] = d * fmaf(dtp, Sv[g], Gv[g]);
+                    Sv[g] *= d;
+                    // ... plus the source's events since then
                     while (__float_as_int(nx[g].z) < ik) {
-                        const float dt = (nx[g].x - lh[g]) + (nx[g].y - ll[g]);
-                        const float d = exp_unbiased(-bv[g] * dt);
-                        if (GRAD) Gv[g] = d * fmaf(dt, Sv[g], Gv[g]);
-                        Sv[g] = fmaf(d, Sv[g], 1.f);
-                        lh[g] = nx[g].x;
-                        ll[g] = nx[g].y;
+                        const float x = (tk.x - nx[g].x) + (tk.y - nx[g].y);
+                        const float e = __expf(-bv[g] * x);
+                        Sv[g] += e;
+                        if (GRAD) Gv[g] = fmaf(x, e, Gv[g]);
                         ++q[g];
                         nx[g] = nx2[g];
                         nx2[g] = q[g] + 1 < qe[g] ? rec[q[g] + 1] : sentinel;
                     }
-                    // the component at the target event's time
-                    const float dt = (tk.x - lh[g]) + (tk.y - ll[g]);
-                    const float d = exp_unbiased(-bv[g] * dt);
-                    sv[g] = d * Sv[g];
-                    if (GRAD) gv[g] = d * fmaf(dt, Sv[g], Gv[g]);
-                    part = fmaf(av[g] * bv[g], sv[g], part);
+                    part = fmaf(av[g] * bv[g], Sv[g], part);
                 }
             }
 #pragma unroll
@@ -411,8 +415,8 @@ __global__ void __launch_bounds__(256, R == 2 ? 3 : 2) k_walk_marks(Problem p,
                 if (lane == 0) dmu += w;
 #pragma unroll
                 for (int g = 0; g < R; ++g) {
-                    dal[g] = fmaf(w, sv[g], dal[g]);
-                    dbe[g] = fmaf(w * av[g], fmaf(-bv[g], gv[g], sv[g]), dbe[g]);
+                    dal[g] = fmaf(w, Sv[g], dal[g]);
+                    dbe[g] = fmaf(w * av[g], fmaf(-bv[g], Gv[g], Sv[g]), dbe[g]);
                 }
             }
         }
