@@ -327,9 +327,8 @@ __global__ void k_seg_carry(Problem p) {
 // exp(-beta_j (t_k - t_l)) over its source events l with index in [index of the previous
 // target, k), and G likewise with the weights (t_k - t_l) (G takes (t_k - t') S first).  The
 // one factor per target that multiplies the state goes through exp_unbiased (it is chained
-// along the targets); each source event's own term is used once and takes the hardware
-// exponential (__expf: a few ulp, nothing chained), which keeps a source step to a handful
-// of instructions.
+// along the targets); each source event's own term is used once and takes expf (nothing
+// chained), which keeps a source step to a handful of instructions.
 template <bool GRAD, int R>
 __global__ void __launch_bounds__(256, R == 2 ? 4 : 2) k_walk_marks(Problem p,
                                                                     unsigned long long* counter) {
@@ -395,7 +394,7 @@ __global__ void __launch_bounds__(256, R == 2 ? 4 : 2) k_walk_marks(Problem p,
                     // ... plus the source's events since then
                     while (__float_as_int(nx[g].z) < ik) {
                         const float x = (tk.x - nx[g].x) + (tk.y - nx[g].y);
-                        const float e = __expf(-bv[g] * x);
+                        const float e = expf(-bv[g] * x);
                         Sv[g] += e;
                         if (GRAD) Gv[g] = fmaf(x, e, Gv[g]);
                         ++q[g];
