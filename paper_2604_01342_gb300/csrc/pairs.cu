@@ -59,9 +59,10 @@ __device__ __forceinline__ int64_t block_scan_i64(int64_t v, int64_t* sh, int64_
 }
 
 // One block per row block: the prefix of its work over the chunks (pcum) and its total;
-// the last block to finish then lays out the plan: nr_rb = ceil(total_rb nb_target / W)
-// blocks for a row block with work (at most one per chunk), their first block, and for every
-// block x its (row block, share) as rb << 16 | k.
+// the last block to finish then lays out the plan: nr_rb = ceil(total_rb B / W) blocks for a
+// row block with work (at least one, at most one per chunk; B chosen so that they add up to
+// at most nb_target), their first block, and for every block x its (row block, share) as
+// rb << 16 | k.
 __global__ void __launch_bounds__(kPairRowThreads) k_pair_plan(Problem p, int32_t* plan,
                                                                int nb_target, unsigned* ticket) {
     __shared__ int64_t sh[33];
@@ -72,19 +73,30 @@ __global__ void __launch_bounds__(kPairRowThreads) k_pair_plan(Problem p, int32_
     const int64_t nbc = num_chunks(p);
     const int64_t ldc = p.nb_max + 1;
     {
-        const int rb = blockIdx.x;
+        // each warp scans a contiguous segment of the chunks, 32 at a time (coalesced reads):
+        // its segment's sum, the warps' prefix over the block, then the segment's prefixes
+        const int rb = blockIdx.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
         const int32_t* w = p.pwork + (int64_t)rb * p.nb_max;
         int64_t* cum = p.pcum + (int64_t)rb * ldc;
-        const int64_t per = (nbc + nt - 1) / nt;
-        const int64_t b0 = min((int64_t)tid * per, nbc), b1 = min(b0 + per, nbc);
+        const int64_t per = ((nbc + nw - 1) / nw + 31) / 32 * 32;
+        const int64_t b0 = min((int64_t)wid * per, nbc), b1 = min(b0 + per, nbc);
         int64_t run = 0;
-        for (int64_t b = b0; b < b1; ++b) run += w[b];
+        for (int64_t b = b0 + lane; b < b1; b += 32) run += w[b];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) run += __shfl_xor_sync(HK_FULL, run, o);
         int64_t total;
-        const int64_t incl = block_scan_i64(run, sh, &total);
-        int64_t at = incl - run;
-        for (int64_t b = b0; b < b1; ++b) {
-            cum[b] = at;
-            at += w[b];
+        const int64_t incl = block_scan_i64(lane == 0 ? run : 0, sh, &total);
+        int64_t at = __shfl_sync(HK_FULL, incl, 0) - run;     // before this warp's segment
+        for (int64_t b = b0; b < b1; b += 32) {
+            const int64_t x = b + lane < b1 ? w[b + lane] : 0;
+            int64_t y = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t z = __shfl_up_sync(HK_FULL, y, o);
+                if (lane >= o) y += z;
+            }
+            if (b + lane < b1) cum[b + lane] = at + y - x;
+            at += __shfl_sync(HK_FULL, y, 31);
         }
         if (tid == 0) {
             cum[nbc] = total;
@@ -101,16 +113,30 @@ __global__ void __launch_bounds__(kPairRowThreads) k_pair_plan(Problem p, int32_
     for (int r = tid; r < n_rb; r += nt) part += __ldcg(p.ptot + r);
     int64_t W;
     block_scan_i64(part, sh, &W);
+    // blocks of a row block with work: ceil(t B / W) for the largest B <= nb_target whose
+    // blocks add up to at most nb_target (each ceil adds less than one, so B lies within
+    // n_rb below nb_target), so that the blocks fill whole waves
+    auto blocks_of = [&](int64_t t, int64_t B) -> int64_t {
+        if (t <= 0 || W <= 0) return 0;
+        int64_t nr = (t * B + W - 1) / W;
+        if (nr > nbc) nr = nbc;
+        return nr < 1 ? 1 : nr;
+    };
+    int64_t lo = nb_target - n_rb > 1 ? nb_target - n_rb : 1, hi = nb_target;
+    while (lo < hi) {                       // the largest B in [lo, hi] that fits (lo always does)
+        const int64_t mid = (lo + hi + 1) / 2;
+        int64_t cnt = 0;
+        for (int r = tid; r < n_rb; r += nt) cnt += blocks_of(__ldcg(p.ptot + r), mid);
+        int64_t sum;
+        block_scan_i64(cnt, sh, &sum);
+        if (sum <= nb_target) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t Bsel = lo;
     int64_t carry = 0;
     for (int r0 = 0; r0 < n_rb; r0 += nt) {
         const int r = r0 + tid;
-        const int64_t t = r < n_rb ? __ldcg(p.ptot + r) : 0;
-        int64_t nr = 0;
-        if (t > 0 && W > 0) {
-            nr = (t * nb_target + W - 1) / W;
-            if (nr > nbc) nr = nbc;
-            if (nr < 1) nr = 1;
-        }
+        const int64_t nr = r < n_rb ? blocks_of(__ldcg(p.ptot + r), Bsel) : 0;
         int64_t sum;
         const int64_t incl = block_scan_i64(nr, sh, &sum);
         const int64_t base = carry + incl - nr;
@@ -471,7 +497,7 @@ static int pair_target_blocks() {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nb = 4 * sms;        // four waves of one 1024-thread block per SM
+    const int nb = 2 * sms;        // two waves of one 1024-thread block per SM
     return nb < kPairBlocksMax ? nb : kPairBlocksMax;
 }
 
