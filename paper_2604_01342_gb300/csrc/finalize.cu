@@ -93,31 +93,43 @@ __global__ void k_finalize_alpha(Problem p, int mode) {
         }
         return;
     }
+    // one block row per dalpha row i (blockIdx.y), its columns over blockIdx.x and the threads
     const float beta = p.beta[0];
-    const int P = p.P, n_rb = p.n_rb, R = 1 << p.lgR;
-    const int64_t total = (int64_t)M * M;
-    for (int64_t ij = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ij < total;
-         ij += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(ij / M), j = (int)(ij % M);
-        float pairs = 0.f;
-        if (!bad) {
-            // row i = I + P pos is row pos mod R of row block I nrb + pos / R
-            const int I = i % P, pos = i / P;
-            const int rb = I * p.nrb + (pos >> p.lgR);
-            const int nr = p.plan_b[1 + rb], base = p.plan_b[1 + n_rb + rb];
-            const float* part = p.dal_part + ((((int64_t)base << p.lgR) + (pos & (R - 1))) * M + j);
-            const int64_t step = (int64_t)R * M;
-            // compensated FP32 sum of the shares (FP64 arithmetic runs at 1/64 of the FP32
-            // rate here)
-            float comp = 0.f;
-            for (int k = 0; k < nr; ++k) {
-                const float y = part[k * step] - comp;
+    const int i = blockIdx.y;
+    const int P = p.P, R = 1 << p.lgR;
+    // row i = I + P pos is row pos mod R of row block I nrb + pos / R
+    const int I = i % P, pos = i / P;
+    const int rb = I * p.nrb + (pos >> p.lgR);
+    const int nr = bad ? 0 : p.plan_b[1 + rb];
+    const int base = bad ? 0 : p.plan_b[1 + p.n_rb + rb];
+    const double wsum = p.wsum_acc[i];
+    const int64_t step = (int64_t)R * M;
+    const float* part0 = p.dal_part + (((int64_t)base << p.lgR) + (pos & (R - 1))) * M;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+        const int64_t ij = (int64_t)i * M + j;
+        // compensated FP32 sum of the shares, in share order (FP64 arithmetic runs at 1/64 of
+        // the FP32 rate here); four shares loaded at a time
+        float pairs = 0.f, comp = 0.f;
+        const float* part = part0 + j;
+        int k = 0;
+        for (; k + 4 <= nr; k += 4) {
+            const float y4[4] = {part[k * step], part[(k + 1) * step], part[(k + 2) * step],
+                                 part[(k + 3) * step]};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float y = y4[u] - comp;
                 const float t = pairs + y;
                 comp = (t - pairs) - y;
                 pairs = t;
             }
         }
-        const double x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * p.wsum_acc[i] +
+        for (; k < nr; ++k) {
+            const float y = part[k * step] - comp;
+            const float t = pairs + y;
+            comp = (t - pairs) - y;
+            pairs = t;
+        }
+        const double x = (double)beta * ((double)p.dal_gemm[ij] + (double)p.cen_S[j] * wsum +
                                          (double)pairs);
         double v = x - p.E_acc[j];
         if (p.support && p.alpha[ij] == 0.f) v = 0.0;       // outside alpha's support
@@ -133,7 +145,10 @@ cudaError_t launch_finalize_mode(const Problem& p, cudaStream_t s, int mode, int
         int64_t total = (int64_t)p.B * p.M * p.M;
         int64_t blocks = (total + 255) / 256;
         if (blocks > 152 * 16) blocks = 152 * 16;
-        k_finalize_alpha<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, mode);
+        if (mode == 0)
+            k_finalize_alpha<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, mode);
+        else
+            k_finalize_alpha<<<dim3((unsigned)((p.M + 255) / 256), (unsigned)p.M), 256, 0, s>>>(p, mode);
         ++*nl;
     }
     prof_mark(s, "finalize");
