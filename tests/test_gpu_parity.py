@@ -29,7 +29,10 @@ def test_walk_forward_only_larger_m(m):
 
 
 # ------------------------------------------------------------ chunk-GEMM path
-@pytest.mark.parametrize("m,chunk", [(5, 16), (16, 64), (100, 32), (130, 64), (256, 128)])
+# (300, 64), (1500, 192): several backward row blocks per mark block, the last one partial;
+# (4096, 192): row blocks of 8 marks
+@pytest.mark.parametrize("m,chunk", [(5, 16), (16, 64), (100, 32), (130, 64), (256, 128),
+                                     (300, 64), (1500, 192), (4096, 192)])
 def test_gemm_path_matches_oracle(m, chunk):
     p = synth.random_problem(m, 4000, 500 + m, True, rho=0.6)
     assert_close(gpu_run(p, path=2, chunk=chunk), oracle_ref(p), what=f"gemm m={m} C={chunk}")
