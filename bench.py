@@ -506,7 +506,7 @@ def run_ours(args):
 # one ncu capture on the first 2e6 events of the benchmark stream.  A launch processes every
 # event of the step and the kernels' traffic grows in proportion to the events, so a launch
 # moves N times this.
-DRAM_BYTES_PER_EVENT = {"pairs_bwd": (51463168 + 37098752) / 2e6,
+DRAM_BYTES_PER_EVENT = {"pairs_bwd": (50371584 + 5120256) / 2e6,
                         "pairs_fwd": (36649984 + 142592) / 2e6}
 
 
