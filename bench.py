@@ -172,13 +172,17 @@ def precision_report(p, dev, ref, n_sample=CPU_SAMPLE_EVENTS):
     return out
 
 
-def workload5_line(dev, steps=3):
+def workload5_line(dev, steps=3, events=0):
     """The fifth workload (M=4096, one decay per source, alpha 1% dense, N=5e7, T ~ 1e7) on
     the mark-major path, gradient on alpha's support: events/s over `steps` calls after one
-    warm-up call (inputs resident, L2 flushed between calls)."""
+    warm-up call (inputs resident, L2 flushed between calls).  `events` > 0 takes only the
+    first that many events of the stream (T = the last one's time; profiling runs)."""
     import torch
     from paper_2604_01342_gb300 import binding as B, synth
     p = synth.workload(5)
+    if 0 < events < p.N:
+        p = synth.Problem(t=p.t[:events].copy(), c=p.c[:events].copy(), T=float(p.t[events - 1]),
+                          mu=p.mu, alpha=p.alpha, beta=p.beta, shared_beta=False, name=p.name)
     N, M = p.N, p.M
     opts = B.make_opts(False, 0, True, 0, support=True)
     t = torch.from_numpy(p.t).to(dev)
@@ -220,7 +224,8 @@ def workload5_line(dev, steps=3):
     m = sum(ms) / len(ms)
     return {"workload": "M=4096, beta_j ~ U[0.2,5] per source, alpha 1% dense at spectral "
                         "radius 0.85, N=50,000,000 on [0, T~1e7], seed 4; gradient on "
-                        "alpha's support; mark-major path",
+                        "alpha's support; mark-major path" +
+                        (f"; first {N:,} events only" if N < 50_000_000 else ""),
             "value": N / (m * 1e-3), "unit": "events/s", "ms_per_step": m, "steps": steps,
             "loglik": float(ll.item()), "kernels_ms": kern}
 
@@ -483,7 +488,8 @@ def run_ours(args):
         cpu, ref = time_oracle(p, want_result=True)
         precision = precision_report(p, dev, ref)
     fp64 = time_fp64_scan(p, dev) if (world == 1 and not args.no_fp64_scan) else None
-    w5 = workload5_line(dev) if (world == 1 and not args.no_workload5) else None
+    w5 = (workload5_line(dev, events=args.workload5_events)
+          if (world == 1 and not args.no_workload5) else None)
     line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -620,7 +626,18 @@ def main():
                     help="skip the fifth workload (per-source decays, M=4096, N=5e7)")
     ap.add_argument("--events", type=int, default=0,
                     help="use only the first N events of the workload (profiling runs)")
+    ap.add_argument("--only-workload5", action="store_true",
+                    help="run only the fifth workload's leg and print its line (profiling runs)")
+    ap.add_argument("--workload5-events", type=int, default=0,
+                    help="use only the first N events of the fifth workload (profiling runs)")
     args = ap.parse_args()
+    if args.only_workload5:
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"workload5": workload5_line(dev, steps=args.steps,
+                                                      events=args.workload5_events)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
