@@ -311,10 +311,9 @@ __global__ void __launch_bounds__(256) k_bwd_prep(Problem p, const float4* __res
 }
 
 // Per-event epilogue: lambda, log, w, the W entries of the dalpha GEMM, the dbeta sum and
-// per-mark sums in shared-memory histograms flushed once per block.  Events are taken in a
-// grid-stride loop (one sequence: event k lies in chunk k / C, which starts at event
-// C (k / C)); W (transposed, zeroed before) is accumulated by global reductions, one per
-// event, and its row sums are taken where W is split for the GEMM.  The compensator sums
+// per-mark sums in shared-memory histograms flushed once per block.  One sequence: event k
+// lies in chunk k / C, which starts at event C (k / C).  W is transposed ([M][nbp]) and its
+// row sums are taken where it is split for the GEMM.  The compensator sums
 // E_j = sum_{c_l = j} (1 - exp(-beta (T - t_l))) = n_j - sum exp(-beta (T - t_l)) and
 // F_j = sum (T - t_l) exp(-beta (T - t_l)) only need the events with beta (T - t) < 104
 // (below that exp underflows to 0 in FP32); n_j comes from the validation's mark counts
@@ -325,64 +324,59 @@ __device__ __forceinline__ int64_t chunk_of(int64_t k, int C, int64_t N) {
     return N < (int64_t(1) << 31) ? (int64_t)((uint32_t)k / (uint32_t)C) : k / C;
 }
 
+// Per-thread sums of the epilogue.
+struct EpiSums {
+    LogProd lp;      // reduce mode 0: running product of the intensities
+    SumF32 ls;       // modes 1, 2: FP32 log-sum
+    double db = 0.0; // dbeta terms: FP32 terms summed in FP64, so that the near-cancelling sum
+                     // does not depend on which thread took which event
+};
+
+// Event k (chunk b, mark ck, delta = t_k - chunk start) given y = Y[b][ck], z = Z[b][ck]
+// (with the gradient) and its pair sums ak, bk: the log-intensity term, the compensator tail and, with the gradient, w, the
+// dbeta term and the per-mark sum of w; returns w e_k, the event's W entry (0 without the
+// gradient).
 template <bool GRAD>
-__global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __restrict__ Aint,
-                                                     const float* __restrict__ Bint, float* wbuf) {
-    extern __shared__ float sh[];
-    const int M = p.M, C = p.C;
-    float* hEt = sh;                          // [M] sum of exp(-beta (T - t)) (tail events)
-    float* hF = hEt + M;                      // [M]
-    float* hmu = hF + M;                      // [M]
-    uint32_t* hcnt = (uint32_t*)(hmu + M);    // [M] events per mark (without validation)
-    __shared__ double red_ll[16];
-    __shared__ double red_db[16];
-    __shared__ SumF32 red_ls[16];
-    if (failed(p.hdr)) return;
-    const int64_t N = p.N, ldw = p.nbp;
-    const int mode = p.reduce;                // 0: FP64 log of running products; 1, 2: FP32 logs
-    const float beta = p.beta[0];
-    const double T = p.Tarr[0];
-    const bool counted = p.validated != 0;
-    for (int j = threadIdx.x; j < 4 * M; j += blockDim.x) sh[j] = 0.f;
-    __syncthreads();
-    LogProd lp;
-    SumF32 ls;
-    float db = 0.f;
-#pragma unroll 4
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = chunk_of(k, C, N);
-        const int ck = __ldg(p.c + k);
-        const float delta = __ldg(p.delta + k);
-        const float ek = exp_unbiased(-beta * delta);
-        const float y = __ldg(p.Y + b * M + ck);
-        const float ak = __ldg(Aint + k);
-        const float aS = ek * y + ak;
-        const float lam = __ldg(p.mu + ck) + beta * aS;
-        if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
-        if (mode == 0) lp.mul(lam);
-        else if (mode == 1) ls.add(logf(lam));
-        else ls.s += logf(lam);
-        if (!counted) atomicAdd(&hcnt[ck], 1u);
-        if (beta * (__ldg(p.Tmt + b) - delta) < kTailLimit + 1.f) {   // T - t_k, to within rounding
-            const float xT = (float)tdiff(p, T, p.t[k]);
-            if (beta * xT < kTailLimit) {
-                const float eT = exp_unbiased(-beta * xT);
-                atomicAdd(&hEt[ck], eT);
-                if (GRAD) atomicAdd(&hF[ck], xT * eT);
-            }
-        }
-        if (GRAD) {
-            const float w = 1.f / lam;
-            const float x = __ldg(p.Z + b * M + ck);
-            db += w * (ek * (x - beta * delta * y) + (ak - beta * __ldg(Bint + k)));
-            wbuf[k] = w;
-            atomicAdd(&p.W[(int64_t)ck * ldw + b], w * ek);
-            atomicAdd(&hmu[ck], w);
+__device__ __forceinline__ float epi_event(const Problem& p, int64_t k, int64_t b, int ck,
+                                           float delta, float y, float z, float ak, float bk,
+                                           float beta, double T,
+                                           int mode, bool counted, EpiSums& acc, float* hEt,
+                                           float* hF, float* hmu, uint32_t* hcnt, float* wbuf) {
+    const float ek = exp_unbiased(-beta * delta);
+    const float aS = ek * y + ak;
+    const float lam = __ldg(p.mu + ck) + beta * aS;
+    if (!(lam > 0.f)) set_status(p.hdr, HAWKES_ERR_NONPOS_INTENSITY);
+    if (mode == 0) acc.lp.mul(lam);
+    else if (mode == 1) acc.ls.add(logf(lam));
+    else acc.ls.s += logf(lam);
+    if (!counted) atomicAdd(&hcnt[ck], 1u);
+    if (beta * (__ldg(p.Tmt + b) - delta) < kTailLimit + 1.f) {   // T - t_k, to within rounding
+        const float xT = (float)tdiff(p, T, p.t[k]);
+        if (beta * xT < kTailLimit) {
+            const float eT = exp_unbiased(-beta * xT);
+            atomicAdd(&hEt[ck], eT);
+            if (GRAD) atomicAdd(&hF[ck], xT * eT);
         }
     }
-    double ll = mode == 0 ? lp.log_value() : 0.0;
-    double dbd = (double)db;
+    if (!GRAD) return 0.f;
+    const float w = 1.f / lam;
+    acc.db += (double)(w * (ek * (z - beta * delta * y) + (ak - beta * bk)));
+    wbuf[k] = w;
+    atomicAdd(&hmu[ck], w);
+    return w * ek;
+}
+
+// The block's sums into the accumulators: the log-likelihood (atomic FP64, or the block's
+// FP32 partial for k_logsum_combine), dbeta, and the per-mark histograms.
+template <bool GRAD>
+__device__ __forceinline__ void epi_flush(const Problem& p, EpiSums& acc, int mode, bool counted,
+                                          const float* hEt, const float* hF, const float* hmu,
+                                          const uint32_t* hcnt, double* red_ll, double* red_db,
+                                          SumF32* red_ls) {
+    const int M = p.M;
+    double ll = mode == 0 ? acc.lp.log_value() : 0.0;
+    double dbd = acc.db;
+    SumF32& ls = acc.ls;
     for (int o = 16; o >= 1; o >>= 1) {
         ll += __shfl_xor_sync(HK_FULL, ll, o);
         dbd += __shfl_xor_sync(HK_FULL, dbd, o);
@@ -425,6 +419,114 @@ __global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __r
             if (hmu[j] != 0.f) atomicAdd(&p.dmu_acc[j], (double)hmu[j]);
         }
     }
+}
+
+// Event by event (for marks too many for the group kernel's shared memory): Y and Z gathered
+// from global memory, W (transposed, zeroed before) accumulated by global reductions.
+template <bool GRAD>
+__global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __restrict__ Aint,
+                                                     const float* __restrict__ Bint, float* wbuf) {
+    extern __shared__ float sh[];
+    const int M = p.M, C = p.C;
+    float* hEt = sh;                          // [M] sum of exp(-beta (T - t)) (tail events)
+    float* hF = hEt + M;                      // [M]
+    float* hmu = hF + M;                      // [M]
+    uint32_t* hcnt = (uint32_t*)(hmu + M);    // [M] events per mark (without validation)
+    __shared__ double red_ll[16];
+    __shared__ double red_db[16];
+    __shared__ SumF32 red_ls[16];
+    if (failed(p.hdr)) return;
+    const int64_t N = p.N, ldw = p.nbp;
+    const int mode = p.reduce;                // 0: FP64 log of running products; 1, 2: FP32 logs
+    const float beta = p.beta[0];
+    const double T = p.Tarr[0];
+    const bool counted = p.validated != 0;
+    for (int j = threadIdx.x; j < 4 * M; j += blockDim.x) sh[j] = 0.f;
+    __syncthreads();
+    EpiSums acc;
+#pragma unroll 4
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = chunk_of(k, C, N);
+        const int ck = __ldg(p.c + k);
+        const float y = __ldg(p.Y + b * M + ck);
+        const float z = GRAD ? __ldg(p.Z + b * M + ck) : 0.f;
+        const float bk = GRAD ? __ldg(Bint + k) : 0.f;
+        const float wv = epi_event<GRAD>(p, k, b, ck, __ldg(p.delta + k), y, z, __ldg(Aint + k), bk,
+                                         beta, T, mode, counted, acc, hEt, hF, hmu, hcnt, wbuf);
+        if (GRAD) atomicAdd(&p.W[(int64_t)ck * ldw + b], wv);
+    }
+    epi_flush<GRAD>(p, acc, mode, counted, hEt, hF, hmu, hcnt, red_ll, red_db, red_ls);
+}
+
+// By groups of kEpiGroup consecutive chunks: a block takes a group at a time, accumulates
+// its W entries in shared memory and writes them out as one 32-byte piece per mark (W is
+// transposed, [M][nbp] with nbp a multiple of kEpiGroup, so the groups cover every column and
+// W needs no zeroing).
+constexpr int kEpiGroup = 8;
+
+template <bool GRAD>
+__global__ void __launch_bounds__(512, 3) k_epilogue_groups(Problem p, const float* __restrict__ Aint,
+                                                         const float* __restrict__ Bint,
+                                                         float* wbuf) {
+    extern __shared__ float sh[];
+    const int M = p.M, C = p.C;
+    float* hEt = sh;                          // [M] sum of exp(-beta (T - t)) (tail events)
+    float* hF = hEt + M;                      // [M]
+    float* hmu = hF + M;                      // [M]
+    uint32_t* hcnt = (uint32_t*)(hmu + M);    // [M] events per mark (without validation)
+    float* Wg = (float*)(hcnt + M);           // [kEpiGroup][M] the group's W entries (GRAD)
+    __shared__ double red_ll[16];
+    __shared__ double red_db[16];
+    __shared__ SumF32 red_ls[16];
+    if (failed(p.hdr)) return;
+    const int64_t N = p.N, nb = p.nb_max, ldw = p.nbp;
+    const int64_t ngroups = (nb + kEpiGroup - 1) / kEpiGroup;
+    const int mode = p.reduce;
+    const float beta = p.beta[0];
+    const double T = p.Tarr[0];
+    const bool counted = p.validated != 0;
+    const int nt = blockDim.x;
+    for (int j = threadIdx.x; j < 4 * M; j += nt) sh[j] = 0.f;
+    __syncthreads();
+    EpiSums acc;
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int64_t b0 = g * kEpiGroup;
+        const int nbg = (int)(nb - b0 < kEpiGroup ? nb - b0 : kEpiGroup);
+        if (GRAD) {
+            __syncthreads();                  // the previous group's entries are written out
+            for (int j = threadIdx.x; j < kEpiGroup * M; j += nt) Wg[j] = 0.f;
+            __syncthreads();
+        }
+        const int64_t k0 = b0 * C;
+        const int64_t k1 = (b0 + nbg) * C < N ? (b0 + nbg) * C : N;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += nt) {
+            const int64_t b = chunk_of(k, C, N);
+            const int ck = __ldg(p.c + k);
+            const float y = __ldg(p.Y + b * M + ck);
+            const float z = GRAD ? __ldg(p.Z + b * M + ck) : 0.f;
+            const float bk = GRAD ? __ldg(Bint + k) : 0.f;
+            const float wv = epi_event<GRAD>(p, k, b, ck, __ldg(p.delta + k), y, z, __ldg(Aint + k),
+                                             bk, beta, T, mode, counted, acc, hEt, hF, hmu, hcnt,
+                                             wbuf);
+            if (GRAD) atomicAdd(&Wg[(int)(b - b0) * M + ck], wv);
+        }
+        if (GRAD) {
+            __syncthreads();
+            for (int m = threadIdx.x; m < M; m += nt) {
+                float4* dst = (float4*)(p.W + (int64_t)m * ldw + b0);
+                dst[0] = make_float4(Wg[m], Wg[M + m], Wg[2 * M + m], Wg[3 * M + m]);
+                dst[1] = make_float4(Wg[4 * M + m], Wg[5 * M + m], Wg[6 * M + m], Wg[7 * M + m]);
+            }
+        }
+    }
+    __syncthreads();
+    epi_flush<GRAD>(p, acc, mode, counted, hEt, hF, hmu, hcnt, red_ll, red_db, red_ls);
+}
+
+// Shared memory of the group epilogue.
+static size_t epi_group_smem(int64_t M, bool grad) {
+    return sizeof(float) * (size_t)M * (4 + (grad ? kEpiGroup : 0));
 }
 
 // The FP32 log-sums of the epilogue's blocks, in block order (mode 1 compensated, mode 2
@@ -549,16 +651,38 @@ cudaError_t launch_gemm_forward(const Problem& p, cudaStream_t s, int* nl) {
 cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nl) {
     cudaError_t err;
     const int64_t M = p.M;
-    if (p.grad) cudaMemsetAsync(p.W, 0, sizeof(float) * (size_t)M * (size_t)p.nbp, s);
-    const size_t smem = sizeof(float) * 4 * (size_t)M;
-    auto kern = p.grad ? k_epilogue<true> : k_epilogue<false>;
-    if (smem > 48 * 1024) {
-        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem_max = 227 * 1024 - 512;
+    const bool groups = epi_group_smem(M, p.grad) <= smem_max;
+    int blocks;
+    if (groups) {
+        const size_t smem = epi_group_smem(M, p.grad);
+        auto kern = p.grad ? k_epilogue_groups<true> : k_epilogue_groups<false>;
+        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem)) != cudaSuccess)
+            return err;
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem);
+        const int64_t ngroups = (p.nb_max + kEpiGroup - 1) / kEpiGroup;
+        int64_t b = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+        if (b > ngroups) b = ngroups;
+        if (p.reduce != 0 && b > kLogSumBlocks) b = kLogSumBlocks;
+        blocks = (int)(b > 0 ? b : 1);
+        kern<<<(unsigned)blocks, 512, smem, s>>>(p, p.Aint, p.Bint, p.wbuf);
+    } else {
+        if (p.grad) cudaMemsetAsync(p.W, 0, sizeof(float) * (size_t)M * (size_t)p.nbp, s);
+        const size_t smem = sizeof(float) * 4 * (size_t)M;
+        auto kern = p.grad ? k_epilogue<true> : k_epilogue<false>;
+        if (smem > 48 * 1024) {
+            err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+        }
+        blocks = epilogue_blocks(p.N);
+        if (p.reduce != 0 && blocks > kLogSumBlocks) blocks = kLogSumBlocks;
+        kern<<<(unsigned)blocks, 512, smem, s>>>(p, p.Aint, p.Bint, p.wbuf);
     }
-    int blocks = epilogue_blocks(p.N);
-    if (p.reduce != 0 && blocks > kLogSumBlocks) blocks = kLogSumBlocks;
-    kern<<<(unsigned)blocks, 512, smem, s>>>(p, p.Aint, p.Bint, p.wbuf);
     ++*nl;
     if (p.reduce != 0) {
         k_logsum_combine<<<1, 32, 0, s>>>(p, blocks);
@@ -661,7 +785,7 @@ __global__ void __launch_bounds__(512) k_epilogue_multi(Problem p, MultiSlices m
     for (int j = threadIdx.x; j < (2 * K + 2) * M; j += blockDim.x) sh[j] = 0.f;
     __syncthreads();
     LogProd lp;
-    float db[kMaxKernels] = {0.f, 0.f, 0.f, 0.f};
+    double db[kMaxKernels] = {0.0, 0.0, 0.0, 0.0};   // FP32 terms summed in FP64
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = chunk_of(k, C, N);
@@ -700,8 +824,8 @@ __global__ void __launch_bounds__(512) k_epilogue_multi(Problem p, MultiSlices m
             for (int q = 0; q < kMaxKernels; ++q) {
                 if (q < K) {
                     const float x = ms.k[q].Z[b * M + ck];
-                    db[q] += w * (e[q] * (x - beta[q] * delta * y[q]) +
-                                  (ms.k[q].A[k] - beta[q] * ms.k[q].B[k]));
+                    db[q] += (double)(w * (e[q] * (x - beta[q] * delta * y[q]) +
+                                           (ms.k[q].A[k] - beta[q] * ms.k[q].B[k])));
                     atomicAdd(&ms.k[q].W[(int64_t)ck * ldw + b], w * e[q]);
                 }
             }
@@ -710,7 +834,7 @@ __global__ void __launch_bounds__(512) k_epilogue_multi(Problem p, MultiSlices m
     double ll = lp.log_value();
     double dbd[kMaxKernels];
 #pragma unroll
-    for (int q = 0; q < kMaxKernels; ++q) dbd[q] = (double)db[q];
+    for (int q = 0; q < kMaxKernels; ++q) dbd[q] = db[q];
     for (int o = 16; o >= 1; o >>= 1) {
         ll += __shfl_xor_sync(HK_FULL, ll, o);
 #pragma unroll
