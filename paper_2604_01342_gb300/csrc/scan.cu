@@ -374,6 +374,102 @@ __global__ void __launch_bounds__(256) k_scan_states_fast(Problem p) {
     }
 }
 
+// Pass A on the chunk-GEMM path (one sequence, one shared decay): the composite of a group
+// of chunks [b0, b1) taken straight from its events, each scaled to the group's end t_E (the
+// first event of chunk b1).  An event l of chunk b adds
+//     e_l = F_b exp(-beta x_l) to S[c_l] and (X_b + x_l) e_l to G[c_l],
+// with x_l = t_{s_{b+1}} - t_l (the chunk's span D_b minus the event's offset delta_l while
+// beta D_b <= 16, else in FP64), X_b = t_E - t_{s_{b+1}} and F_b = exp(-beta X_b): the sums
+// that the chunk-by-chunk walk forms through its chain of decays, without a pass over the
+// whole state and a barrier per chunk.  One thread per chunk first lays out the chunk table
+// (the offsets t_{s_b}, spans, X_b, F_b; D_b and T - t_{s_b} stored for the later kernels).
+// A group that holds the sequence's last chunk maps to the zero state (the walk resets there)
+// and only stores the offsets.
+constexpr int kMaxGroupChunks = 64;
+
+template <bool GRAD>
+__global__ void __launch_bounds__(128) k_scan_reduce_fast(Problem p, int64_t g_begin) {
+    extern __shared__ float sm[];
+    float* S = sm;
+    float* G = sm + p.M;
+    const bool split = p.M <= kScanSplitM;
+    const int nwarps = blockDim.x >> 5;
+    float* Sw = sm + 2 * p.M + (threadIdx.x >> 5) * p.M;     // this warp's copies (split only)
+    float* Gw = sm + 2 * p.M + (nwarps + (threadIdx.x >> 5)) * p.M;
+    __shared__ double t0_sh[kMaxGroupChunks], tn_sh[kMaxGroupChunks];
+    __shared__ float D_sh[kMaxGroupChunks], X_sh[kMaxGroupChunks], F_sh[kMaxGroupChunks];
+    __shared__ int narrow_sh[kMaxGroupChunks];
+    if (failed(p.hdr)) return;
+    const int64_t nb = num_chunks(p);
+    const int64_t g = g_begin + blockIdx.x;
+    const int64_t b0 = g * p.Gc;
+    if (b0 >= nb) return;
+    const int64_t b1 = b0 + p.Gc < nb ? b0 + p.Gc : nb;
+    const int M = p.M, C = p.C, tid = threadIdx.x, nbg = (int)(b1 - b0);
+    const int64_t N = p.N;
+    const float beta = p.beta[0];
+    const bool final = b1 == nb;              // holds the last chunk
+    const double tE = final ? 0.0 : p.t[b1 * C];
+    for (int j = tid; j < M; j += blockDim.x) {
+        S[j] = 0.f;
+        if (GRAD) G[j] = 0.f;
+    }
+    if (split)
+        for (int j = tid; j < 2 * nwarps * M; j += blockDim.x) sm[2 * M + j] = 0.f;
+    for (int i = tid; i < nbg; i += blockDim.x) {
+        const int64_t b = b0 + i, s0 = b * C, s1 = s0 + C < N ? s0 + C : N;
+        const double t0 = p.t[s0];
+        t0_sh[i] = t0;
+        p.Tmt[b] = (float)tdiff(p, p.Tarr[0], t0);
+        if (s1 < N) {
+            const double tn = p.t[s1];
+            const float D = (float)tdiff(p, tn, t0);
+            p.Dspan[b] = D;
+            tn_sh[i] = tn;
+            D_sh[i] = D;
+            narrow_sh[i] = beta * D <= 16.f;
+            if (!final) {
+                const float X = (float)tdiff(p, tE, tn);
+                X_sh[i] = X;
+                F_sh[i] = exp_unbiased(-beta * X);
+            }
+        }
+    }
+    if (tid == 0) {
+        p.grp_dt[g] = final ? 0.0 : tdiff(p, tE, p.t[b0 * C]);
+        p.grp_reset[g] = final ? 1 : 0;
+    }
+    __syncthreads();
+    const int64_t k0 = b0 * C, k1 = b1 * C < N ? b1 * C : N;
+    for (int64_t l = k0 + tid; l < k1; l += blockDim.x) {
+        const int i = (int)((uint64_t)(l - k0) / (uint64_t)C);
+        const double tl = p.t[l];
+        const float dl = (float)tdiff(p, tl, t0_sh[i]);
+        p.delta[l] = dl;
+        if (final) continue;
+        const float x = narrow_sh[i] ? D_sh[i] - dl : (float)tdiff(p, tn_sh[i], tl);
+        const float e = F_sh[i] * exp_unbiased(-beta * x);
+        const int cl = p.c[l];
+        atomicAdd(split ? &Sw[cl] : &S[cl], e);
+        if (GRAD) atomicAdd(split ? &Gw[cl] : &G[cl], (X_sh[i] + x) * e);
+    }
+    __syncthreads();
+    if (split)      // fold the warps' copies
+        for (int j = tid; j < M; j += blockDim.x) {
+            float sv = S[j], gv = GRAD ? G[j] : 0.f;
+            for (int w = 0; w < nwarps; ++w) {
+                sv += sm[2 * M + w * M + j];
+                if (GRAD) gv += sm[2 * M + (nwarps + w) * M + j];
+            }
+            S[j] = sv;
+            if (GRAD) G[j] = gv;
+        }
+    for (int j = tid; j < M; j += blockDim.x) {
+        p.grp_v[g * M + j] = S[j];
+        if (GRAD) p.grp_g[g * M + j] = G[j];
+    }
+}
+
 // the chunk-GEMM path's pass C: one sequence, one shared decay, offsets written by pass A
 static bool fast_states(const Problem& p) { return p.delta != nullptr && p.shared && p.B == 1; }
 
@@ -386,7 +482,8 @@ static cudaError_t scan_attributes(const Problem& p) {
     if (smem > 48 * 1024) {       // large M on the chunk-GEMM path: opt in to more shared memory
         const void* kerns[] = {(const void*)k_scan_group<0, true>, (const void*)k_scan_group<1, true>,
                                (const void*)k_scan_group<0, false>, (const void*)k_scan_group<1, false>,
-                               (const void*)k_scan_states_fast<true>, (const void*)k_scan_states_fast<false>};
+                               (const void*)k_scan_states_fast<true>, (const void*)k_scan_states_fast<false>,
+                               (const void*)k_scan_reduce_fast<true>, (const void*)k_scan_reduce_fast<false>};
         for (const void* k : kerns) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
@@ -402,8 +499,14 @@ cudaError_t launch_scan_reduce(const Problem& p, cudaStream_t s, int64_t g_begin
     if (err != cudaSuccess) return err;
     if (g_end > p.ng_max) g_end = p.ng_max;
     const unsigned grid = (unsigned)(g_end > g_begin ? g_end - g_begin : 1);
-    if (p.grad) k_scan_group<0, true><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
-    else k_scan_group<0, false><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
+    if (fast_states(p) && p.Gc <= kMaxGroupChunks) {
+        if (p.grad) k_scan_reduce_fast<true><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
+        else k_scan_reduce_fast<false><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
+    } else if (p.grad) {
+        k_scan_group<0, true><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
+    } else {
+        k_scan_group<0, false><<<grid, 128, scan_smem_bytes(p), s>>>(p, g_begin);
+    }
     ++*nl;
     prof_mark(s, "scan_reduce");
     return cudaGetLastError();
