@@ -260,53 +260,85 @@ __global__ void __launch_bounds__(256) k_bucket(Problem p, float4* recs, float2*
 // one add.  Also the backward pairs' work of every (row block, chunk) in pwork: per target its
 // 32-source steps plus one.  Chunks too wide for the factorised weights get only the work
 // (their pairs take one exp each, over all earlier sources).
-__global__ void __launch_bounds__(256) k_bwd_prep(Problem p, const float4* __restrict__ recs,
+__global__ void __launch_bounds__(256, 4) k_bwd_prep(Problem p, const float4* __restrict__ recs,
                                                   const int32_t* __restrict__ bstart,
                                                   const uint8_t* __restrict__ wide,
                                                   const float* __restrict__ wbuf, int4* kprep) {
+    // A warp takes a chunk and its buckets kPrepBatch at a time: the bounds, first 32
+    // records and weights of the batch's buckets are loaded together (three dependent loads
+    // per batch instead of per bucket), then each bucket is processed in turn.
+    constexpr int kPrepBatch = 8;
     __shared__ int32_t wsh[8][128];      // per warp: work of the bucket's row blocks
     if (failed(p.hdr)) return;
     const int P = p.P, C = p.C, lane = threadIdx.x & 31;
     const int nrb = p.nrb, lgR = p.lgR;
     int32_t* work = wsh[threadIdx.x >> 5];
     const int64_t nb = num_chunks(p);
-    const int64_t nseg = nb * P;
     const int64_t wpb = blockDim.x >> 5;
-    for (int64_t sgi = blockIdx.x * wpb + (threadIdx.x >> 5); sgi < nseg; sgi += (int64_t)gridDim.x * wpb) {
-        const int64_t b = sgi / P;
-        const int I = (int)(sgi % P);
+    // one 32-event step of bucket I: the row groups' U and previous indices, and the work
+    auto step = [&](int64_t s0, bool isw, int kk, int k1, float4 rk, float wk) {
+        const bool have = kk < k1;
+        const int ik = have ? rec_idx(rk) : -1;
+        const int row = have ? rec_pos(rk) : -1 - lane;   // distinct for idle lanes
+        int n = ik;                                        // sources of a wide chunk's target
+        if (!isw) {
+            float U = wk * rk.y;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float up = __shfl_down_sync(HK_FULL, U, o);
+                const int rowo = __shfl_down_sync(HK_FULL, row, o);
+                if (lane + o < 32 && rowo == row) U += up;
+            }
+            const int prow = __shfl_up_sync(HK_FULL, row, 1);
+            const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
+            const int lo = (lane > 0 && prow == row) ? pidx : -1;
+            if (have) kprep[s0 + kk] = make_int4(row, __float_as_int(U), ik, lo);
+            n = ik - (lo > 0 ? lo : 0);
+        }
+        if (have) atomicAdd(&work[row >> lgR], ((n + 31) >> 5) + 1);
+    };
+    for (int64_t b = blockIdx.x * wpb + (threadIdx.x >> 5); b < nb; b += (int64_t)gridDim.x * wpb) {
         const bool isw = wide[b] != 0;
         const int64_t s0 = b * C;
-        const int k0 = bstart[b * (P + 1) + I], k1 = bstart[b * (P + 1) + I + 1];
-        for (int e = lane; e < nrb; e += 32) work[e] = 0;
-        __syncwarp();
-        for (int kb = k0; kb < k1; kb += 32) {
-            const int kk = kb + lane;
-            const bool have = kk < k1;
-            const float4 rk = have ? recs[s0 + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int ik = have ? rec_idx(rk) : -1;
-            const int row = have ? rec_pos(rk) : -1 - lane;   // distinct for idle lanes
-            int n = ik;                                        // sources of a wide chunk's target
-            if (!isw) {
-                const float wk = have ? wbuf[s0 + ik] : 0.f;
-                float U = wk * rk.y;
+        const int32_t* bs = bstart + b * (P + 1);
+        for (int I0 = 0; I0 < P; I0 += kPrepBatch) {
+            int k0v[kPrepBatch], k1v[kPrepBatch];
+            float4 rkv[kPrepBatch];
+            float wkv[kPrepBatch];
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float up = __shfl_down_sync(HK_FULL, U, o);
-                    const int rowo = __shfl_down_sync(HK_FULL, row, o);
-                    if (lane + o < 32 && rowo == row) U += up;
-                }
-                const int prow = __shfl_up_sync(HK_FULL, row, 1);
-                const int pidx = __shfl_up_sync(HK_FULL, ik, 1);
-                const int lo = (lane > 0 && prow == row) ? pidx : -1;
-                if (have) kprep[s0 + kk] = make_int4(row, __float_as_int(U), ik, lo);
-                n = ik - (lo > 0 ? lo : 0);
+            for (int q = 0; q < kPrepBatch; ++q) {
+                const bool in = I0 + q < P;
+                k0v[q] = in ? __ldg(bs + I0 + q) : 0;
+                k1v[q] = in ? __ldg(bs + I0 + q + 1) : 0;
             }
-            if (have) atomicAdd(&work[row >> lgR], ((n + 31) >> 5) + 1);
+#pragma unroll
+            for (int q = 0; q < kPrepBatch; ++q) {
+                const int kk = k0v[q] + lane;
+                rkv[q] = kk < k1v[q] ? __ldg(recs + s0 + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < kPrepBatch; ++q) {
+                const int kk = k0v[q] + lane;
+                wkv[q] = (!isw && kk < k1v[q]) ? __ldg(wbuf + s0 + rec_idx(rkv[q])) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < kPrepBatch; ++q) {
+                const int I = I0 + q;
+                if (I >= P) break;
+                for (int e = lane; e < nrb; e += 32) work[e] = 0;
+                __syncwarp();
+                step(s0, isw, k0v[q] + lane, k1v[q], rkv[q], wkv[q]);
+                for (int kb = k0v[q] + 32; kb < k1v[q]; kb += 32) {
+                    const int kk = kb + lane;
+                    const float4 rk = kk < k1v[q] ? __ldg(recs + s0 + kk) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float wk = (!isw && kk < k1v[q]) ? __ldg(wbuf + s0 + rec_idx(rk)) : 0.f;
+                    step(s0, isw, kk, k1v[q], rk, wk);
+                }
+                __syncwarp();
+                for (int e = lane; e < nrb; e += 32) p.pwork[(int64_t)(I * nrb + e) * p.nb_max + b] = work[e];
+                __syncwarp();
+            }
         }
-        __syncwarp();
-        for (int e = lane; e < nrb; e += 32) p.pwork[(int64_t)(I * nrb + e) * p.nb_max + b] = work[e];
-        __syncwarp();
     }
 }
 
@@ -703,7 +735,7 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int P = p.P;
     if (p.grad) {
-        int64_t blocks = (nb * P + 7) / 8;
+        int64_t blocks = (nb + 7) / 8;
         if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
         k_bwd_prep<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(p, p.recs, p.bstart, p.wide,
                                                                         p.wbuf, p.kprep);

@@ -440,18 +440,32 @@ __global__ void __launch_bounds__(128) k_scan_reduce_fast(Problem p, int64_t g_b
         p.grp_reset[g] = final ? 1 : 0;
     }
     __syncthreads();
+    // four events per thread and step, their loads issued before any of their stores
+    constexpr int U = 4;
     const int64_t k0 = b0 * C, k1 = b1 * C < N ? b1 * C : N;
-    for (int64_t l = k0 + tid; l < k1; l += blockDim.x) {
-        const int i = (int)((uint64_t)(l - k0) / (uint64_t)C);
-        const double tl = p.t[l];
-        const float dl = (float)tdiff(p, tl, t0_sh[i]);
-        p.delta[l] = dl;
-        if (final) continue;
-        const float x = narrow_sh[i] ? D_sh[i] - dl : (float)tdiff(p, tn_sh[i], tl);
-        const float e = F_sh[i] * exp_unbiased(-beta * x);
-        const int cl = p.c[l];
-        atomicAdd(split ? &Sw[cl] : &S[cl], e);
-        if (GRAD) atomicAdd(split ? &Gw[cl] : &G[cl], (X_sh[i] + x) * e);
+    const int nt = blockDim.x;
+    for (int64_t lb = k0 + tid; lb < k1; lb += (int64_t)U * nt) {
+        double tl[U];
+        int cl[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t l = lb + (int64_t)u * nt;
+            tl[u] = l < k1 ? __ldg(p.t + l) : 0.0;
+            cl[u] = (!final && l < k1) ? __ldg(p.c + l) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t l = lb + (int64_t)u * nt;
+            if (l >= k1) break;
+            const int i = (int)((uint64_t)(l - k0) / (uint64_t)C);
+            const float dl = (float)tdiff(p, tl[u], t0_sh[i]);
+            p.delta[l] = dl;
+            if (final) continue;
+            const float x = narrow_sh[i] ? D_sh[i] - dl : (float)tdiff(p, tn_sh[i], tl[u]);
+            const float e = F_sh[i] * exp_unbiased(-beta * x);
+            atomicAdd(split ? &Sw[cl[u]] : &S[cl[u]], e);
+            if (GRAD) atomicAdd(split ? &Gw[cl[u]] : &G[cl[u]], (X_sh[i] + x) * e);
+        }
     }
     __syncthreads();
     if (split)      // fold the warps' copies
