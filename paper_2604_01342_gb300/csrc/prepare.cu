@@ -141,7 +141,39 @@ __global__ void k_validate_events(Problem p, int chunks_per_block, int64_t b_beg
         for (int i = threadIdx.x; i < span; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     int bad = 0;
-    for (int64_t b = b0; b < b1; ++b) {
+    if (p.B == 1) {
+        // one sequence: the block's chunks are one run of events [e0, e1), taken four events
+        // per thread and step with their loads issued together
+        int64_t e0, e1, x0, x1;
+        chunk_range(p, b0, 0, e0, x0);
+        chunk_range(p, b1 - 1, 0, x1, e1);
+        const uint64_t Tkey = time_key(p.Tarr[0]);
+        const int64_t first = p.off[0];
+        constexpr int U = 4;
+        const int nt = blockDim.x;
+        for (int64_t kb = e0 + threadIdx.x; kb < e1; kb += (int64_t)U * nt) {
+            uint64_t key[U], prev[U];
+            int32_t ck[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = kb + (int64_t)u * nt;
+                const bool in = k < e1;
+                key[u] = in ? time_key(__ldg(p.t + k)) : 0ull;
+                prev[u] = (in && k > first) ? time_key(__ldg(p.t + k - 1)) : 0ull;
+                ck[u] = in ? __ldg(p.c + k) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (kb + (int64_t)u * nt >= e1) break;
+                if (key[u] > Tkey) bad = bad ? bad : HAWKES_ERR_TIME_RANGE;
+                if (key[u] < prev[u]) bad = bad ? bad : HAWKES_ERR_UNSORTED;
+                if (ck[u] < 0 || ck[u] >= p.M) { bad = bad ? bad : HAWKES_ERR_MARK_RANGE; continue; }
+                if (use_hist) atomicAdd(&hist[ck[u]], 1);
+                else atomicAdd((unsigned long long*)&p.counts[ck[u]], 1ull);
+            }
+        }
+    }
+    for (int64_t b = b0; b < b1 && p.B != 1; ++b) {
         int32_t seq = p.chunk_seq[b];
         int64_t s0, s1;
         chunk_range(p, b, seq, s0, s1);
@@ -200,7 +232,7 @@ cudaError_t launch_prepare_head(const Problem& p, cudaStream_t s, int validate, 
 // The event checks and counts of chunks [b_begin, b_end).
 cudaError_t launch_validate_chunks(const Problem& p, cudaStream_t s, int64_t b_begin,
                                    int64_t b_end, int* nl) {
-    const int cpb = 16;
+    const int cpb = p.B == 1 ? 64 : 16;
     if (b_end > p.nb_max) b_end = p.nb_max;
     int64_t blocks = (b_end - b_begin + cpb - 1) / cpb;
     if (blocks < 1) blocks = 1;
