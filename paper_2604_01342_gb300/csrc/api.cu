@@ -204,7 +204,7 @@ int make_plan(int64_t N, int32_t M, int32_t B, int grad, const hawkes_opts* o, P
         pl->off_Y = take(sizeof(float) * nbM);
         pl->off_llpart = take(sizeof(float) * 2 * (size_t)hk::kLogSumBlocks);
         pl->off_isc = take(sizeof(float) * (3 * (size_t)M + 2 * (size_t)pl->nb_max));
-        pl->off_colmax = take(sizeof(uint32_t) * (size_t)M);
+        pl->off_colmax = take(sizeof(uint32_t) * 2 * (size_t)M);   // colmax, then wmax
         pl->off_al_p = take(h * (size_t)M * pl->ldk);
         pl->off_S_p = take(h * (size_t)pl->nb_max * pl->ldk);
         if (grad) {
@@ -314,6 +314,8 @@ void bind(hk::Problem& p, void* ws, const Plan& pl, int32_t B, int32_t M, int gr
     p.isc_Wt = p.isc_G ? p.isc_G + pl.nb_max : nullptr;
     p.isc_St = p.isc_Wt ? p.isc_Wt + M : nullptr;
     p.colmax = at<uint32_t>(ws, pl.off_colmax);
+    p.wmax = p.colmax ? p.colmax + M : nullptr;
+    p.w_rowstats = 0;
     p.ldk = pl.ldk;
     p.ldt = pl.ldt;
     p.nbp = pl.nbp;

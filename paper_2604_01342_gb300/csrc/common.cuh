@@ -126,6 +126,8 @@ struct Problem {
     float* cen_acc;          // [32][2M] column sums of the sampled rows per row slice, then
                              // the number of sampled rows
     double* wsum_acc;        // [M] sum_b W[b][i]
+    uint32_t* wmax;          // [M] largest W[b][i] over b (bits of a non-negative float)
+    int32_t w_rowstats;      // 1: the epilogue takes wsum_acc and wmax while it writes W
     int64_t ldk;             // 64 ceil(M / 32): halves per paired row of K = M elements
     int64_t ldt;             // 64 ceil(nbp / 32): halves per paired row of K = nbp elements
     int64_t nbp;             // nb_max rounded up to 8

@@ -33,7 +33,7 @@ cudaError_t split_f16_rows(const float* src, int64_t lds, __half* dst, int64_t l
                            const float* coef);
 cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* dst, int64_t ldd,
                                 int64_t rows, int64_t cols, cudaStream_t s, float* inv_scale,
-                                double* row_sum);
+                                double* row_sum, const uint32_t* row_max = nullptr);
 cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
                                 const float* centre, const float* centre2, const float* coef,
                                 __half* out1,
@@ -494,20 +494,25 @@ __global__ void __launch_bounds__(512, 3) k_epilogue(Problem p, const float* __r
 // By groups of kEpiGroup consecutive chunks: a block takes a group at a time, accumulates
 // its W entries in shared memory and writes them out as one 32-byte piece per mark (W is
 // transposed, [M][nbp] with nbp a multiple of kEpiGroup, so the groups cover every column and
-// W needs no zeroing).
+// W needs no zeroing).  The thread that writes a mark's piece also keeps the mark's largest
+// entry and, in FP64, the sum of its entries, flushed once per block (wmax, wsum_acc), so
+// that the split of W for the dalpha GEMM needs one pass over it instead of two.
 constexpr int kEpiGroup = 8;
 
 template <bool GRAD>
 __global__ void __launch_bounds__(512, 3) k_epilogue_groups(Problem p, const float* __restrict__ Aint,
                                                          const float* __restrict__ Bint,
                                                          float* wbuf) {
-    extern __shared__ float sh[];
+    extern __shared__ double shd[];
     const int M = p.M, C = p.C;
+    double* wsum = shd;                       // [M] this block's sums of W entries (GRAD)
+    float* sh = (float*)(shd + (GRAD ? M : 0));
     float* hEt = sh;                          // [M] sum of exp(-beta (T - t)) (tail events)
     float* hF = hEt + M;                      // [M]
     float* hmu = hF + M;                      // [M]
     uint32_t* hcnt = (uint32_t*)(hmu + M);    // [M] events per mark (without validation)
-    float* Wg = (float*)(hcnt + M);           // [kEpiGroup][M] the group's W entries (GRAD)
+    uint32_t* wmx = hcnt + M;                 // [M] this block's largest W entries (GRAD)
+    float* Wg = (float*)(wmx + (GRAD ? M : 0));   // [kEpiGroup][M] the group's W entries (GRAD)
     __shared__ double red_ll[16];
     __shared__ double red_db[16];
     __shared__ SumF32 red_ls[16];
@@ -519,7 +524,9 @@ __global__ void __launch_bounds__(512, 3) k_epilogue_groups(Problem p, const flo
     const double T = p.Tarr[0];
     const bool counted = p.validated != 0;
     const int nt = blockDim.x;
-    for (int j = threadIdx.x; j < 4 * M; j += nt) sh[j] = 0.f;
+    for (int j = threadIdx.x; j < (GRAD ? 5 : 4) * M; j += nt) sh[j] = 0.f;
+    if (GRAD)
+        for (int j = threadIdx.x; j < M; j += nt) wsum[j] = 0.0;
     __syncthreads();
     EpiSums acc;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
@@ -546,19 +553,35 @@ __global__ void __launch_bounds__(512, 3) k_epilogue_groups(Problem p, const flo
         if (GRAD) {
             __syncthreads();
             for (int m = threadIdx.x; m < M; m += nt) {
+                const float4 lo = make_float4(Wg[m], Wg[M + m], Wg[2 * M + m], Wg[3 * M + m]);
+                const float4 hi = make_float4(Wg[4 * M + m], Wg[5 * M + m], Wg[6 * M + m], Wg[7 * M + m]);
                 float4* dst = (float4*)(p.W + (int64_t)m * ldw + b0);
-                dst[0] = make_float4(Wg[m], Wg[M + m], Wg[2 * M + m], Wg[3 * M + m]);
-                dst[1] = make_float4(Wg[4 * M + m], Wg[5 * M + m], Wg[6 * M + m], Wg[7 * M + m]);
+                dst[0] = lo;
+                dst[1] = hi;
+                const float mx = fmaxf(fmaxf(fmaxf(lo.x, lo.y), fmaxf(lo.z, lo.w)),
+                                       fmaxf(fmaxf(hi.x, hi.y), fmaxf(hi.z, hi.w)));
+                wmx[m] = max(wmx[m], __float_as_uint(mx));     // entries are >= 0
+                wsum[m] += (double)((lo.x + lo.y) + (lo.z + lo.w)) +
+                           (double)((hi.x + hi.y) + (hi.z + hi.w));
             }
         }
     }
     __syncthreads();
+    if (GRAD)
+        for (int m = threadIdx.x; m < M; m += nt) {
+            if (wmx[m]) atomicMax(&p.wmax[m], wmx[m]);
+            if (wsum[m] != 0.0) atomicAdd(&p.wsum_acc[m], wsum[m]);
+        }
     epi_flush<GRAD>(p, acc, mode, counted, hEt, hF, hmu, hcnt, red_ll, red_db, red_ls);
 }
 
-// Shared memory of the group epilogue.
+// Shared memory of the group epilogue, and whether it fits.
 static size_t epi_group_smem(int64_t M, bool grad) {
-    return sizeof(float) * (size_t)M * (4 + (grad ? kEpiGroup : 0));
+    return sizeof(float) * (size_t)M * (4 + (grad ? 1 + kEpiGroup : 0)) +
+           (grad ? sizeof(double) * (size_t)M : 0);
+}
+static bool epi_groups(const Problem& p) {
+    return epi_group_smem(p.M, p.grad) <= 227 * 1024 - 512;
 }
 
 // The FP32 log-sums of the epilogue's blocks, in block order (mode 1 compensated, mode 2
@@ -686,10 +709,10 @@ cudaError_t launch_gemm_epilogue(const Problem& p, cudaStream_t s, int* nl) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem_max = 227 * 1024 - 512;
-    const bool groups = epi_group_smem(M, p.grad) <= smem_max;
+    const bool groups = epi_groups(p);
     int blocks;
     if (groups) {
+        if (p.grad && p.w_rowstats) cudaMemsetAsync(p.wmax, 0, sizeof(uint32_t) * (size_t)M, s);
         const size_t smem = epi_group_smem(M, p.grad);
         auto kern = p.grad ? k_epilogue_groups<true> : k_epilogue_groups<false>;
         if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -751,8 +774,10 @@ cudaError_t launch_gemm_backward(const Problem& p, cudaStream_t s, int* nl) {
         // dalpha_gemm[i][j] = sum_b W[b][i] S^[b][j] with the chunk index as the contiguous
         // K dimension: W is already transposed (columns past the chunk count are 0), S^ is
         // transposed here
+        // (row maxima and sums from the group epilogue when it took them: one pass over W)
         if ((err = split_f16_long_rows(p.W, p.nbp, p.Wt_p, p.ldt, M, p.nbp, s, p.isc_Wt,
-                                       p.wsum_acc)) != cudaSuccess)
+                                       p.w_rowstats ? nullptr : p.wsum_acc,
+                                       p.w_rowstats ? p.wmax : nullptr)) != cudaSuccess)
             return err;
         ++*nl;
         prof_mark(s, "split_W");
@@ -916,7 +941,9 @@ cudaError_t launch_epilogue_multi(const Problem& p, const MultiSlices& ms, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_path(const Problem& p, cudaStream_t s, int* nl) {
+cudaError_t launch_gemm_path(const Problem& p0, cudaStream_t s, int* nl) {
+    Problem p = p0;
+    p.w_rowstats = p.grad && epi_groups(p) ? 1 : 0;
     cudaError_t err = launch_gemm_forward(p, s, nl);
     if (err == cudaSuccess) err = launch_gemm_epilogue(p, s, nl);
     if (err == cudaSuccess) err = launch_gemm_backward(p, s, nl);

@@ -692,7 +692,7 @@ cudaError_t split_f16_rows_pair(const float* src, const float* sub, int64_t lds,
 constexpr int kLongRowThreads = 512;
 __global__ void __launch_bounds__(kLongRowThreads) k_split_f16_long_rows(
     const float* __restrict__ src, int64_t lds, __half* dst, int64_t ldd, int64_t rows,
-    int64_t cols, float* inv_scale, double* row_sum) {
+    int64_t cols, float* inv_scale, double* row_sum, const uint32_t* __restrict__ row_max) {
     __shared__ float red[kLongRowThreads / 32];
     __shared__ double reds[kLongRowThreads / 32];
     const int64_t cpad = tc::round32(cols);
@@ -700,7 +700,12 @@ __global__ void __launch_bounds__(kLongRowThreads) k_split_f16_long_rows(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
         const float* sr = src + r * lds;
-        float amax = 0.f, part = 0.f;         // FP32 partial sums per thread, FP64 across
+        float amax = 0.f;
+        if (row_max) {
+            // the row's largest magnitude is given (non-negative rows): one pass
+            amax = __uint_as_float(row_max[r]);
+        } else {
+        float part = 0.f;                     // FP32 partial sums per thread, FP64 across
         const int64_t c4end = vec ? (cols & ~(int64_t)3) : 0;
 #pragma unroll 4
         for (int64_t c = 4 * (int64_t)threadIdx.x; c < c4end; c += 4 * (int64_t)blockDim.x) {
@@ -726,6 +731,7 @@ __global__ void __launch_bounds__(kLongRowThreads) k_split_f16_long_rows(
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { amax = fmaxf(amax, red[w]); sum += reds[w]; }
         __syncthreads();                                  // red is reused by the next row
         if (row_sum && threadIdx.x == 0) row_sum[r] = sum;
+        }
         const int a = tc::row_exponent(amax);
         const float sc = ldexpf(1.f, a);
         __half* dr = dst + r * ldd;
@@ -740,14 +746,17 @@ __global__ void __launch_bounds__(kLongRowThreads) k_split_f16_long_rows(
     }
 }
 
+// row_max (optional): the largest magnitude of every row as float bits, taken by the caller;
+// the rows are then read once (row_sum is not formed).
 cudaError_t split_f16_long_rows(const float* src, int64_t lds, __half* dst, int64_t ldd,
                                 int64_t rows, int64_t cols, cudaStream_t s, float* inv_scale,
-                                double* row_sum) {
+                                double* row_sum, const uint32_t* row_max) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     if ((ldd & 1) || ldd < 2 * tc::round32(cols)) return cudaErrorInvalidValue;
     const int64_t blocks = rows < 152 * 2 ? rows : 152 * 2;
     k_split_f16_long_rows<<<(unsigned)blocks, kLongRowThreads, 0, s>>>(src, lds, dst, ldd, rows,
-                                                                       cols, inv_scale, row_sum);
+                                                                       cols, inv_scale, row_sum,
+                                                                       row_max);
     return cudaGetLastError();
 }
 
@@ -759,7 +768,7 @@ cudaError_t split_f16_rows(const float* src, int64_t lds, __half* dst, int64_t l
     if ((sub == nullptr) != (coef == nullptr) || (ldd & 1) || ldd < 2 * tc::round32(cols))
         return cudaErrorInvalidValue;
     if (cols >= 4096 && !centre && !rows_valid && !sub)
-        return split_f16_long_rows(src, lds, dst, ldd, rows, cols, s, inv_scale, nullptr);
+        return split_f16_long_rows(src, lds, dst, ldd, rows, cols, s, inv_scale, nullptr, nullptr);
     int64_t blocks = (rows + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_split_f16_rows<<<(unsigned)blocks, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, centre,
