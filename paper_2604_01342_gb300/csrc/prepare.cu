@@ -232,8 +232,19 @@ cudaError_t launch_prepare_head(const Problem& p, cudaStream_t s, int validate, 
 // The event checks and counts of chunks [b_begin, b_end).
 cudaError_t launch_validate_chunks(const Problem& p, cudaStream_t s, int64_t b_begin,
                                    int64_t b_end, int* nl) {
-    const int cpb = p.B == 1 ? 64 : 16;
     if (b_end > p.nb_max) b_end = p.nb_max;
+    // one sequence: about 12,288 events per block (one mark-histogram flush per block), but
+    // at least two blocks per SM
+    int cpb = 16;
+    if (p.B == 1) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int64_t per = (12288 + p.C - 1) / p.C;
+        const int64_t spread = (b_end - b_begin) / (2 * (int64_t)sms);
+        if (per > spread) per = spread;
+        cpb = (int)(per < 1 ? 1 : (per > 64 ? 64 : per));
+    }
     int64_t blocks = (b_end - b_begin + cpb - 1) / cpb;
     if (blocks < 1) blocks = 1;
     k_validate_events<<<(unsigned)blocks, 256, 0, s>>>(p, cpb, b_begin, b_end);
