@@ -5,14 +5,9 @@ compare with the stated tolerances:
   max-norm relative gradient error max|g - g*| / max|g*|    <= 1e-4 per block
 The oracle is evaluated at the FP32-rounded parameters the GPU receives.
 
-One reading is allowed for the log-likelihood only, and only where a test asks
-for it (the batch of short per-source sequences): L is the difference of the
-intensity logs and the compensator, and for some short sequences the two nearly
-cancel, so that |L*| is far below the size of its terms and a relative error
-of 1e-6 would need the FP32 intensities to be better than FP32.  With the
-oracle's conditioning scale S of L (the sum of the magnitudes of its terms,
-oracle.condition), such an L passes when |L - L*| <= 1e-7 S.  Every such case
-is reported with its kappa = S / |L*|.  Gradients have no such reading."""
+Both are asserted as such.  Where a result is a known miss (a near-cancelling sum whose
+FP32 terms cannot reach the tolerance), the test asserts everything else at the stated
+tolerances and reports the miss as an expected failure with its measured error."""
 import numpy as np
 
 LL_RTOL = 1e-6
@@ -65,27 +60,14 @@ def maxnorm_rel(got, ref):
     return float(np.max(np.abs(got - ref))) / (den if den > 0 else 1.0)
 
 
-SCALE_REL = 1e-7
-
-
-def assert_close(got, ref, grad=True, ll_rtol=LL_RTOL, grad_rtol=GRAD_RTOL, what="",
-                 ll_scale=None):
-    """Stated tolerances per result; ``ll_scale`` (the oracle's conditioning scale of L)
-    admits an ill-conditioned L at 1e-7 of its scale, and returns True when it did."""
-    used_scale = False
+def assert_close(got, ref, grad=True, ll_rtol=LL_RTOL, grad_rtol=GRAD_RTOL, what=""):
+    """Stated tolerances per result."""
     e = rel_err(got["ll"], ref["ll"])
-    if e > ll_rtol and ll_scale is not None:
-        kappa = ll_scale / abs(ref["ll"])
-        e_s = abs(got["ll"] - ref["ll"]) / ll_scale
-        print(f"{what}: loglik kappa {kappa:.1f}: rel err {e:.3e}, err / scale {e_s:.3e}")
-        e = e_s * ll_rtol / SCALE_REL
-        used_scale = True
     assert e <= ll_rtol, f"{what} loglik rel err {e:.3e} (gpu {got['ll']!r} vs {ref['ll']!r})"
     if grad:
         for k in ("dmu", "dalpha", "dbeta"):
             e = maxnorm_rel(got[k], ref[k])
             assert e <= grad_rtol, f"{what} {k} max-norm rel err {e:.3e}"
-    return used_scale
 
 
 def support_oracle_from_files(paths):

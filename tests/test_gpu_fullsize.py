@@ -6,15 +6,17 @@ per block):
     minute on one host core; it starts in a background thread when this module's first
     test runs) and a 2e5-event prefix;
   * the M=64 per-source stream of 1e6 events;
-  * the 4,096-sequence batch of M=8 sequences, where the log-likelihood of some short
-    sequences is ill-conditioned (see helpers.py) and is then stated against its scale.
+  * the 4,096-sequence batch of M=8 sequences: every gradient and every log-likelihood at the
+    stated tolerances, except the log-likelihoods of a few short sequences whose intensity
+    logs and compensator nearly cancel (a known miss, reported as an expected failure with
+    each case's error and conditioning).
 """
 import threading
 
 import numpy as np
 import pytest
 
-from helpers import assert_close, f32, gpu_run, maxnorm_rel, oracle_ref, rel_err
+from helpers import GRAD_RTOL, LL_RTOL, assert_close, f32, gpu_run, maxnorm_rel, oracle_ref, rel_err
 from paper_2604_01342_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -99,26 +101,37 @@ def test_varlen_4096_full_size():
     ll, dmu, dal, dbe = [x.cpu().numpy().astype(np.float64) for x in r]
     ref = oracle.loglik_grad_varlen(vp.t, vp.c, vp.offsets, vp.T, f32(vp.mu), f32(vp.alpha),
                                     f32(vp.beta))
-    worst, n_scaled, worst_scaled = 0.0, 0, (0.0, 0.0, -1)
+    worst, misses = 0.0, []
     for s in range(vp.B):
         got = {"ll": ll[s], "dmu": dmu[s], "dalpha": dal[s], "dbeta": dbe[s]}
         want = {k: ref[k][s] for k in ("ll", "dmu", "dalpha", "dbeta")}
-        scale = None
-        if rel_err(got["ll"], want["ll"]) > 1e-6:
-            a, b = vp.offsets[s], vp.offsets[s + 1]
-            scale = oracle.condition(vp.t[a:b], vp.c[a:b], vp.T[s], f32(vp.mu[s]),
-                                     f32(vp.alpha[s]), f32(vp.beta[s]))["ll"]
-        if assert_close(got, want, what=f"seq {s}", ll_scale=scale):
-            n_scaled += 1
-            e = rel_err(got["ll"], want["ll"])
-            if e > worst_scaled[0]:
-                worst_scaled = (e, scale / abs(want["ll"]), s)
-        else:
-            worst = max(worst, rel_err(got["ll"], want["ll"]))
-    print(f"varlen 4096 x M=8: worst loglik rel err of the well-conditioned sequences "
-          f"{worst:.3e}; {n_scaled} ill-conditioned L stated against their scale, worst rel err "
-          f"{worst_scaled[0]:.3e} at kappa {worst_scaled[1]:.0f} (sequence {worst_scaled[2]}); "
-          f"every gradient at the stated tolerance")
+        for k in ("dmu", "dalpha", "dbeta"):
+            e = maxnorm_rel(got[k], want[k])
+            assert e <= GRAD_RTOL, f"seq {s} {k} max-norm rel err {e:.3e}"
+        e = rel_err(got["ll"], want["ll"])
+        if e <= LL_RTOL:
+            worst = max(worst, e)
+            continue
+        # a miss must be explained by the conditioning of L (the intensity logs and the
+        # compensator nearly cancel): its error at most 1e-7 of the sum of its terms'
+        # magnitudes, the level of FP32 intensities
+        a, b = vp.offsets[s], vp.offsets[s + 1]
+        scale = oracle.condition(vp.t[a:b], vp.c[a:b], vp.T[s], f32(vp.mu[s]),
+                                 f32(vp.alpha[s]), f32(vp.beta[s]))["ll"]
+        kappa = scale / abs(want["ll"])
+        err_scale = abs(got["ll"] - want["ll"]) / scale
+        assert err_scale <= 1e-7, (s, e, kappa, err_scale)
+        misses.append((e, kappa, s))
+    print(f"varlen 4096 x M=8: worst loglik rel err of the others {worst:.3e}; every gradient "
+          f"at the stated tolerance")
+    if misses:
+        e, kappa, s = max(misses)
+        pytest.xfail(f"known miss: {len(misses)} of {vp.B} short-sequence log-likelihoods are "
+                     f"ill-conditioned (kappa {min(m[1] for m in misses):.0f} to "
+                     f"{max(m[1] for m in misses):.0f}) and miss 1e-6 relative, worst {e:.2e} "
+                     f"at kappa {kappa:.0f} (sequence {s}); their errors are below 1e-7 of the "
+                     f"sum of their terms' magnitudes; every gradient and the other "
+                     f"{vp.B - len(misses)} log-likelihoods meet the stated tolerances")
 
 
 @pytest.fixture(scope="module")
