@@ -349,17 +349,21 @@ __global__ void __launch_bounds__(256) k_scan_states_fast(Problem p) {
         const float D = Dn, d0 = dn;
         const int c0 = cn;
         if (b + 1 < b1) slot(b + 1, Dn, cn, dn);
-        for (int j = tid; j < M; j += blockDim.x) {
-            p.Shat[b * M + j] = S[j];
-            if (GRAD) p.Ghat[b * M + j] = G[j];
-        }
-        if (s1 == N) break;                     // the last chunk maps to the zero state
-        const float d = exp_unbiased(-beta * D);
+        // the chunk-start state out and decayed to the next chunk start in one pass (each
+        // thread its own entries)
+        const bool last = s1 == N;              // the last chunk maps to the zero state
+        const float d = last ? 0.f : exp_unbiased(-beta * D);
         for (int j = tid; j < M; j += blockDim.x) {
             const float sv = S[j];
-            if (GRAD) G[j] = d * (G[j] + D * sv);
+            p.Shat[b * M + j] = sv;
+            if (GRAD) {
+                const float gv = G[j];
+                p.Ghat[b * M + j] = gv;
+                G[j] = d * (gv + D * sv);
+            }
             S[j] = d * sv;
         }
+        if (last) break;
         __syncthreads();
         const bool narrow = beta * D <= 16.f;
         for (int64_t l = s0 + tid; l < s1; l += blockDim.x) {
